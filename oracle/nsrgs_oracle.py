@@ -1,0 +1,280 @@
+"""Plain FP64 NumPy oracle of NS-RGS (Peng, Han, Chen, Huang, arXiv 2604.07372).
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py``; never by the CUDA product path.
+
+Everything here is written straight from the paper's definitions, in float64,
+with library primitives (matmul, SVD, symmetric eigensolver) as steps and no
+blocking, fusion or reordering beyond what the definitions state.
+
+Notation (paper §1.4): X = (X_1; ...; X_n) is nd x d with d x d blocks X_i;
+A = [A_ij] is the symmetric nd x nd matrix of pairwise measurements with
+A_ii = I_d (self-loops excluded, §2.2 eq. (4)).
+
+Readings of points the paper leaves open (each one also listed in the design
+notes of the repository):
+  * gradient: Algorithm 2's form G_i = sum_{j != i} (X_i - A_ij X_j), taken
+    literally (also for sparse data, where unobserved A_ij = 0);
+  * projection: the paper's (G - X_i G^T X_i)/2, applied also when X_i is only
+    approximately orthogonal ("pseudo projection", §2.2);
+  * all blocks are updated simultaneously from X^t (Algorithm 2 uses X_j^t on
+    the right-hand side);
+  * Newton-Schulz starts unscaled, S_0 = F_i (Algorithm 1);
+  * spectral initialisation takes the eigenvectors of the d largest
+    *algebraic* eigenvalues of A;
+  * GPM (the paper's comparison method, not written out there) is read as
+    X_i <- sgn(sum_j A_ij X_j) including the j = i term A_ii X_i = X_i.
+
+Pins (tests marked "not gpu" in tests/test_oracle_pins.py) tie each function
+to something other than itself: the Newton-Schulz singular-value map and
+Lemma 2.1's bound, tangent-space identities, a finite-difference check of the
+gradient, hand-derived closed forms of one iteration for rotations in O(2),
+exact recovery at sigma = 0, equivariance, brute-force minimality of d_F,
+Courant-Fischer for the spectral subspace, and Table 1's relative errors.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "sgn",
+    "sgn_blocks",
+    "newton_schulz",
+    "tangent_projection",
+    "euclidean_gradient",
+    "nsrgs_iteration",
+    "spectral_init",
+    "nsrgs",
+    "objective",
+    "dF",
+    "rel_err",
+    "mse",
+    "update_norm",
+    "gpm_iteration",
+    "gpm",
+    "blocks",
+    "stack",
+]
+
+
+# ---------------------------------------------------------------- helpers
+def blocks(X: np.ndarray, d: int) -> np.ndarray:
+    """View the nd x d stack X as an (n, d, d) array of blocks X_i."""
+    return np.asarray(X, dtype=np.float64).reshape(-1, d, d)
+
+
+def stack(Xb: np.ndarray) -> np.ndarray:
+    """Inverse of ``blocks``: (n, d, d) -> nd x d."""
+    n, d, _ = Xb.shape
+    return Xb.reshape(n * d, d)
+
+
+# ------------------------------------------------------ §2.1: matrix sign
+def sgn(M: np.ndarray) -> np.ndarray:
+    """Matrix sign of a square matrix (§2.1): M = U Sigma V^T (full SVD) -> U V^T."""
+    U, _, Vt = np.linalg.svd(np.asarray(M, dtype=np.float64))
+    return U @ Vt
+
+
+def sgn_blocks(Phi: np.ndarray, d: int) -> np.ndarray:
+    """Blockwise matrix sign of an nd x d stack (§2.1): (sgn(A_1); ...; sgn(A_n))."""
+    Pb = blocks(Phi, d)
+    U, _, Vt = np.linalg.svd(Pb)
+    return stack(U @ Vt)
+
+
+# ------------------------------------ §2.1, Algorithm 1: Newton-Schulz
+def newton_schulz(M: np.ndarray, Ts: int) -> np.ndarray:
+    """Algorithm 1: S_0 = M, S_{t+1} = (1/2) S_t (3 I - S_t^T S_t), t < Ts.
+
+    Accepts one d x d matrix or a stack (n, d, d) of them (applied blockwise).
+    """
+    S = np.array(M, dtype=np.float64, copy=True)
+    d = S.shape[-1]
+    I = np.eye(d)
+    for _ in range(Ts):
+        S = 0.5 * (S @ (3.0 * I - np.swapaxes(S, -1, -2) @ S))
+    return S
+
+
+# ---------------------------------------------- §2.2: tangent projection
+def tangent_projection(Xi: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """P_{X_i}(G) = (G - X_i G^T X_i) / 2 (§2.2); blockwise on (n, d, d) stacks."""
+    Xi = np.asarray(Xi, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    return 0.5 * (G - Xi @ np.swapaxes(G, -1, -2) @ Xi)
+
+
+# ------------------------------------------ §2.2 / Algorithm 2: gradient
+def euclidean_gradient(A: np.ndarray, X: np.ndarray, n: int, d: int) -> np.ndarray:
+    """G_i = sum_{j != i} (X_i - A_ij X_j) for every i (Algorithm 2), as (n, d, d).
+
+    sum_{j != i} A_ij X_j is the i-th block of A X minus the diagonal term
+    A_ii X_i; the library matmul A @ X serves as the step that forms A X.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Xb = blocks(X, d)
+    AX = blocks(A @ stack(Xb), d)
+    Aii = np.stack([A[i * d : (i + 1) * d, i * d : (i + 1) * d] for i in range(n)])
+    offdiag = AX - Aii @ Xb
+    return (n - 1) * Xb - offdiag
+
+
+# ------------------------------------------ Algorithm 2: one iteration
+def nsrgs_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, Ts: int) -> np.ndarray:
+    """One sweep of Algorithm 2's loop body for all i, every block from X^t.
+
+    G_i = sum_{j != i}(X_i - A_ij X_j);  F_i = X_i - mu P_{X_i}(G_i);
+    X_i^{t+1} = S(F_i) with S = Algorithm 1 run for Ts steps.
+    """
+    Xb = blocks(X, d)
+    G = euclidean_gradient(A, X, n, d)
+    F = Xb - mu * tangent_projection(Xb, G)
+    return stack(newton_schulz(F, Ts))
+
+
+# ---------------------------------------- Algorithm 2: spectral start
+def spectral_init(A: np.ndarray, n: int, d: int, method: str = "auto") -> tuple[np.ndarray, np.ndarray]:
+    """Spectral initialisation of Algorithm 2.
+
+    Y = eigenvectors of the d largest (algebraic) eigenvalues of A, Y^T Y = I;
+    X^0 = sgn_n(Y) (blockwise matrix sign).  Returns (X0, Y).
+
+    ``method='eigh'`` is the full symmetric eigensolver (LAPACK); ``'eigsh'`` the
+    ARPACK Lanczos solver for the same top-d eigenpairs, used for large nd
+    where the full solve takes minutes.  ``'auto'`` picks eigh for nd <= 4000.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    N = n * d
+    if method == "auto":
+        method = "eigh" if N <= 4000 else "eigsh"
+    if method == "eigh":
+        w, V = np.linalg.eigh(A)
+        order = np.argsort(w)[::-1][:d]
+        Y = V[:, order]
+    elif method == "eigsh":
+        from scipy.sparse.linalg import eigsh
+
+        v0 = np.ones(N) / math.sqrt(N)
+        w, V = eigsh(A, k=d, which="LA", v0=v0, tol=1e-13, maxiter=20 * N)
+        Y = V[:, np.argsort(w)[::-1]]
+    else:
+        raise ValueError(method)
+    return sgn_blocks(Y, d), Y
+
+
+# ----------------------------------------------- eq. (1): objective F
+def objective(A: np.ndarray, X: np.ndarray, n: int, d: int) -> float:
+    """F(X) = (1/2) sum_{i != j} ||X_i X_j^T - A_ij||_F^2 (eq. (1))."""
+    X = np.asarray(X, dtype=np.float64)
+    total = 0.0
+    for i in range(n):
+        rows = slice(i * d, (i + 1) * d)
+        R = X[rows] @ X.T - np.asarray(A[rows], dtype=np.float64)  # d x nd: blocks j = 0..n-1
+        R[:, i * d : (i + 1) * d] = 0.0  # j = i excluded
+        total += float(np.sum(R * R))
+    return 0.5 * total
+
+
+# -------------------------------------------------- Algorithm 2: loop
+def nsrgs(
+    A: np.ndarray,
+    n: int,
+    d: int,
+    mu: float,
+    T: int,
+    Ts: int,
+    X0: np.ndarray | None = None,
+    rel_tol: float | None = None,
+    history: bool = False,
+):
+    """Algorithm 2: spectral start (unless X0 is given), then up to T iterations.
+
+    With ``rel_tol`` set, stops after the first iteration t whose relative
+    decrease R^t = (F(X^t) - F(X^{t+1})) / F(X^{t+1}) is below it (§4.1's rule:
+    R^t < 1e-8 or 100 iterations).  Returns (X, info) where info holds the
+    number of iterations run and, with ``history``, every iterate's update
+    norm ||X^{t+1} - X^t||_F / sqrt(nd).
+    """
+    if X0 is None:
+        X0, _ = spectral_init(A, n, d)
+    X = np.array(X0, dtype=np.float64, copy=True)
+    info = {"iters": 0, "upd": []}
+    Fcur = objective(A, X, n, d) if rel_tol is not None else None
+    for t in range(T):
+        Xn = nsrgs_iteration(A, X, n, d, mu, Ts)
+        if history:
+            info["upd"].append(update_norm(Xn, X))
+        info["iters"] = t + 1
+        if rel_tol is not None:
+            Fn = objective(A, Xn, n, d)
+            R = (Fcur - Fn) / Fn if Fn != 0.0 else 0.0
+            X, Fcur = Xn, Fn
+            if R < rel_tol:
+                break
+        else:
+            X = Xn
+    return X, info
+
+
+# ------------------------------------- §1.4 notations: distance d_F
+def dF(X: np.ndarray, Y: np.ndarray, d: int) -> float:
+    """d_F(X, Y) = min_{Q in O(d)} ||X - Y Q||_F (§1.4).
+
+    The minimiser is Q* = sgn(Y^T X) (proof of Lemma 7.4); the distance is then
+    evaluated directly as ||X - Y Q*||_F rather than through the nuclear-norm
+    identity, which keeps resolution near zero.
+    """
+    X = np.asarray(X, dtype=np.float64).reshape(-1, d)
+    Y = np.asarray(Y, dtype=np.float64).reshape(-1, d)
+    Q = sgn(Y.T @ X)
+    return float(np.linalg.norm(X - Y @ Q))
+
+
+def rel_err(X: np.ndarray, Z: np.ndarray, d: int, chunk: int = 2048) -> float:
+    """Rel.Err = ||Z Z^T - X X^T||_F / ||Z Z^T||_F (§4.1), evaluated by row chunks."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, d)
+    Z = np.asarray(Z, dtype=np.float64).reshape(-1, d)
+    num = 0.0
+    den = 0.0
+    for s in range(0, X.shape[0], chunk):
+        ZZ = Z[s : s + chunk] @ Z.T
+        XX = X[s : s + chunk] @ X.T
+        num += float(np.sum((ZZ - XX) ** 2))
+        den += float(np.sum(ZZ**2))
+    return math.sqrt(num / den)
+
+
+def mse(Xhat: np.ndarray, X: np.ndarray, n: int, d: int) -> float:
+    """MSE = d_F(Xhat, X)^2 / n (§4.2)."""
+    return dF(Xhat, X, d) ** 2 / n
+
+
+def update_norm(Xnew: np.ndarray, Xold: np.ndarray) -> float:
+    """||X^{t+1} - X^t||_F / sqrt(nd): the per-iteration change used as a retire rule."""
+    Xnew = np.asarray(Xnew, dtype=np.float64)
+    Xold = np.asarray(Xold, dtype=np.float64)
+    rows = Xnew.size // Xnew.shape[-1]  # nd
+    return float(np.linalg.norm(Xnew - Xold) / math.sqrt(rows))
+
+
+# --------------------------------------------- GPM (comparison method)
+def gpm_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int) -> np.ndarray:
+    """Generalised power method step X_i <- sgn((A X)_i), with A_ii = I included.
+
+    The paper compares against GPM (§1.1, §4.1) without writing it out; this is
+    the reading used here: one full matrix product followed by an exact
+    blockwise matrix sign.
+    """
+    return sgn_blocks(np.asarray(A, dtype=np.float64) @ np.asarray(X, dtype=np.float64), d)
+
+
+def gpm(A: np.ndarray, n: int, d: int, T: int, X0: np.ndarray | None = None):
+    if X0 is None:
+        X0, _ = spectral_init(A, n, d)
+    X = np.array(X0, dtype=np.float64, copy=True)
+    for _ in range(T):
+        X = gpm_iteration(A, X, n, d)
+    return X

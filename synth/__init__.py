@@ -1,0 +1,145 @@
+"""Seeded synthetic instances of orthogonal group synchronization.
+
+This module only *generates inputs*.  It holds none of the NS-RGS arithmetic
+(no gradient, projection, Newton-Schulz step, spectral initialisation or
+distance): both the FP64 CPU oracle and the CUDA library receive the arrays
+built here, so the two sides never share method code.
+
+Measurement model (paper §1.1 and eq. (4) of §2.2): for i < j
+
+    A_ij = Z_i Z_j^T + sigma * W_ij,   W_ij with i.i.d. N(0, 1) entries,
+    A_ji = A_ij^T,   A_ii = I_d   (W_ii = 0, self-loops excluded).
+
+Ground truth (§4.1): i.i.d. standard Gaussian d x d matrices projected onto
+O(d), i.e. the polar factor U V^T of each draw (det = -1 is allowed).
+
+Incomplete observations (§4.1): each unordered pair {i, j} is observed with
+probability p; an unobserved pair has A_ij = A_ji = 0.  The mask is symmetric
+because A is symmetric; the diagonal is always present.
+
+Noise scale used by the workloads: sigma = c * sqrt(n) / (sqrt(d) + sqrt(ln n))
+(natural log), with c stated per workload.
+
+Canonical packed order ("upper-block list"): the n(n-1)/2 blocks (i, j), i < j,
+ordered by i, then j; each block d x d row-major.  Block (i, j) sits at index
+``upper_index(i, j, n)``.
+
+Random-stream order, fixed so instances are reproducible from (n, d, sigma, p,
+seed): one ``numpy.random.Generator(PCG64(seed))``; first the n ground-truth
+draws (n*d*d normals), then for each block row i = 0..n-2 the W_ij draws for
+j = i+1..n-1 ((n-1-i)*d*d normals) followed, when p < 1, by (n-1-i) uniforms for
+the observation mask (pair observed iff uniform < p).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "sigma_rule",
+    "haar_orthogonal",
+    "upper_index",
+    "num_upper_blocks",
+    "upper_blocks",
+    "dense_from_upper",
+    "Instance",
+    "make_instance",
+]
+
+
+def sigma_rule(c: float, n: int, d: int) -> float:
+    """sigma = c * sqrt(n) / (sqrt(d) + sqrt(ln n))."""
+    return float(c) * math.sqrt(n) / (math.sqrt(d) + math.sqrt(math.log(n)))
+
+
+def haar_orthogonal(rng: np.random.Generator, n: int, d: int) -> np.ndarray:
+    """n ground-truth blocks: Gaussian d x d draws projected onto O(d) (§4.1)."""
+    g = rng.standard_normal((n, d, d))
+    u, _, vt = np.linalg.svd(g)
+    return u @ vt
+
+
+def num_upper_blocks(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def upper_index(i: int, j: int, n: int) -> int:
+    """Index of block (i, j), i < j, in the canonical upper-block list."""
+    if not 0 <= i < j < n:
+        raise ValueError(f"need 0 <= i < j < n, got i={i} j={j} n={n}")
+    return i * n - i * (i + 1) // 2 + (j - i - 1)
+
+
+def upper_blocks(
+    Z: np.ndarray,
+    sigma: float,
+    rng: np.random.Generator,
+    p: float = 1.0,
+    dtype=np.float64,
+) -> np.ndarray:
+    """Canonical upper-block list of A (shape (n(n-1)/2, d, d)).
+
+    Each block row is built in float64 and then stored in ``dtype``.
+    """
+    n, d, _ = Z.shape
+    out = np.empty((num_upper_blocks(n), d, d), dtype=dtype)
+    off = 0
+    for i in range(n - 1):
+        m = n - 1 - i
+        w = rng.standard_normal((m, d, d))
+        blk = Z[i][None, :, :] @ np.transpose(Z[i + 1 :], (0, 2, 1))
+        blk += sigma * w
+        if p < 1.0:
+            keep = rng.random(m) < p
+            blk[~keep] = 0.0
+        out[off : off + m] = blk
+        off += m
+    return out
+
+
+def dense_from_upper(upper: np.ndarray, n: int, d: int, dtype=np.float64) -> np.ndarray:
+    """Symmetric nd x nd matrix with A_ii = I_d and the given upper blocks."""
+    U = np.zeros((n * d, n * d), dtype=dtype)
+    off = 0
+    for i in range(n - 1):
+        m = n - 1 - i
+        row = upper[off : off + m]  # (m, d, d): blocks (i, i+1..n-1)
+        U[i * d : (i + 1) * d, (i + 1) * d :] = np.transpose(row, (1, 0, 2)).reshape(d, m * d)
+        off += m
+    A = U + U.T
+    A[np.diag_indices(n * d)] += 1.0
+    return A
+
+
+@dataclass
+class Instance:
+    """One synthetic instance; ``upper`` is the canonical upper-block list."""
+
+    n: int
+    d: int
+    sigma: float
+    p: float
+    seed: int
+    Z: np.ndarray
+    upper: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    def dense(self, dtype=np.float64) -> np.ndarray:
+        return dense_from_upper(self.upper, self.n, self.d, dtype=dtype)
+
+    def Zstack(self) -> np.ndarray:
+        """Ground truth stacked as an nd x d matrix (Z_1; ...; Z_n)."""
+        return self.Z.reshape(self.n * self.d, self.d)
+
+
+def make_instance(n: int, d: int, sigma: float, seed: int, p: float = 1.0, dtype=np.float64) -> Instance:
+    if n < 2 or d < 1:
+        raise ValueError("need n >= 2 and d >= 1")
+    if not 0.0 < p <= 1.0:
+        raise ValueError("need 0 < p <= 1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Z = haar_orthogonal(rng, n, d)
+    up = upper_blocks(Z, sigma, rng, p=p, dtype=dtype)
+    return Instance(n=n, d=d, sigma=float(sigma), p=float(p), seed=int(seed), Z=Z, upper=up)
