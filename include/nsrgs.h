@@ -1,0 +1,164 @@
+/*
+ * nsrgs.h -- C ABI of the GB300 (sm_103a) NS-RGS library (libnsrgs.so).
+ *
+ * NS-RGS (Peng, Han, Chen, Huang, arXiv 2604.07372) recovers X = (X_1; ...; X_n),
+ * X_i in O(d), from a symmetric nd x nd matrix of pairwise measurements
+ * A = [A_ij] with A_ij ~ Z_i Z_j^T (problem statement §1.1; block model eq. (4),
+ * §2.2, where self-loops are excluded so A_ii = I_d).  Each iteration of
+ * Algorithm 2 forms, for every block i simultaneously from X^t,
+ *
+ *     G_i = sum_{j != i} (X_i - A_ij X_j)
+ *     F_i = X_i - eta * (G_i - X_i G_i^T X_i) / 2          (tangent projection, §2.2)
+ *     X_i^{t+1} = S_K(F_i),  S_{k+1} = S_k (3I - S_k^T S_k) / 2   (Algorithm 1, K steps)
+ *
+ * and starts from the spectral initialisation X^0 = sgn_n(Y), Y the top-d
+ * eigenvectors of A (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major.  X is the nd x d stack of d x d blocks, float32.
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every buffer:
+ *    the library allocates no device memory.  Scratch space ("workspace") is a
+ *    caller-provided device buffer of at least nsrgs_workspace_bytes(n, d)
+ *    bytes, 256-byte aligned; its contents between calls are unspecified.
+ *  - Every call is asynchronous on the caller's stream `st` (a cudaStream_t,
+ *    passed as void* so that this header needs no CUDA header), except where a
+ *    host output is written: those calls synchronise `st` before returning.
+ *  - Errors are returned as nsrgs_status; nothing is thrown across the ABI and
+ *    no kernel traps.  nsrgs_last_error() returns a thread-local message for
+ *    the last failing call on the calling thread.
+ *  - Argument checks: 2 <= n, 1 <= d <= 64, eta > 0 and finite, K >= 0,
+ *    T >= 0, non-null pointers, 16-byte aligned device pointers.
+ */
+#ifndef NSRGS_H
+#define NSRGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NSRGS_OK = 0,
+  NSRGS_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of contract */
+  NSRGS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  NSRGS_ERR_NOMEM = 3,         /* a caller buffer is smaller than the size query returned */
+  NSRGS_ERR_NONFINITE = 4,     /* an iterate became NaN or Inf */
+  NSRGS_ERR_NS_PRECOND = 5,    /* ||I - F_i^T F_i||_F >= 1 for some i (Lemma 2.1's precondition
+                                  checked conservatively); reported through nsrgs_info.flags */
+  NSRGS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  NSRGS_ERR_NOT_CONVERGED = 7, /* spectral initialisation hit max_iters above tol */
+  NSRGS_ERR_UNSUPPORTED = 8    /* valid arguments that this build does not implement */
+} nsrgs_status;
+
+/* Storage precision of the packed A.  Arithmetic is float32 in every case.
+ *  F32     : A stored as float32.
+ *  BF16    : A rounded to bfloat16 (round to nearest even).
+ *  FP8E4M3 : A stored as FP8 E4M3 (round to nearest, saturating at +-448) with one
+ *            float32 scale per block row i: s_i = max_{j>i} max|A_ij| / 448 and
+ *            A_ij ~ s_i * q_ij.  The per-block-row scale is this library's choice;
+ *            the paper does not discuss reduced precision.
+ *  DENSE_F32: the full nd x nd float32 matrix, both triangles, no symmetric reuse
+ *            (twice the bytes of F32).  Works for every d; it is the plain form the
+ *            symmetric layouts are measured against. */
+typedef enum {
+  NSRGS_F32 = 0,
+  NSRGS_BF16 = 1,
+  NSRGS_FP8E4M3 = 2,
+  NSRGS_DENSE_F32 = 3
+} nsrgs_storage;
+
+/* A packed measurement matrix.  `packed` is the device buffer written by
+ * nsrgs_pack_upper / nsrgs_pack_dense for the same (n, d, storage).  Only the
+ * strict block-upper triangle of A is kept (symmetric layouts): A_ji = A_ij^T
+ * and A_ii = I_d are implied, which is the model of eq. (4).  The struct lives
+ * in host memory; the library keeps no pointer to it after a call returns. */
+typedef struct nsrgs_A {
+  const void* packed;
+  int n;
+  int d;
+  int storage; /* nsrgs_storage */
+} nsrgs_A;
+
+/* Host-side report filled by nsrgs_solve when `info` is non-null. */
+typedef struct nsrgs_info {
+  int spectral_iters;      /* subspace iterations run by the spectral initialisation (0 if skipped) */
+  int iters;               /* NS-RGS iterations run (< T when tol > 0 stopped the loop early) */
+  double last_update_norm; /* ||X^{t+1} - X^t||_F / sqrt(nd) of the last iteration run */
+  double spectral_residual;/* ||A V - V H||_F / ||H||_F at the end of the spectral initialisation */
+  uint32_t flags;          /* bit 0: non-finite iterate; bit 1: NS precondition violated;
+                              bit 2: spectral initialisation not converged */
+} nsrgs_info;
+
+/* ---------------------------------------------------------------- sizes */
+
+/* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
+ * supported (symmetric layouts need d <= 4 in this build; DENSE_F32 any d <= 64). */
+size_t nsrgs_packed_bytes(int n, int d, int storage);
+
+/* Bytes of scratch workspace that every call below accepts for (n, d). */
+size_t nsrgs_workspace_bytes(int n, int d);
+
+/* ------------------------------------------------------------- packing */
+
+/* Build the packed A from the canonical upper-block list (device, float32):
+ * the n(n-1)/2 blocks (i, j), i < j, ordered by i then j, each d x d row-major
+ * (block (i, j) at index i*n - i*(i+1)/2 + (j - i - 1)).  `packed` (device,
+ * nsrgs_packed_bytes bytes) is fully overwritten.  Model: eq. (4), §2.2. */
+nsrgs_status nsrgs_pack_upper(const float* upper, int n, int d, int storage, void* packed, void* st);
+
+/* Same, from the dense symmetric nd x nd float32 matrix A (device, row-major).
+ * Only the strict block-upper triangle is read for symmetric layouts; the
+ * diagonal blocks are taken to be I_d as in eq. (4). */
+nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* packed, void* st);
+
+/* ---------------------------------------------------------- the method */
+
+/* Spectral initialisation (Algorithm 2): X0 (device, nd x d) = sgn_n(Y), Y an
+ * orthonormal basis of the top-d eigenvectors of A, found by block subspace
+ * iteration V <- orth(A V) with float64 d x d Gram/Cholesky steps, stopped when
+ * ||A V - V (V^T A V)||_F / ||V^T A V||_F <= tol or after max_iters passes.
+ * The per-block matrix sign is exact (float64 one-sided Jacobi SVD).  Returns
+ * NSRGS_ERR_NOT_CONVERGED (X0 still written) when max_iters ran out; with
+ * `residual` non-null the final residual is written there (host; synchronises). */
+nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, double tol,
+                                 double* residual, void* ws, size_t ws_bytes, void* st);
+
+/* One iteration of Algorithm 2 for all blocks: X_out = NS_K(X_in - eta P(G)).
+ * X_in and X_out (device, nd x d) must not overlap.  When `upd_norm` (device,
+ * one double) is non-null it receives ||X_out - X_in||_F / sqrt(nd). */
+nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, float* X_out,
+                        double* upd_norm, void* ws, size_t ws_bytes, void* st);
+
+/* Whole solve (Algorithm 2): when `init` != 0, spectral initialisation into X
+ * first (spectral_max_iters passes, tolerance 1e-6); otherwise X holds X^0 on
+ * entry.  Then T iterations with step eta and K Newton-Schulz steps; with
+ * tol > 0 the loop stops after the first iteration whose update norm
+ * ||X^{t+1} - X^t||_F / sqrt(nd) is below tol.  X (device, nd x d) receives the
+ * final iterate.  The iteration loop is replayed from a CUDA graph cached per
+ * (A, X, workspace, parameters).  `info` (host, nullable) is filled after a
+ * synchronisation of `st`.  Returns NSRGS_ERR_NONFINITE if an iterate became
+ * non-finite (checked only when info is non-null). */
+nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
+                         int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
+                         size_t ws_bytes, void* st);
+
+/* d_F(X, Y) = min_{Q in O(d)} ||X - Y Q||_F (§1.4) for two nd x d device stacks,
+ * with Q = sgn(Y^T X) from a float64 Jacobi SVD and float64 accumulation.
+ * `out` is a host double; the call synchronises `st`. */
+nsrgs_status nsrgs_dF(const float* X, const float* Y, int n, int d, double* out, void* ws,
+                      size_t ws_bytes, void* st);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* nsrgs_last_error(void);
+
+/* Library version string. */
+const char* nsrgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSRGS_H */

@@ -45,6 +45,7 @@ __all__ = [
     "tangent_projection",
     "euclidean_gradient",
     "nsrgs_iteration",
+    "nsrgs_rows_update",
     "spectral_init",
     "nsrgs",
     "objective",
@@ -133,6 +134,25 @@ def nsrgs_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, Ts:
     G = euclidean_gradient(A, X, n, d)
     F = Xb - mu * tangent_projection(Xb, G)
     return stack(newton_schulz(F, Ts))
+
+
+def nsrgs_rows_update(Arows: np.ndarray, X: np.ndarray, idx, n: int, d: int, mu: float, Ts: int) -> np.ndarray:
+    """Algorithm 2's loop body for the listed blocks i only, as (len(idx), d, d).
+
+    ``Arows[k]`` is the whole k-th listed block row of A (d x nd), so one block
+    update costs O(n d^2): this lets a sample of blocks of a very large instance
+    be checked one by one.  Same steps as ``nsrgs_iteration``.
+    """
+    Xs = np.asarray(X, dtype=np.float64)
+    Xb = blocks(Xs, d)
+    out = []
+    for k, i in enumerate(idx):
+        Ar = np.asarray(Arows[k], dtype=np.float64)
+        off = Ar @ Xs - Ar[:, i * d : (i + 1) * d] @ Xb[i]  # sum_{j != i} A_ij X_j
+        G = (n - 1) * Xb[i] - off
+        F = Xb[i] - mu * tangent_projection(Xb[i], G)
+        out.append(newton_schulz(F, Ts))
+    return np.stack(out)
 
 
 # ---------------------------------------- Algorithm 2: spectral start

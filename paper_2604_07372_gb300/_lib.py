@@ -1,0 +1,243 @@
+"""ctypes binding of libnsrgs.so with the ABI's names (include/nsrgs.h).
+
+Arguments are torch tensors on the current CUDA device; the binding passes
+their data pointers and ``torch.cuda.current_stream()`` to the C calls and
+turns non-zero status codes into ``NsrgsError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+F32, BF16, FP8E4M3, DENSE_F32 = 0, 1, 2, 3
+STORAGE = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "dense_f32": DENSE_F32}
+_STATUS = {
+    0: "NSRGS_OK",
+    1: "NSRGS_ERR_INVALID_ARG",
+    2: "NSRGS_ERR_CUDA",
+    3: "NSRGS_ERR_NOMEM",
+    4: "NSRGS_ERR_NONFINITE",
+    5: "NSRGS_ERR_NS_PRECOND",
+    6: "NSRGS_ERR_TIMEOUT",
+    7: "NSRGS_ERR_NOT_CONVERGED",
+    8: "NSRGS_ERR_UNSUPPORTED",
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libnsrgs.so")
+
+
+class NsrgsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _A(ctypes.Structure):
+    _fields_ = [("packed", ctypes.c_void_p), ("n", ctypes.c_int), ("d", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("spectral_iters", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("last_update_norm", ctypes.c_double),
+        ("spectral_residual", ctypes.c_double),
+        ("flags", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnsrgs.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i, sz, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float, ctypes.c_double
+    Ap = ctypes.POINTER(_A)
+    sig = {
+        "nsrgs_packed_bytes": (sz, [i, i, i]),
+        "nsrgs_workspace_bytes": (sz, [i, i]),
+        "nsrgs_pack_upper": (i, [vp, i, i, i, vp, vp]),
+        "nsrgs_pack_dense": (i, [vp, i, i, i, vp, vp]),
+        "nsrgs_spectral_init": (i, [Ap, vp, i, d, ctypes.POINTER(d), vp, sz, vp]),
+        "nsrgs_step": (i, [Ap, f, i, vp, vp, vp, vp, sz, vp]),
+        "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
+        "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
+        "nsrgs_last_error": (ctypes.c_char_p, []),
+        "nsrgs_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise NsrgsError(status, lib().nsrgs_last_error().decode())
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def nsrgs_version() -> str:
+    return lib().nsrgs_version().decode()
+
+
+def nsrgs_packed_bytes(n: int, d: int, storage: int) -> int:
+    return int(lib().nsrgs_packed_bytes(n, d, storage))
+
+
+def nsrgs_workspace_bytes(n: int, d: int) -> int:
+    return int(lib().nsrgs_workspace_bytes(n, d))
+
+
+def workspace(n: int, d: int, device=None) -> torch.Tensor:
+    """A device buffer of nsrgs_workspace_bytes(n, d) bytes (torch allocations are 512-byte aligned)."""
+    nb = nsrgs_workspace_bytes(n, d)
+    if nb == 0:
+        raise ValueError("unsupported (n, d)")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class PackedA:
+    """A packed measurement matrix: the device buffer plus its (n, d, storage)."""
+
+    buf: torch.Tensor
+    n: int
+    d: int
+    storage: int
+
+    def struct(self) -> _A:
+        return _A(self.buf.data_ptr(), self.n, self.d, self.storage)
+
+    @property
+    def nbytes(self) -> int:
+        return self.buf.numel()
+
+
+def _alloc_packed(n: int, d: int, storage: int, device) -> torch.Tensor:
+    nb = nsrgs_packed_bytes(n, d, storage)
+    if nb == 0:
+        raise NsrgsError(8, f"storage {storage} does not support (n={n}, d={d})")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def nsrgs_pack_upper(upper: torch.Tensor, n: int, d: int, storage: int = F32) -> PackedA:
+    """Pack the canonical upper-block list (n(n-1)/2, d, d) float32 on the device."""
+    assert upper.dtype == torch.float32 and upper.numel() == n * (n - 1) // 2 * d * d
+    buf = _alloc_packed(n, d, storage, upper.device)
+    _check(lib().nsrgs_pack_upper(_ptr(upper), n, d, storage, _ptr(buf), _stream()))
+    return PackedA(buf, n, d, storage)
+
+
+def nsrgs_pack_dense(A: torch.Tensor, n: int, d: int, storage: int = F32) -> PackedA:
+    """Pack a dense symmetric (nd, nd) float32 device matrix."""
+    assert A.dtype == torch.float32 and A.shape == (n * d, n * d)
+    buf = _alloc_packed(n, d, storage, A.device)
+    _check(lib().nsrgs_pack_dense(_ptr(A), n, d, storage, _ptr(buf), _stream()))
+    return PackedA(buf, n, d, storage)
+
+
+def _ws(A: PackedA, ws: torch.Tensor | None) -> torch.Tensor:
+    return ws if ws is not None else workspace(A.n, A.d, A.buf.device)
+
+
+def nsrgs_spectral_init(
+    A: PackedA, X0: torch.Tensor | None = None, max_iters: int = 50, tol: float = 1e-6, ws=None, strict=True
+):
+    """Spectral initialisation into X0 (nd, d) float32; returns (X0, residual)."""
+    if X0 is None:
+        X0 = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    res = ctypes.c_double(0.0)
+    a = A.struct()
+    st = lib().nsrgs_spectral_init(ctypes.byref(a), _ptr(X0), max_iters, tol, ctypes.byref(res), _ptr(w), w.numel(), _stream())
+    if st != 7 or strict:
+        _check(st)
+    return X0, res.value
+
+
+def nsrgs_step(A: PackedA, eta: float, K: int, X_in: torch.Tensor, X_out: torch.Tensor, upd_norm=None, ws=None):
+    """One NS-RGS iteration X_out = NS_K(X_in - eta P(G)); upd_norm: optional device float64 scalar."""
+    w = _ws(A, ws)
+    a = A.struct()
+    _check(
+        lib().nsrgs_step(
+            ctypes.byref(a), eta, K, _ptr(X_in), _ptr(X_out), _ptr(upd_norm), _ptr(w), w.numel(), _stream()
+        )
+    )
+    return X_out
+
+
+def nsrgs_solve(
+    A: PackedA,
+    eta: float,
+    T: int,
+    K: int,
+    tol: float = 0.0,
+    init: bool = True,
+    spectral_max_iters: int = 50,
+    X: torch.Tensor | None = None,
+    ws=None,
+    info: bool = True,
+):
+    """Spectral start (init=True) then T iterations; returns (X, Info or None)."""
+    if X is None:
+        X = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    a = A.struct()
+    inf = Info() if info else None
+    _check(
+        lib().nsrgs_solve(
+            ctypes.byref(a),
+            eta,
+            T,
+            K,
+            tol,
+            1 if init else 0,
+            spectral_max_iters,
+            _ptr(X),
+            ctypes.byref(inf) if inf is not None else None,
+            _ptr(w),
+            w.numel(),
+            _stream(),
+        )
+    )
+    return X, inf
+
+
+def nsrgs_dF(X: torch.Tensor, Y: torch.Tensor, n: int, d: int, ws=None) -> float:
+    """d_F(X, Y) = min over O(d) of ||X - Y Q||_F, float64 on the device."""
+    w = ws if ws is not None else workspace(n, d, X.device)
+    out = ctypes.c_double(0.0)
+    _check(lib().nsrgs_dF(_ptr(X), _ptr(Y), n, d, ctypes.byref(out), _ptr(w), w.numel(), _stream()))
+    return out.value

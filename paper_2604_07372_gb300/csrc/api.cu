@@ -1,0 +1,433 @@
+// C ABI of libnsrgs: argument checks, workspace layout, the spectral
+// initialisation sequence, one iteration, and the graph-replayed solve.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nsrgs {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+int num_sms() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+// ------------------------------------------------- kernels in other units
+nsrgs_status pack_upper_impl(const float*, int, int, int, void*, cudaStream_t);
+nsrgs_status pack_dense_impl(const float*, int, int, int, void*, cudaStream_t);
+long long dense_pitch(int n, int d);
+cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
+                         const int* skip, cudaStream_t st);
+cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float* Y, const int* skip,
+                         cudaStream_t st);
+cudaError_t stream_panel_prepare(const PanelGeom& g);
+
+int reduce_grid(long long rows);
+cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, double, Ctl*, double*, cudaStream_t);
+cudaError_t launch_spec_v0(float*, long long, int, cudaStream_t);
+cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
+                             cudaStream_t);
+cudaError_t launch_spec_update(const float*, const float*, float*, long long, int, const SpecScratch&, double, int,
+                               Ctl*, cudaStream_t);
+cudaError_t launch_polar_blocks(const float*, float*, int, int, cudaStream_t);
+cudaError_t launch_dF(const float*, const float*, long long, int, const SpecScratch&, Ctl*, cudaStream_t);
+cudaError_t launch_copy_out(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
+cudaError_t launch_select_copy(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
+
+constexpr int kMaxReduceGrid = 512;
+constexpr int kMaxSmallD = 8;
+
+// ---------------------------------------------------------- workspace map
+struct Workspace {
+  Ctl* ctl;
+  float* X[2];
+  float* Y;
+  float* W;
+  SpecScratch s;
+  size_t bytes;
+};
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+static Workspace map_workspace(void* base, int n, int d) {
+  Workspace w{};
+  size_t off = 0;
+  uint8_t* p = reinterpret_cast<uint8_t*>(base);
+  auto take = [&](size_t bytes) {
+    uint8_t* q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  const size_t vec = (size_t)xpad_rows(n, d) * d * sizeof(float);
+  w.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
+  w.X[0] = reinterpret_cast<float*>(take(vec));
+  w.X[1] = reinterpret_cast<float*>(take(vec));
+  w.Y = reinterpret_cast<float*>(take(vec));
+  w.W = reinterpret_cast<float*>(take(vec));
+  const size_t dd = (size_t)d * d * sizeof(double);
+  w.s.WW = reinterpret_cast<double*>(take(dd));
+  w.s.H = reinterpret_cast<double*>(take(dd));
+  w.s.Rinv = reinterpret_cast<double*>(take(dd));
+  w.s.M = reinterpret_cast<double*>(take(dd));
+  w.s.Q = reinterpret_cast<double*>(take(dd));
+  w.s.scal = reinterpret_cast<double*>(take(8 * sizeof(double)));
+  w.s.partials = reinterpret_cast<double*>(take((size_t)kMaxReduceGrid * 2 * dd));
+  w.bytes = off;
+  return w;
+}
+
+// ------------------------------------------------------------- checks
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static nsrgs_status check_nd(int n, int d) {
+  NSRGS_CHECK_ARG(n >= 2, "n must be >= 2");
+  NSRGS_CHECK_ARG(d >= 1 && d <= 64, "d must be in [1, 64]");
+  NSRGS_CHECK_ARG((long long)n * d <= (1LL << 30) / 64, "n*d too large");
+  return NSRGS_OK;
+}
+
+static nsrgs_status check_small_d(int d) {
+  if (d > kMaxSmallD) {
+    set_error("per-block kernels of this build cover d <= 8");
+    return NSRGS_ERR_UNSUPPORTED;
+  }
+  return NSRGS_OK;
+}
+
+static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
+  NSRGS_CHECK_ARG(A != nullptr, "A is null");
+  nsrgs_status s = check_nd(A->n, A->d);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(A->packed != nullptr && aligned16(A->packed), "A->packed must be a 16-byte aligned device pointer");
+  if (A->storage == NSRGS_DENSE_F32) return NSRGS_OK;
+  NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
+  if (!make_panel_geom(A->n, A->d, A->storage, g)) {
+    set_error("symmetric storage needs 1 <= d <= 4 in this build (use NSRGS_DENSE_F32)");
+    return NSRGS_ERR_UNSUPPORTED;
+  }
+  NSRGS_CUDA_TRY(stream_panel_prepare(*g));
+  return NSRGS_OK;
+}
+
+static nsrgs_status check_ws(void* ws, size_t ws_bytes, int n, int d) {
+  NSRGS_CHECK_ARG(ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & 255u) == 0,
+                  "workspace must be a 256-byte aligned device pointer");
+  const size_t need = map_workspace(nullptr, n, d).bytes;
+  if (ws_bytes < need) {
+    set_error("workspace smaller than nsrgs_workspace_bytes(n, d)");
+    return NSRGS_ERR_NOMEM;
+  }
+  return NSRGS_OK;
+}
+
+// ---------------------------------------------------------------- pieces
+static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
+                             const int* skip, cudaStream_t st) {
+  if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, Y, skip, st);
+  return stream_panel(A->packed, g, X, Y, ctl, skip, st);
+}
+
+// Resets the control block and zeroes Y and the padding of the X buffers.
+static cudaError_t reset_ws(const Workspace& w, int n, int d, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st);
+  if (e != cudaSuccess) return e;
+  const size_t vec = (size_t)xpad_rows(n, d) * d * sizeof(float);
+  const size_t body = (size_t)n * d * d * sizeof(float);
+  if ((e = cudaMemsetAsync(w.Y, 0, vec, st)) != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k)
+    if ((e = cudaMemsetAsync(reinterpret_cast<uint8_t*>(w.X[k]) + body, 0, vec - body, st)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Subspace iteration for the top-d eigenvectors of A = A_off + I, then the exact
+// blockwise sign: X0 = sgn_n(V) (Algorithm 2's spectral initialisation).
+// Leaves X0 in `out` (which may be w.X[0]); uses X[0], X[1], Y, W.
+static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, int max_iters,
+                                    double tol, float* out, cudaStream_t st) {
+  const int n = A->n, d = A->d;
+  const long long rows = (long long)n * d;
+  cudaError_t e;
+  if ((e = launch_spec_v0(w.X[0], rows, d, st)) != cudaSuccess) return e;
+  // orthonormalise the start: W = V0 (Y is zero), V1 = W chol(W^T W)^{-1}
+  if ((e = launch_spec_gram(w.X[0], w.Y, w.W, rows, d, 1.0f, w.s, w.ctl, st)) != cudaSuccess) return e;
+  if ((e = launch_spec_update(w.X[0], w.W, w.X[1], rows, d, w.s, tol, 0, w.ctl, st)) != cudaSuccess) return e;
+  for (int k = 0; k < max_iters; ++k) {
+    const float* V = w.X[(k + 1) & 1];
+    float* Vn = w.X[k & 1];
+    if ((e = stream_AX(A, g, V, w.Y, w.ctl, &w.ctl->spec_stop, st)) != cudaSuccess) return e;
+    if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, w.s, w.ctl, st)) != cudaSuccess) return e;
+    if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, 1, w.ctl, st)) != cudaSuccess) return e;
+  }
+  // final basis -> W, then X0 = sgn_n(W)
+  if ((e = launch_select_copy(w.X[0], w.X[1], w.W, rows * d, w.ctl, st)) != cudaSuccess) return e;
+  return launch_polar_blocks(w.W, out, n, d, st);
+}
+
+static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
+                                      int K, double tol, cudaStream_t st) {
+  cudaError_t e;
+  for (int t = 0; t < T; ++t) {
+    const float* Xt = w.X[t & 1];
+    float* Xn = w.X[(t + 1) & 1];
+    if ((e = stream_AX(A, g, Xt, w.Y, w.ctl, &w.ctl->stop, st)) != cudaSuccess) return e;
+    if ((e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------ graph cache
+struct GraphKey {
+  int dev;
+  const void* packed;
+  int n, d, storage;
+  float eta;
+  int T, K;
+  double tol;
+  int init, smax;
+  float* X;
+  void* ws;
+  bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+};
+
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;  // most recent last
+static cudaStream_t g_capture_stream[64] = {};
+
+static cudaError_t capture_stream(int dev, cudaStream_t* out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_capture_stream[dev]) {
+    cudaError_t e = cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = g_capture_stream[dev];
+  return cudaSuccess;
+}
+
+}  // namespace nsrgs
+
+using namespace nsrgs;
+
+extern "C" {
+
+const char* nsrgs_last_error(void) { return get_error(); }
+
+const char* nsrgs_version(void) { return "nsrgs-gb300 0.1 (sm_103a)"; }
+
+size_t nsrgs_packed_bytes(int n, int d, int storage) {
+  if (n < 2 || d < 1 || d > 64) return 0;
+  if (storage == NSRGS_DENSE_F32) return (size_t)n * d * (size_t)dense_pitch(n, d) * sizeof(float);
+  PanelGeom g;
+  if (!make_panel_geom(n, d, storage, &g)) return 0;
+  return (size_t)(g.header_bytes + g.panel_bytes);
+}
+
+size_t nsrgs_workspace_bytes(int n, int d) {
+  if (n < 2 || d < 1 || d > 64) return 0;
+  return map_workspace(nullptr, n, d).bytes;
+}
+
+nsrgs_status nsrgs_pack_upper(const float* upper, int n, int d, int storage, void* packed, void* st) {
+  nsrgs_status s = check_nd(n, d);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(upper && packed && aligned16(packed), "null or misaligned pointer");
+  return pack_upper_impl(upper, n, d, storage, packed, (cudaStream_t)st);
+}
+
+nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* packed, void* st) {
+  nsrgs_status s = check_nd(n, d);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(A && packed && aligned16(packed), "null or misaligned pointer");
+  return pack_dense_impl(A, n, d, storage, packed, (cudaStream_t)st);
+}
+
+nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, double tol, double* residual, void* ws,
+                                 size_t ws_bytes, void* stv) {
+  PanelGeom g{};
+  nsrgs_status s = check_A(A, &g);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_small_d(A->d)) != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(X0 && aligned16(X0), "X0 must be a 16-byte aligned device pointer");
+  NSRGS_CHECK_ARG(max_iters >= 1 && max_iters <= 10000, "max_iters must be in [1, 10000]");
+  NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
+  NSRGS_CUDA_TRY(enqueue_spectral(A, g, w, max_iters, tol, X0, st));
+  Ctl c{};
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (residual) *residual = c.spec_res;
+  if (c.flags & FLAG_TIMEOUT) {
+    set_error("a device-side wait timed out");
+    return NSRGS_ERR_TIMEOUT;
+  }
+  if (!c.spec_stop) {
+    set_error("spectral initialisation did not reach tol within max_iters");
+    return NSRGS_ERR_NOT_CONVERGED;
+  }
+  return NSRGS_OK;
+}
+
+nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, float* X_out, double* upd_norm,
+                        void* ws, size_t ws_bytes, void* stv) {
+  PanelGeom g{};
+  nsrgs_status s = check_A(A, &g);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_small_d(A->d)) != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
+  NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");
+  NSRGS_CHECK_ARG(X_in && X_out && aligned16(X_in) && aligned16(X_out), "X_in/X_out must be 16-byte aligned");
+  const size_t bytes = (size_t)A->n * A->d * A->d * sizeof(float);
+  const uint8_t* a0 = reinterpret_cast<const uint8_t*>(X_in);
+  const uint8_t* b0 = reinterpret_cast<const uint8_t*>(X_out);
+  NSRGS_CHECK_ARG(a0 + bytes <= b0 || b0 + bytes <= a0, "X_in and X_out overlap");
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X_in, bytes, cudaMemcpyDeviceToDevice, st));
+  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w.Y, w.ctl, &w.ctl->stop, st));
+  NSRGS_CUDA_TRY(launch_epilogue(w.X[0], w.Y, X_out, A->n, A->d, eta, K, 0.0, w.ctl, upd_norm, st));
+  return NSRGS_OK;
+}
+
+nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, int init, int spectral_max_iters,
+                         float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  PanelGeom g{};
+  nsrgs_status s = check_A(A, &g);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_small_d(A->d)) != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
+  NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");
+  NSRGS_CHECK_ARG(T >= 0 && T <= 100000, "T must be in [0, 100000]");
+  NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
+  NSRGS_CHECK_ARG(!init || (spectral_max_iters >= 1 && spectral_max_iters <= 10000),
+                  "spectral_max_iters must be in [1, 10000]");
+  NSRGS_CHECK_ARG(X && aligned16(X), "X must be a 16-byte aligned device pointer");
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, A->n, A->d);
+  const int n = A->n, d = A->d;
+  const size_t bytes = (size_t)n * d * d * sizeof(float);
+
+  int dev = 0;
+  NSRGS_CUDA_TRY(cudaGetDevice(&dev));
+  GraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.dev = dev;
+  key.packed = A->packed;
+  key.n = n;
+  key.d = d;
+  key.storage = A->storage;
+  key.eta = eta;
+  key.T = T;
+  key.K = K;
+  key.tol = tol;
+  key.init = init ? 1 : 0;
+  key.smax = init ? spectral_max_iters : 0;
+  key.X = X;
+  key.ws = ws;
+
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (size_t k = 0; k < g_graphs.size(); ++k)
+      if (g_graphs[k].key == key) {
+        exec = g_graphs[k].exec;
+        GraphEntry e = g_graphs[k];
+        g_graphs.erase(g_graphs.begin() + k);
+        g_graphs.push_back(e);
+        break;
+      }
+  }
+  if (!exec) {
+    cudaStream_t cs;
+    NSRGS_CUDA_TRY(capture_stream(dev, &cs));
+    // first launches configure kernel attributes outside of capture
+    NSRGS_CUDA_TRY(cudaStreamSynchronize(cs));
+    NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = reset_ws(w, n, d, cs);
+    if (e == cudaSuccess) {
+      if (init) e = enqueue_spectral(A, g, w, spectral_max_iters, 1e-6, w.X[0], cs);
+      else e = cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, cs);
+    }
+    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, cs);
+    if (e == cudaSuccess) e = launch_copy_out(w.X[0], w.X[1], X, (long long)n * d * d, w.ctl, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      set_error(std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      return NSRGS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      return NSRGS_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs.push_back(GraphEntry{key, exec});
+    if (g_graphs.size() > 8) {
+      cudaGraphExecDestroy(g_graphs.front().exec);
+      g_graphs.erase(g_graphs.begin());
+    }
+  }
+  NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  if (info) {
+    Ctl c{};
+    NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+    info->spectral_iters = c.spec_iters;
+    info->iters = c.iters_done;
+    info->last_update_norm = c.last_upd;
+    info->spectral_residual = c.spec_res;
+    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND)) | ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
+    if (c.flags & FLAG_TIMEOUT) {
+      set_error("a device-side wait timed out");
+      return NSRGS_ERR_TIMEOUT;
+    }
+    if (c.flags & FLAG_NONFINITE) {
+      set_error("an iterate became non-finite");
+      return NSRGS_ERR_NONFINITE;
+    }
+  }
+  return NSRGS_OK;
+}
+
+nsrgs_status nsrgs_dF(const float* X, const float* Y, int n, int d, double* out, void* ws, size_t ws_bytes,
+                      void* stv) {
+  nsrgs_status s = check_nd(n, d);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_small_d(d)) != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, n, d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(X && Y && out && aligned16(X) && aligned16(Y), "X, Y must be 16-byte aligned; out non-null");
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, n, d);
+  NSRGS_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
+  NSRGS_CUDA_TRY(launch_dF(X, Y, (long long)n * d, d, w.s, w.ctl, st));
+  double r = 0.0;
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(&r, w.s.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = sqrt(r);
+  return NSRGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Internal definitions shared by the libnsrgs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nsrgs.h"
+
+namespace nsrgs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define NSRGS_CUDA_TRY(expr)                                                      \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      ::nsrgs::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+      return NSRGS_ERR_CUDA;                                                      \
+    }                                                                             \
+  } while (0)
+
+#define NSRGS_CHECK_ARG(cond, msg)                                                \
+  do {                                                                            \
+    if (!(cond)) {                                                                \
+      ::nsrgs::set_error(msg);                                                    \
+      return NSRGS_ERR_INVALID_ARG;                                               \
+    }                                                                             \
+  } while (0)
+
+// ------------------------------------------------------- device control
+// One per workspace.  Written only by the library's kernels and by
+// cudaMemsetAsync at the start of a call.
+struct Ctl {
+  double upd_acc;          // sum ||X^{t+1}_i - X^t_i||^2 of the running epilogue
+  double last_upd;         // ||X^{t+1} - X^t||_F / sqrt(nd) of the last finished iteration
+  double spec_res;         // spectral-init relative residual of the last pass
+  double spec_res_acc;     // accumulator of the residual pass
+  unsigned int counter;    // CTAs finished in the running epilogue / reduction
+  int iters_done;          // NS-RGS iterations completed
+  int stop;                // set when the update norm fell below tol
+  unsigned int flags;      // FLAG_* bits
+  int spec_iters;          // subspace iterations run
+  int spec_stop;           // set when the subspace residual fell below tol
+  int pad[2];
+};
+
+enum : unsigned int {
+  FLAG_NONFINITE = 1u << 0,
+  FLAG_NS_PRECOND = 1u << 1,
+  FLAG_SPEC_NOT_CONVERGED = 1u << 2,
+  FLAG_TIMEOUT = 1u << 3,
+};
+
+// float64 scratch of the spectral initialisation and of d_F (all d x d unless noted).
+struct SpecScratch {
+  double* WW;        // W^T W
+  double* H;         // V^T W
+  double* Rinv;      // chol(W^T W)^{-1}
+  double* M;         // scratch / Y^T X
+  double* Q;         // sgn(Y^T X)
+  double* scal;      // [0] ||H||_F^2, [1] d_F^2, [2] residual accumulator
+  double* partials;  // per-CTA partial sums
+};
+
+// ----------------------------------------------------------- panel geometry
+// The symmetric read-once layout ("panel layout") of the packed strict
+// block-upper triangle.  Block rows are grouped into slabs of SB block rows
+// (RS = SB*D scalar rows).  Slab b starts at scalar column c0 = b*SB*D (its own
+// diagonal block column) and runs to column n*D, cut into steps of SC columns.
+// One step is the unit that one CTA stages in shared memory: up to NW warp
+// slices of WB bytes each; warp slice w covers slab rows [w*WROWS, (w+1)*WROWS).
+// Inside a warp slice the order is [row-in-thread rt][lane][LOADB bytes], lane =
+// rg*4 + cg, so that the 32 lanes of a warp read 32 consecutive LOADB-byte
+// vectors.  Steps that cross the slab's own diagonal square store only the
+// warp slices that hold a nonzero block (a prefix, since rows below the
+// staircase are zero); everything else in a stored slice that lies on or
+// below the block diagonal, or past column n*D / row n*D, is stored as zero.
+struct PanelGeom {
+  int n, D, storage;
+  int E;       // bytes per stored element
+  int RB;      // block rows per thread
+  int RT;      // scalar rows per thread (RB*D)
+  int LOADB;   // bytes one thread loads per row and step
+  int CPT;     // columns per thread (LOADB / E)
+  int SC;      // columns per step (4*CPT)
+  int NW;      // consumer warps per CTA
+  int SB;      // block rows per slab (NW*8*RB)
+  int RS;      // scalar rows per slab
+  int WROWS;   // rows per warp slice (8*RT)
+  int WB;      // bytes per warp slice (WROWS*SC*E)
+  int nslabs;
+  long long total_steps;
+  long long panel_bytes;   // bytes of all stored warp slices
+  long long header_bytes;  // bytes before the panels (tables, scales), 256-aligned
+  // header layout (byte offsets from the packed base)
+  long long off_step_start;  // int64[nslabs+1]: global index of each slab's first step
+  long long off_byte_off;    // int64[nslabs+1]: byte offset of each slab's panels
+  long long off_scale;       // float[n]: FP8 per-block-row scales (absent otherwise)
+};
+
+// Rows of X/Y padding needed by a layout (columns of the last step run past n*D).
+__host__ __device__ inline int xpad_rows(int n, int D) { return n * D + 64; }
+
+__host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Number of warp slices stored for step q of slab b.
+__host__ __device__ inline int panel_warps(const PanelGeom& g, int b, long long q) {
+  long long c_end = (long long)b * g.SB * g.D + (q + 1) * g.SC;  // exclusive global column
+  long long jmax = (c_end - 1) / g.D;                              // last block column touched
+  if (jmax > g.n - 1) jmax = g.n - 1;
+  long long rmax = (jmax - (long long)b * g.SB) * g.D;             // rows with a nonzero block
+  long long rlim = ((long long)g.n - (long long)b * g.SB) * g.D;
+  if (rmax > rlim) rmax = rlim;
+  if (rmax > g.RS) rmax = g.RS;
+  if (rmax < 1) rmax = 1;
+  int w = (int)((rmax + g.WROWS - 1) / g.WROWS);
+  return w < g.NW ? w : g.NW;
+}
+
+__host__ __device__ inline long long slab_steps(const PanelGeom& g, int b) {
+  long long L = (long long)g.n * g.D - (long long)b * g.SB * g.D;
+  return (L + g.SC - 1) / g.SC;
+}
+
+// Byte offset of step q inside slab b's panels.
+__host__ __device__ inline long long panel_step_offset(const PanelGeom& g, int b, long long q) {
+  long long off = 0;
+  long long t = 0;
+  for (; t < q; ++t) {
+    int w = panel_warps(g, b, t);
+    if (w == g.NW) break;
+    off += (long long)w * g.WB;
+  }
+  off += (q - t) * (long long)g.NW * g.WB;
+  return off;
+}
+
+bool make_panel_geom(int n, int d, int storage, PanelGeom* g);
+
+// -------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: false after `limit_ns` nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = globaltimer_ns();
+  while (true) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// 1-D bulk copy global -> shared through the TMA engine, completion on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4_f32(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far above any legitimate stage wait
+
+// ------------------------------------------------------ launch helpers
+int num_sms();
+cudaError_t occupancy(const void* kernel, int threads, size_t smem, int* blocks_per_sm);
+
+}  // namespace nsrgs

@@ -1,0 +1,223 @@
+// Packing of the measurement matrix A into the layouts the iteration streams.
+//
+// Model (§2.2, eq. (4)): A is symmetric with d x d blocks, A_ji = A_ij^T and
+// A_ii = I_d.  The symmetric layouts keep only the strict block-upper triangle
+// (each stored block feeds both Y_i += A_ij X_j and Y_j += A_ij^T X_i); the
+// dense layout keeps the whole matrix with its diagonal blocks zeroed, so the
+// plain product A_off X needs no special case.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nsrgs {
+
+static int storage_elem_bytes(int storage) {
+  switch (storage) {
+    case NSRGS_F32: return 4;
+    case NSRGS_BF16: return 2;
+    case NSRGS_FP8E4M3: return 1;
+    default: return 0;
+  }
+}
+
+bool make_panel_geom(int n, int d, int storage, PanelGeom* g) {
+  if (d < 1 || d > 4 || n < 2) return false;
+  int E = storage_elem_bytes(storage);
+  if (E == 0) return false;
+  PanelGeom G{};
+  G.n = n;
+  G.D = d;
+  G.storage = storage;
+  G.E = E;
+  static const int rb_for_d[5] = {0, 8, 4, 2, 1};
+  G.RB = rb_for_d[d];
+  G.RT = G.RB * d;
+  G.LOADB = (storage == NSRGS_FP8E4M3) ? 8 : 16;
+  G.CPT = G.LOADB / E;
+  G.SC = 4 * G.CPT;
+  G.NW = 8;
+  G.SB = G.NW * 8 * G.RB;
+  G.RS = G.SB * d;
+  G.WROWS = 8 * G.RT;
+  G.WB = G.WROWS * G.SC * E;
+  G.nslabs = (n + G.SB - 1) / G.SB;
+  long long steps = 0, bytes = 0;
+  for (int b = 0; b < G.nslabs; ++b) {
+    long long S = slab_steps(G, b);
+    steps += S;
+    bytes += panel_step_offset(G, b, S);
+  }
+  G.total_steps = steps;
+  G.panel_bytes = bytes;
+  G.off_step_start = 0;
+  G.off_byte_off = 8LL * (G.nslabs + 1);
+  G.off_scale = G.off_byte_off + 8LL * (G.nslabs + 1);
+  long long hdr = G.off_scale + (storage == NSRGS_FP8E4M3 ? 4LL * n : 0);
+  G.header_bytes = (hdr + 255) / 256 * 256;
+  *g = G;
+  return true;
+}
+
+static void panel_tables(const PanelGeom& G, std::vector<long long>& tab) {
+  tab.assign(2 * (G.nslabs + 1), 0);
+  long long s = 0, off = 0;
+  for (int b = 0; b <= G.nslabs; ++b) {
+    tab[b] = s;
+    tab[G.nslabs + 1 + b] = off;
+    if (b < G.nslabs) {
+      long long S = slab_steps(G, b);
+      s += S;
+      off += panel_step_offset(G, b, S);
+    }
+  }
+}
+
+// Source accessors: element (row, col) of A_off (zero on/below the block diagonal
+// and outside the matrix), read from the canonical upper-block list or a dense matrix.
+struct UpperSrc {
+  const float* p;
+  int n, d;
+  __device__ float operator()(long long row, long long col) const {
+    long long N = (long long)n * d;
+    if (row >= N || col >= N) return 0.f;
+    long long i = row / d, j = col / d;
+    if (j <= i) return 0.f;
+    long long a = row - i * d, bcol = col - j * d;
+    long long idx = i * n - i * (i + 1) / 2 + (j - i - 1);
+    return p[idx * d * d + a * d + bcol];
+  }
+};
+
+struct DenseSrc {
+  const float* p;
+  int n, d;
+  __device__ float operator()(long long row, long long col) const {
+    long long N = (long long)n * d;
+    if (row >= N || col >= N) return 0.f;
+    if (col / d <= row / d) return 0.f;
+    return p[row * N + col];
+  }
+};
+
+// FP8 scales: s_i = max_{j > i} max |A_ij| / 448 (1 when the row is all zero).
+template <class Src>
+__global__ void fp8_scale_kernel(Src src, int n, int d, float* scale) {
+  int i = blockIdx.x;
+  long long N = (long long)n * d;
+  float m = 0.f;
+  for (long long c = (long long)(i + 1) * d + threadIdx.x; c < N; c += blockDim.x)
+    for (int a = 0; a < d; ++a) m = fmaxf(m, fabsf(src((long long)i * d + a, c)));
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) scale[i] = (m > 0.f) ? m / 448.f : 1.f;
+  }
+}
+
+// One CTA per step: writes the step's stored warp slices.
+template <class Src>
+__global__ void pack_panel_kernel(Src src, PanelGeom g, uint8_t* packed) {
+  const long long* step_start = (const long long*)(packed + g.off_step_start);
+  const long long* byte_off = (const long long*)(packed + g.off_byte_off);
+  const float* scale = (const float*)(packed + g.off_scale);
+  long long gs = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  if (gs >= g.total_steps) return;
+  int lo = 0, hi = g.nslabs - 1;
+  while (lo < hi) {  // last slab whose first step <= gs
+    int mid = (lo + hi + 1) >> 1;
+    if (step_start[mid] <= gs) lo = mid; else hi = mid - 1;
+  }
+  int b = lo;
+  long long q = gs - step_start[b];
+  int W = panel_warps(g, b, q);
+  uint8_t* dst = packed + g.header_bytes + byte_off[b] + panel_step_offset(g, b, q);
+  long long elems = (long long)W * g.WB / g.E;
+  long long row0 = (long long)b * g.SB * g.D;
+  long long col0 = (long long)b * g.SB * g.D + q * g.SC;
+  int per_load = g.LOADB / g.E;
+  for (long long e = threadIdx.x; e < elems; e += blockDim.x) {
+    // e -> (w, rt, lane, cc) in the order [w][rt][lane][cc]
+    int cc = (int)(e % per_load);
+    long long t = e / per_load;
+    int lane = (int)(t % 32);
+    t /= 32;
+    int rt = (int)(t % g.RT);
+    int w = (int)(t / g.RT);
+    int rg = lane >> 2, cg = lane & 3;
+    long long r = (long long)w * g.WROWS + rg * g.RT + rt;
+    long long c = (long long)cg * g.CPT + cc;
+    float v = src(row0 + r, col0 + c);
+    if (g.storage == NSRGS_F32) {
+      ((float*)dst)[e] = v;
+    } else if (g.storage == NSRGS_BF16) {
+      ((__nv_bfloat16*)dst)[e] = __float2bfloat16_rn(v);
+    } else {
+      long long i = (row0 + r) / g.D;
+      float s = (i < g.n) ? scale[i] : 1.f;
+      ((__nv_fp8_storage_t*)dst)[e] = __nv_cvt_float_to_fp8(v / s, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
+}
+
+// Dense layout: row pitch = round_up(nd, 4) floats, diagonal blocks zeroed.
+template <class Src>
+__global__ void pack_dense_kernel(Src src, int n, int d, int pitch, float* out) {
+  long long N = (long long)n * d;
+  long long total = N * pitch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e / pitch, c = e % pitch;
+    float v = 0.f;
+    if (c < N) {
+      long long i = r / d, j = c / d;
+      if (i < j) v = src(r, c);
+      else if (i > j) v = src(c, r);  // A_ij = A_ji^T: element (r, c) = (c, r) of the upper part
+    }
+    out[e] = v;
+  }
+}
+
+long long dense_pitch(int n, int d) { return ((long long)n * d + 3) / 4 * 4; }
+
+template <class Src>
+static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, cudaStream_t st) {
+  if (storage == NSRGS_DENSE_F32) {
+    long long pitch = dense_pitch(n, d);
+    pack_dense_kernel<<<4 * num_sms(), 256, 0, st>>>(src, n, d, (int)pitch, (float*)packed);
+    NSRGS_CUDA_TRY(cudaGetLastError());
+    return NSRGS_OK;
+  }
+  PanelGeom g;
+  if (!make_panel_geom(n, d, storage, &g)) {
+    set_error("symmetric storage needs 1 <= d <= 4 in this build (use NSRGS_DENSE_F32)");
+    return NSRGS_ERR_UNSUPPORTED;
+  }
+  std::vector<long long> tab;
+  panel_tables(g, tab);
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(packed, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+  if (storage == NSRGS_FP8E4M3) {
+    fp8_scale_kernel<<<n, 256, 0, st>>>(src, n, d, (float*)((uint8_t*)packed + g.off_scale));
+    NSRGS_CUDA_TRY(cudaGetLastError());
+  }
+  long long S = g.total_steps;
+  dim3 grid((unsigned)std::min<long long>(S, 65535), (unsigned)((S + 65534) / 65535));
+  pack_panel_kernel<<<grid, 256, 0, st>>>(src, g, (uint8_t*)packed);
+  NSRGS_CUDA_TRY(cudaGetLastError());
+  // cudaMemcpyAsync from pageable memory has staged `tab` before returning.
+  return NSRGS_OK;
+}
+
+nsrgs_status pack_upper_impl(const float* upper, int n, int d, int storage, void* packed, cudaStream_t st) {
+  return pack_any(UpperSrc{upper, n, d}, n, d, storage, packed, st);
+}
+
+nsrgs_status pack_dense_impl(const float* A, int n, int d, int storage, void* packed, cudaStream_t st) {
+  return pack_any(DenseSrc{A, n, d}, n, d, storage, packed, st);
+}
+
+}  // namespace nsrgs

@@ -1,0 +1,589 @@
+// Per-block and reduction kernels around the A stream:
+//  * the iteration epilogue of Algorithm 2 (gradient, tangent projection, step,
+//    K Newton-Schulz steps, update norm, status flags);
+//  * the spectral initialisation's subspace-iteration steps (float64 Gram,
+//    Cholesky, V <- W R^{-1}, residual) and the exact blockwise matrix sign;
+//  * the distance d_F(X, Y) of §1.4.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nsrgs {
+
+constexpr int kDmaxSmall = 8;  // thread-per-block kernels are instantiated for d <= 8
+
+// ------------------------------------------------------ float64 d x d polar
+// One-sided Jacobi (Hestenes) SVD: rotate column pairs of U = M until they are
+// orthogonal, accumulating the rotations in V; then U Sigma = M V and
+// sgn(M) = (U Sigma) Sigma^{-1} V^T (§2.1's matrix sign, exact up to rounding).
+template <int D>
+__device__ void polar_fp64(const double (&M)[D][D], double (&Q)[D][D]) {
+  double U[D][D], V[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      U[r][c] = M[r][c];
+      V[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+#pragma unroll
+    for (int p = 0; p < D - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < D; ++q) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          al += U[r][p] * U[r][p];
+          be += U[r][q] * U[r][q];
+          ga += U[r][p] * U[r][q];
+        }
+        const double nrm = sqrt(al * be);
+        if (nrm == 0.0 || fabs(ga) <= 1e-17 * nrm) continue;
+        off = fmax(off, fabs(ga) / nrm);
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        const double s = c * t;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          const double up = U[r][p], uq = U[r][q];
+          U[r][p] = c * up - s * uq;
+          U[r][q] = s * up + c * uq;
+          const double vp = V[r][p], vq = V[r][q];
+          V[r][p] = c * vp - s * vq;
+          V[r][q] = s * vp + c * vq;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) s2 += U[r][c] * U[r][c];
+    const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) U[r][c] *= inv;
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += U[r][k] * V[c][k];
+      Q[r][c] = acc;
+    }
+}
+
+// ------------------------------------------------- block reductions (fp64)
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; result valid in thread 0.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Last-CTA election: returns true in every thread of the CTA that finishes last.
+__device__ bool last_block(unsigned int* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// ------------------------------------------------------ iteration epilogue
+// Thread i handles block i (Algorithm 2's loop body, §2.2 projection):
+//   G = (n-1) X_i - Y_i,  P = (G - X_i G^T X_i)/2,  F = X_i - eta P,
+//   S <- S (3I - S^T S)/2 applied K times (Algorithm 1), X_i^{t+1} = S.
+// It also zeroes Y_i for the next pass and adds ||X^{t+1}_i - X_i||^2 to the
+// iteration's update norm; the last CTA finishes the norm and the stop test.
+template <int D>
+__global__ void __launch_bounds__(128) epilogue_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                                       float* __restrict__ Xout, int n, float eta, int K,
+                                                       double tol, Ctl* ctl, double* upd_out) {
+  __shared__ double sh[32];
+  if (ctl->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double diff2 = 0.0;
+  unsigned int flags = 0;
+  if (i < n) {
+    float x[D][D], gm[D][D];
+    const float nm1 = (float)(n - 1);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const long long e = ((long long)i * D + r) * D + c;
+        x[r][c] = X[e];
+        gm[r][c] = nm1 * x[r][c] - Y[e];
+        Y[e] = 0.f;
+      }
+    // T = G^T X
+    float t[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc = fmaf(gm[k][r], x[k][c], acc);
+        t[r][c] = acc;
+      }
+    // F = X - eta/2 (G - X T)
+    float s[D][D];
+    const float h = 0.5f * eta;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float xt = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) xt = fmaf(x[r][k], t[k][c], xt);
+        s[r][c] = x[r][c] - h * (gm[r][c] - xt);
+      }
+    // Lemma 2.1 precondition, checked with ||I - F^T F||_F (>= the spectral norm)
+    {
+      float e2 = 0.f;
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float acc = (r == c) ? 1.f : 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc = fmaf(-s[k][r], s[k][c], acc);
+          e2 = fmaf(acc, acc, e2);
+        }
+      if (!(e2 < 1.f)) flags |= FLAG_NS_PRECOND;
+    }
+    for (int k = 0; k < K; ++k) {
+      float m[D][D];  // 3I - S^T S
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float acc = (r == c) ? 3.f : 0.f;
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc = fmaf(-s[l][r], s[l][c], acc);
+          m[r][c] = acc;
+        }
+      float sn[D][D];
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float acc = 0.f;
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc = fmaf(s[r][l], m[l][c], acc);
+          sn[r][c] = 0.5f * acc;
+        }
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) s[r][c] = sn[r][c];
+    }
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const float v = s[r][c];
+        finite = finite && isfinite(v);
+        Xout[((long long)i * D + r) * D + c] = v;
+        const double dd = (double)v - (double)x[r][c];
+        diff2 += dd * dd;
+      }
+    if (!finite) flags |= FLAG_NONFINITE;
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+  const double bs = block_sum(diff2, sh);
+  if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&ctl->upd_acc, 0.0);
+      const double un = sqrt(tot / ((double)n * D));
+      ctl->last_upd = un;
+      ctl->iters_done += 1;
+      if (tol > 0.0 && un < tol) ctl->stop = 1;
+      ctl->upd_acc = 0.0;
+      ctl->counter = 0u;
+      if (upd_out) *upd_out = un;
+    }
+  }
+}
+
+// ------------------------------------------- spectral init: subspace steps
+// Deterministic start V0 (any full-rank start works; entries uniform in (-1, 1)).
+__global__ void spec_v0_kernel(float* V, long long rows, int D) {
+  const long long total = rows * D;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    V[e] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+// Cholesky G = R^T R (R upper) and R^{-1}, float64, one thread, D <= 64.
+__device__ void chol_inv(const double* G, double* Rinv, int D, double* Rtmp) {
+  for (int j = 0; j < D; ++j) {
+    double s = G[j * D + j];
+    for (int k = 0; k < j; ++k) s -= Rtmp[k * D + j] * Rtmp[k * D + j];
+    const double rjj = sqrt(fmax(s, 1e-300));
+    Rtmp[j * D + j] = rjj;
+    for (int i = j + 1; i < D; ++i) {
+      double t = G[j * D + i];
+      for (int k = 0; k < j; ++k) t -= Rtmp[k * D + j] * Rtmp[k * D + i];
+      Rtmp[j * D + i] = t / rjj;
+    }
+    for (int i = 0; i < j; ++i) Rtmp[j * D + i] = 0.0;
+  }
+  // upper-triangular inverse by back substitution, column by column
+  for (int c = 0; c < D; ++c) {
+    for (int r = D - 1; r >= 0; --r) {
+      double t = (r == c) ? 1.0 : 0.0;
+      for (int k = r + 1; k < D; ++k) t -= Rtmp[r * D + k] * Rinv[k * D + c];
+      Rinv[r * D + c] = (r <= c) ? t / Rtmp[r * D + r] : 0.0;
+    }
+  }
+}
+
+// W = Y + shift V (written to W, Y zeroed), partial sums of W^T W and V^T W;
+// the last CTA reduces them, forms H = V^T W, ||H||_F^2 and Rinv = chol(W^T W)^{-1}.
+template <int D>
+__global__ void __launch_bounds__(256) spec_gram_kernel(const float* __restrict__ V, float* __restrict__ Y,
+                                                        float* __restrict__ W, long long rows, float shift,
+                                                        SpecScratch s, Ctl* ctl) {
+  __shared__ double sh[32];
+  if (ctl->spec_stop) return;
+  double ww[D][D], vw[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) ww[a][b] = vw[a][b] = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    float v[D], w[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = V[r * D + k];
+      w[k] = Y[r * D + k] + shift * v[k];
+      W[r * D + k] = w[k];
+      Y[r * D + k] = 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        ww[a][b] += (double)w[a] * (double)w[b];
+        vw[a][b] += (double)v[a] * (double)w[b];
+      }
+  }
+  double* part = s.partials + (long long)blockIdx.x * 2 * D * D;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double x1 = block_sum(ww[a][b], sh);
+      const double x2 = block_sum(vw[a][b], sh);
+      if (threadIdx.x == 0) {
+        part[a * D + b] = x1;
+        part[D * D + a * D + b] = x2;
+      }
+    }
+  if (last_block(&ctl->counter)) {
+    for (int o = threadIdx.x; o < 2 * D * D; o += blockDim.x) {
+      double acc = 0.0;
+      for (unsigned int bb = 0; bb < gridDim.x; ++bb) acc += s.partials[(long long)bb * 2 * D * D + o];
+      if (o < D * D) s.WW[o] = acc; else s.H[o - D * D] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double h2 = 0.0;
+      for (int o = 0; o < D * D; ++o) h2 += s.H[o] * s.H[o];
+      s.scal[0] = h2;
+      chol_inv(s.WW, s.Rinv, D, s.M);
+      s.scal[2] = 0.0;
+      ctl->counter = 0u;
+    }
+  }
+}
+
+// Vnew = W Rinv and the residual ||W - V H||_F; the last CTA finishes the
+// residual ||A V - V H||_F / ||H||_F and sets spec_stop when it is <= tol.
+template <int D>
+__global__ void __launch_bounds__(256) spec_update_kernel(const float* __restrict__ V, const float* __restrict__ W,
+                                                          float* __restrict__ Vnew, long long rows, SpecScratch s,
+                                                          double tol, int count_pass, Ctl* ctl) {
+  __shared__ double sh[32];
+  __shared__ double rinv[D * D], hh[D * D];
+  if (ctl->spec_stop) return;
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
+    rinv[o] = s.Rinv[o];
+    hh[o] = s.H[o];
+  }
+  __syncthreads();
+  double res = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double v[D], w[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = V[r * D + k];
+      w[k] = W[r * D + k];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double nv = 0.0, vh = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        nv += w[k] * rinv[k * D + c];
+        vh += v[k] * hh[k * D + c];
+      }
+      Vnew[r * D + c] = (float)nv;
+      const double e = w[c] - vh;
+      res += e * e;
+    }
+  }
+  const double bs = block_sum(res, sh);
+  if (threadIdx.x == 0) atomicAdd(&s.scal[2], bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&s.scal[2], 0.0);
+      ctl->counter = 0u;
+      if (count_pass) {
+        const double rel = sqrt(tot / fmax(s.scal[0], 1e-300));
+        ctl->spec_res = rel;
+        ctl->spec_iters += 1;
+        if (rel <= tol) ctl->spec_stop = 1;
+      }
+    }
+  }
+}
+
+// X0_i = sgn(V_i): exact float64 polar of each block (Algorithm 2's X^0).
+template <int D>
+__global__ void polar_blocks_kernel(const float* __restrict__ V, float* __restrict__ X0, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double M[D][D], Q[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) M[r][c] = V[((long long)i * D + r) * D + c];
+  polar_fp64<D>(M, Q);
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) X0[((long long)i * D + r) * D + c] = (float)Q[r][c];
+}
+
+// ------------------------------------------------------------- d_F(X, Y)
+// M = Y^T X (float64); the last CTA forms Q = sgn(M) (the minimiser of
+// ||X - Y Q||_F over O(d), proof of Lemma 7.4).
+template <int D>
+__global__ void __launch_bounds__(256) cross_gram_kernel(const float* __restrict__ X, const float* __restrict__ Yv,
+                                                         long long rows, SpecScratch s, Ctl* ctl) {
+  __shared__ double sh[32];
+  double m[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) m[a][b] = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double x[D], y[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      x[k] = X[r * D + k];
+      y[k] = Yv[r * D + k];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) m[a][b] += y[a] * x[b];
+  }
+  double* part = s.partials + (long long)blockIdx.x * D * D;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double v = block_sum(m[a][b], sh);
+      if (threadIdx.x == 0) part[a * D + b] = v;
+    }
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      double M[D][D], Q[D][D];
+      for (int o = 0; o < D * D; ++o) {
+        double acc = 0.0;
+        for (unsigned int bb = 0; bb < gridDim.x; ++bb) acc += s.partials[(long long)bb * D * D + o];
+        M[o / D][o % D] = acc;
+      }
+      polar_fp64<D>(M, Q);
+      for (int o = 0; o < D * D; ++o) s.Q[o] = Q[o / D][o % D];
+      s.scal[1] = 0.0;
+      ctl->counter = 0u;
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) dist_kernel(const float* __restrict__ X, const float* __restrict__ Yv,
+                                                   long long rows, SpecScratch s, Ctl* ctl) {
+  __shared__ double sh[32];
+  __shared__ double q[D * D];
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) q[o] = s.Q[o];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double y[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) y[k] = Yv[r * D + k];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double yq = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) yq += y[k] * q[k * D + c];
+      const double e = (double)X[r * D + c] - yq;
+      acc += e * e;
+    }
+  }
+  const double bs = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(&s.scal[1], bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) ctl->counter = 0u;
+  }
+}
+
+// Copy the final iterate (in ping-pong buffer iters_done & 1) to the caller's X.
+__global__ void copy_out_kernel(const float* __restrict__ X0, const float* __restrict__ X1, float* __restrict__ out,
+                                long long count, const Ctl* ctl) {
+  const float* src = (ctl->iters_done & 1) ? X1 : X0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = src[e];
+}
+
+// Spectral init's final basis sits in buffer spec_iters & 1 (the start V0 is in buffer 0
+// after the initial orthonormalisation, which writes buffer 1 ... see host sequence).
+__global__ void select_copy_kernel(const float* __restrict__ B0, const float* __restrict__ B1, float* __restrict__ out,
+                                   long long count, const Ctl* ctl) {
+  const float* src = (ctl->spec_iters & 1) ? B0 : B1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = src[e];
+}
+
+// ------------------------------------------------------------- dispatch
+#define NSRGS_DISPATCH_D(d, F)        \
+  switch (d) {                        \
+    case 1: F(1); break;              \
+    case 2: F(2); break;              \
+    case 3: F(3); break;              \
+    case 4: F(4); break;              \
+    case 5: F(5); break;              \
+    case 6: F(6); break;              \
+    case 7: F(7); break;              \
+    case 8: F(8); break;              \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_epilogue(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, double tol,
+                            Ctl* ctl, double* upd_out, cudaStream_t st) {
+  const int grid = (n + 127) / 128;
+#define L(DD) epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, eta, K, tol, ctl, upd_out)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+int reduce_grid(long long rows) {
+  long long g = (rows + 255) / 256;
+  const long long cap = 2LL * num_sms();
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_spec_v0(float* V, long long rows, int d, cudaStream_t st) {
+  spec_v0_kernel<<<reduce_grid(rows), 256, 0, st>>>(V, rows, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows, int d, float shift,
+                             const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+  const int grid = reduce_grid(rows);
+#define L(DD) spec_gram_kernel<DD><<<grid, 256, 0, st>>>(V, Y, W, rows, shift, s, ctl)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_update(const float* V, const float* W, float* Vnew, long long rows, int d,
+                               const SpecScratch& s, double tol, int count_pass, Ctl* ctl, cudaStream_t st) {
+  const int grid = reduce_grid(rows);
+#define L(DD) spec_update_kernel<DD><<<grid, 256, 0, st>>>(V, W, Vnew, rows, s, tol, count_pass, ctl)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polar_blocks(const float* V, float* X0, int n, int d, cudaStream_t st) {
+  const int grid = (n + 127) / 128;
+#define L(DD) polar_blocks_kernel<DD><<<grid, 128, 0, st>>>(V, X0, n)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dF(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
+                      cudaStream_t st) {
+  const int grid = reduce_grid(rows);
+#define L(DD) cross_gram_kernel<DD><<<grid, 256, 0, st>>>(X, Yv, rows, s, ctl)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+#define L(DD) dist_kernel<DD><<<grid, 256, 0, st>>>(X, Yv, rows, s, ctl)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(const float* X0, const float* X1, float* out, long long count, const Ctl* ctl,
+                            cudaStream_t st) {
+  copy_out_kernel<<<reduce_grid(count), 256, 0, st>>>(X0, X1, out, count, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_copy(const float* B0, const float* B1, float* out, long long count, const Ctl* ctl,
+                               cudaStream_t st) {
+  select_copy_kernel<<<reduce_grid(count), 256, 0, st>>>(B0, B1, out, count, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace nsrgs

@@ -1,0 +1,475 @@
+// The symmetric block product Y = A_off X of Algorithm 2's gradient
+// G_i = sum_{j != i} (X_i - A_ij X_j) = (n-1) X_i - Y_i, streaming A once.
+//
+// Each stored block A_ij (i < j) feeds both Y_i += A_ij X_j and
+// Y_j += A_ij^T X_i, so only the strict block-upper triangle is read.
+//
+// Kernel structure (persistent, one CTA per SM):
+//  * warp 8 (producer): lane 0 walks the CTA's contiguous range of steps and
+//    issues 1-D TMA bulk copies (cp.async.bulk) of each step's warp slices and
+//    of the X rows of the step's columns into a ring of shared-memory stages,
+//    completion tracked by mbarriers (expect_tx);
+//  * warps 0..7 (consumers): warp w owns slab rows [w*WROWS, (w+1)*WROWS); lane
+//    (rg, cg) owns RB whole block rows and CPT consecutive columns of each step.
+//    Row partials Y_i accumulate in registers across the whole walk through a
+//    slab (reduced over the 4 cg lanes and added to Y once per slab); column
+//    partials of a step are reduced over the 8 rg lanes with shuffles, then
+//    across the 8 warps through shared memory, and added to Y with one
+//    red.global.add.v4.f32 per 4 values.
+// Every wait is bounded (globaltimer); a timeout sets FLAG_TIMEOUT and ends the
+// kernel instead of hanging.
+#include "common.cuh"
+
+namespace nsrgs {
+
+template <int D, int RB, int ST>
+struct PCfg {
+  static constexpr int E = ST == NSRGS_F32 ? 4 : (ST == NSRGS_BF16 ? 2 : 1);
+  static constexpr int LOADB = ST == NSRGS_FP8E4M3 ? 8 : 16;
+  static constexpr int CPT = LOADB / E;
+  static constexpr int SC = 4 * CPT;
+  static constexpr int NW = 8;
+  static constexpr int RT = RB * D;
+  static constexpr int WROWS = 8 * RT;
+  static constexpr int WB = WROWS * SC * E;
+  static constexpr int STAGE_A = NW * WB;
+  static constexpr int STAGE_X = SC * D * 4;
+  static constexpr int STAGE_BYTES = (STAGE_A + STAGE_X + 127) / 128 * 128;
+  static constexpr int NSTAGE_RAW = (160 * 1024) / STAGE_BYTES;
+  static constexpr int NSTAGE = NSTAGE_RAW > 12 ? 12 : (NSTAGE_RAW < 2 ? 2 : NSTAGE_RAW);
+  static constexpr int NV = CPT * D;          // column-partial values per thread and step
+  static constexpr int COLVALS = SC * D;      // column-partial values per warp and step
+  static constexpr int THREADS = (NW + 1) * 32;
+  // shared memory: stages | colbuf[2][NW][COLVALS] | full[NSTAGE] empty[NSTAGE] colbar[2]
+  static constexpr int OFF_COLBUF = NSTAGE * STAGE_BYTES;
+  static constexpr int OFF_BARS = OFF_COLBUF + 2 * NW * COLVALS * 4;
+  static constexpr int SMEM = OFF_BARS + (2 * NSTAGE + 2) * 8;
+};
+
+// ---------------------------------------------------- column reduction
+// Transposed butterfly over the 8 rg lanes (lane bits 4, 3, 2).  While the
+// value count splits into whole columns the two partners exchange halves;
+// otherwise they do a full exchange (and only one of them remains the owner).
+template <int N, int D, int LVL>
+struct RedLevel {
+  static constexpr bool kSplit = (N % 2 == 0) && ((N / 2) % D == 0);
+  static constexpr int kNext = kSplit ? N / 2 : N;
+  static constexpr int kFinal = RedLevel<kNext, D, LVL + 1>::kFinal;
+  __device__ __forceinline__ static void run(float* v, int lane, int& col0, bool& owner) {
+    constexpr int mask = 16 >> LVL;
+    const bool bit = (lane & mask) != 0;
+    if constexpr (kSplit) {
+      constexpr int H = N / 2;
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        float send = bit ? v[k] : v[k + H];
+        float keep = bit ? v[k + H] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+      }
+      col0 += bit ? (H / D) : 0;
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], mask);
+      owner = owner && !bit;
+    }
+    RedLevel<kNext, D, LVL + 1>::run(v, lane, col0, owner);
+  }
+};
+
+template <int N, int D>
+struct RedLevel<N, D, 3> {
+  static constexpr int kFinal = N;
+  __device__ __forceinline__ static void run(float*, int, int&, bool&) {}
+};
+
+// ---------------------------------------------------- element unpacking
+template <int ST, int CPT>
+struct Unpack;
+
+template <int CPT>
+struct Unpack<NSRGS_F32, CPT> {
+  using V = float4;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+  }
+};
+
+template <int CPT>
+struct Unpack<NSRGS_BF16, CPT> {
+  using V = uint4;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+
+template <int CPT>
+struct Unpack<NSRGS_FP8E4M3, CPT> {
+  using V = uint2;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    const uint32_t w[2] = {x.x, x.y};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
+      __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+      float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+      float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+      o[4 * k + 0] = a.x; o[4 * k + 1] = a.y; o[4 * k + 2] = b.x; o[4 * k + 3] = b.y;
+    }
+  }
+};
+
+struct StreamArgs {
+  const uint8_t* packed;
+  const float* X;  // padded, xpad_rows(n, D) x D
+  float* Y;        // padded accumulator, zero on entry
+  Ctl* ctl;
+  const int* skip;  // the launch does nothing when *skip != 0 (set by earlier launches)
+  PanelGeom g;
+};
+
+__device__ __forceinline__ int find_slab(const long long* step_start, int nslabs, long long s) {
+  int lo = 0, hi = nslabs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (step_start[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D, int RB, int ST>
+__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kernel(StreamArgs a) {
+  using C = PCfg<D, RB, ST>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  if (*a.skip) return;  // written only by earlier launches: uniform
+  const PanelGeom& g = a.g;
+  const long long G = g.total_steps;
+  const long long g0 = G * blockIdx.x / gridDim.x;
+  const long long g1 = G * (blockIdx.x + 1) / gridDim.x;
+  if (g0 >= g1) return;
+
+  float* colbuf = reinterpret_cast<float*>(smem + C::OFF_COLBUF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BARS);
+  uint64_t* empty = full + C::NSTAGE;
+  uint64_t* colbar = empty + C::NSTAGE;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::NW);
+    }
+    mbar_init(&colbar[0], C::NW);
+    mbar_init(&colbar[1], C::NW);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const long long* step_start = reinterpret_cast<const long long*>(a.packed + g.off_step_start);
+  const long long* byte_off = reinterpret_cast<const long long*>(a.packed + g.off_byte_off);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (warp == C::NW) {
+    // ------------------------------------------------------------- producer
+    if (lane != 0) return;
+    const uint8_t* panels = a.packed + g.header_bytes;
+    int b = find_slab(step_start, g.nslabs, g0);
+    long long q = g0 - step_start[b];
+    long long Sb = step_start[b + 1] - step_start[b];
+    long long off = byte_off[b] + panel_step_offset(g, b, q);
+    long long it = 0;
+    bool ok = true;
+    for (long long s = g0; s < g1; ++s, ++it) {
+      const int st = (int)(it % C::NSTAGE);
+      const uint32_t ph = (uint32_t)((it / C::NSTAGE) & 1);
+      if (it >= C::NSTAGE && !mbar_wait_bounded(&empty[st], ph ^ 1u, kWaitLimitNs)) {
+        atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
+        ok = false;
+        break;
+      }
+      const int W = panel_warps(g, b, q);
+      const uint32_t bytesA = (uint32_t)W * C::WB;
+      uint8_t* stage = smem + st * C::STAGE_BYTES;
+      mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
+      bulk_g2s(stage, panels + off, bytesA, &full[st]);
+      const long long xcol = (long long)b * g.SB * D + q * C::SC;
+      bulk_g2s(stage + C::STAGE_A, a.X + xcol * D, C::STAGE_X, &full[st]);
+      off += bytesA;
+      if (++q == Sb) {
+        ++b;
+        q = 0;
+        if (b < g.nslabs) {
+          Sb = step_start[b + 1] - step_start[b];
+          off = byte_off[b];
+        }
+      }
+    }
+    // Do not leave while copies into this CTA's shared memory may be in flight.
+    const long long issued = it;
+    const long long first = issued > C::NSTAGE ? issued - C::NSTAGE : 0;
+    for (long long k = first; k < issued; ++k) {
+      const int st = (int)(k % C::NSTAGE);
+      const uint32_t ph = (uint32_t)((k / C::NSTAGE) & 1);
+      if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
+        atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
+        break;
+      }
+    }
+    (void)ok;
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumers
+  using Vec = typename Unpack<ST, C::CPT>::V;
+  const int rg = lane >> 2;
+  const int cg = lane & 3;
+  const int n = g.n;
+  const float* scale = (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(a.packed + g.off_scale) : nullptr;
+
+  int b = find_slab(step_start, g.nslabs, g0);
+  long long q = g0 - step_start[b];
+  long long Sb = step_start[b + 1] - step_start[b];
+
+  float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
+  float racc[C::RT][D];  // row partials
+  float rsc[RB];         // FP8 row scales
+  auto load_rows = [&](int bb) {
+#pragma unroll
+    for (int rb = 0; rb < RB; ++rb) {
+      const long long i = (long long)bb * g.SB + (warp * 8 + rg) * RB + rb;
+      float s = 1.f;
+      if (ST == NSRGS_FP8E4M3 && i < n) s = scale[i];
+      rsc[rb] = s;
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          xr[rb * D + r][k] = (i < n) ? a.X[(i * D + r) * D + k] * s : 0.f;
+          racc[rb * D + r][k] = 0.f;
+        }
+    }
+  };
+  auto flush_rows = [&](int bb) {
+#pragma unroll
+    for (int r = 0; r < C::RT; ++r)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float v = racc[r][k];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        racc[r][k] = v;
+      }
+    if (cg == 0) {
+#pragma unroll
+      for (int rb = 0; rb < RB; ++rb) {
+        const long long i = (long long)bb * g.SB + (warp * 8 + rg) * RB + rb;
+        if (i < n) {
+#pragma unroll
+          for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int k = 0; k < D; ++k) red_add_f32(a.Y + (i * D + r) * D + k, racc[rb * D + r][k] * rsc[rb]);
+        }
+      }
+    }
+  };
+
+  load_rows(b);
+  long long it = 0;
+  for (long long s = g0; s < g1; ++s, ++it) {
+    const int st = (int)(it % C::NSTAGE);
+    const uint32_t ph = (uint32_t)((it / C::NSTAGE) & 1);
+    const int W = panel_warps(g, b, q);
+    if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
+      atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
+      return;
+    }
+    const uint8_t* stage = smem + st * C::STAGE_BYTES;
+    float cacc[C::NV];
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v) cacc[v] = 0.f;
+    if (warp < W) {
+      Vec raw[C::RT];
+#pragma unroll
+      for (int rt = 0; rt < C::RT; ++rt)
+        raw[rt] = *reinterpret_cast<const Vec*>(stage + warp * C::WB + (rt * 32 + lane) * C::LOADB);
+      float xc[C::CPT][D];
+      const float* xs = reinterpret_cast<const float*>(stage + C::STAGE_A) + cg * C::CPT * D;
+#pragma unroll
+      for (int cc = 0; cc < C::CPT; ++cc)
+#pragma unroll
+        for (int k = 0; k < D; ++k) xc[cc][k] = xs[cc * D + k];
+#pragma unroll
+      for (int rt = 0; rt < C::RT; ++rt) {
+        float av[C::CPT];
+        Unpack<ST, C::CPT>::run(raw[rt], av);
+#pragma unroll
+        for (int cc = 0; cc < C::CPT; ++cc) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            racc[rt][k] = fmaf(av[cc], xc[cc][k], racc[rt][k]);
+            cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);  // stage fully read (values consumed above)
+
+    // column partials: 8 rg lanes -> owner lanes -> colbuf[it&1][warp]
+    int col0 = 0;
+    bool owner = true;
+    RedLevel<C::NV, D, 0>::run(cacc, lane, col0, owner);
+    constexpr int NF = RedLevel<C::NV, D, 0>::kFinal;
+    float* cb = colbuf + ((it & 1) * C::NW + warp) * C::COLVALS;
+    if (owner && warp < W) {
+#pragma unroll
+      for (int v = 0; v < NF; ++v) cb[(cg * C::CPT + col0) * D + v] = cacc[v];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&colbar[it & 1]);
+    if (!mbar_wait_bounded(&colbar[it & 1], (uint32_t)((it >> 1) & 1), kWaitLimitNs)) {
+      atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
+      return;
+    }
+    const int t = threadIdx.x;
+    if (t < C::COLVALS / 4) {
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* base = colbuf + (it & 1) * C::NW * C::COLVALS + 4 * t;
+      for (int w = 0; w < W; ++w) {
+        const float4 v = *reinterpret_cast<const float4*>(base + w * C::COLVALS);
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+      }
+      const long long xcol = (long long)b * g.SB * D + q * C::SC;
+      red_add_v4_f32(a.Y + xcol * D + 4 * t, sum.x, sum.y, sum.z, sum.w);
+    }
+
+    if (++q == Sb) {
+      flush_rows(b);
+      ++b;
+      q = 0;
+      if (b < g.nslabs) {
+        Sb = step_start[b + 1] - step_start[b];
+        if (s + 1 < g1) load_rows(b);
+      }
+    }
+  }
+  if (q != 0) flush_rows(b);
+}
+
+// ------------------------------------------------------------ dense form
+// Y = A_off X with A_off the full nd x nd matrix (diagonal blocks zero), no
+// symmetric reuse: the plain form the symmetric layouts are compared with, and
+// the path for block sizes the symmetric layouts do not cover.  CTA = 64 rows;
+// thread (row, quarter) sums over every 4th float4 of its row.
+template <int DMAX>
+__global__ void __launch_bounds__(256) dense_stream_kernel(const float* __restrict__ A, int N, int pitch, int D,
+                                                           const float* __restrict__ X, float* __restrict__ Y,
+                                                           const int* skip) {
+  if (*skip) return;
+  __shared__ __align__(16) float xs[64 * DMAX];
+  const int r = blockIdx.x * 64 + (threadIdx.x >> 2);
+  const int qtr = threadIdx.x & 3;
+  float acc[DMAX];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) acc[k] = 0.f;
+  for (int c0 = 0; c0 < N; c0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * D; e += 256) {
+      const int c = c0 + e / D;
+      xs[e] = (c < N) ? X[(long long)c0 * D + e] : 0.f;
+    }
+    __syncthreads();
+    if (r < N) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int cl = s * 16 + qtr * 4;
+        const int c = c0 + cl;
+        if (c < pitch) {
+          const float4 v = *reinterpret_cast<const float4*>(A + (long long)r * pitch + c);
+          const float av[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < DMAX; ++k)
+              if (k < D) acc[k] = fmaf(av[u], xs[(cl + u) * D + k], acc[k]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+    acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
+  }
+  if (r < N && qtr == 0)
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (k < D) Y[(long long)r * D + k] = acc[k];
+}
+
+// ------------------------------------------------------------- launchers
+// Opt-in to the kernel's dynamic shared memory; called outside of any stream
+// capture (cudaFuncSetAttribute is a device-wide setting, idempotent).
+template <int D, int RB, int ST>
+static cudaError_t prepare_panel() {
+  using C = PCfg<D, RB, ST>;
+  return cudaFuncSetAttribute(panel_stream_kernel<D, RB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+}
+
+template <int D, int RB, int ST>
+static cudaError_t launch_panel(const StreamArgs& a, cudaStream_t st) {
+  using C = PCfg<D, RB, ST>;
+  if (a.g.n < 0) return prepare_panel<D, RB, ST>();  // preparation request
+  panel_stream_kernel<D, RB, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int RB>
+static cudaError_t launch_panel_st(const StreamArgs& a, cudaStream_t st) {
+  switch (a.g.storage) {
+    case NSRGS_F32: return launch_panel<D, RB, NSRGS_F32>(a, st);
+    case NSRGS_BF16: return launch_panel<D, RB, NSRGS_BF16>(a, st);
+    case NSRGS_FP8E4M3: return launch_panel<D, RB, NSRGS_FP8E4M3>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
+                         const int* skip, cudaStream_t st) {
+  StreamArgs a{reinterpret_cast<const uint8_t*>(packed), X, Y, ctl, skip, g};
+  switch (g.D) {
+    case 1: return launch_panel_st<1, 8>(a, st);
+    case 2: return launch_panel_st<2, 4>(a, st);
+    case 3: return launch_panel_st<3, 2>(a, st);
+    case 4: return launch_panel_st<4, 1>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Sets the launch attributes of the stream kernel for this geometry.
+cudaError_t stream_panel_prepare(const PanelGeom& g) {
+  PanelGeom h = g;
+  h.n = -1;
+  return stream_panel(nullptr, h, nullptr, nullptr, nullptr, nullptr, 0);
+}
+
+long long dense_pitch(int n, int d);
+
+cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float* Y, const int* skip,
+                         cudaStream_t st) {
+  const int N = n * d;
+  const int pitch = (int)dense_pitch(n, d);
+  dim3 grid((N + 63) / 64);
+  const float* A = reinterpret_cast<const float*>(packed);
+  if (d <= 4) dense_stream_kernel<4><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  else if (d <= 8) dense_stream_kernel<8><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  else if (d <= 16) dense_stream_kernel<16><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  else if (d <= 32) dense_stream_kernel<32><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  else dense_stream_kernel<64><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace nsrgs

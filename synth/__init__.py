@@ -44,6 +44,7 @@ __all__ = [
     "num_upper_blocks",
     "upper_blocks",
     "dense_from_upper",
+    "block_row",
     "Instance",
     "make_instance",
 ]
@@ -111,6 +112,19 @@ def dense_from_upper(upper: np.ndarray, n: int, d: int, dtype=np.float64) -> np.
     A = U + U.T
     A[np.diag_indices(n * d)] += 1.0
     return A
+
+
+def block_row(upper: np.ndarray, n: int, d: int, i: int) -> np.ndarray:
+    """Block row i of A (d x nd, float64) read from the canonical upper-block list."""
+    R = np.zeros((d, n * d))
+    for j in range(n):
+        if j == i:
+            R[:, j * d : (j + 1) * d] = np.eye(d)
+        elif j > i:
+            R[:, j * d : (j + 1) * d] = upper[upper_index(i, j, n)]
+        else:
+            R[:, j * d : (j + 1) * d] = np.asarray(upper[upper_index(j, i, n)]).T
+    return R
 
 
 @dataclass

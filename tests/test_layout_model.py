@@ -1,0 +1,150 @@
+"""Host-side checks of the symmetric panel layout, without a GPU.
+
+A NumPy model of the layout arithmetic (slabs, steps, stored warp slices, the
+[w][rt][lane][cc] order) is checked for: (1) the library's nsrgs_packed_bytes
+(a host function of libnsrgs.so) agrees with it; (2) every element of the
+strict block-upper triangle lands in exactly one stored slot and every other
+slot holds a zero; (3) walking the steps as the stream kernel does (row
+partials into Y[rows], column partials into Y[cols]) rebuilds A_off X; (4) the
+reads and writes stay inside the buffers the library sizes (packed buffer,
+X/Y padded to n*d + 64 rows) and every bulk copy is 16-byte aligned.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+E_OF = {0: 4, 1: 2, 2: 1}
+RB_OF = {1: 8, 2: 4, 3: 2, 4: 1}
+
+
+class Geom:
+    def __init__(self, n, d, storage):
+        self.n, self.D, self.st = n, d, storage
+        self.E = E_OF[storage]
+        self.RB = RB_OF[d]
+        self.RT = self.RB * d
+        self.LOADB = 8 if storage == 2 else 16
+        self.CPT = self.LOADB // self.E
+        self.SC = 4 * self.CPT
+        self.NW = 8
+        self.SB = self.NW * 8 * self.RB
+        self.RS = self.SB * d
+        self.WROWS = 8 * self.RT
+        self.WB = self.WROWS * self.SC * self.E
+        self.nslabs = -(-n // self.SB)
+
+    def warps(self, b, q):
+        c_end = b * self.SB * self.D + (q + 1) * self.SC
+        jmax = min((c_end - 1) // self.D, self.n - 1)
+        rmax = (jmax - b * self.SB) * self.D
+        rmax = min(rmax, (self.n - b * self.SB) * self.D, self.RS)
+        rmax = max(rmax, 1)
+        return min(-(-rmax // self.WROWS), self.NW)
+
+    def steps(self, b):
+        L = self.n * self.D - b * self.SB * self.D
+        return -(-L // self.SC)
+
+    def header_bytes(self):
+        hdr = 16 * (self.nslabs + 1) + (4 * self.n if self.st == 2 else 0)
+        return -(-hdr // 256) * 256
+
+    def panel_bytes(self):
+        return sum(self.warps(b, q) * self.WB for b in range(self.nslabs) for q in range(self.steps(b)))
+
+
+def walk(g):
+    """Yield (b, q, W, byte offset) in storage order."""
+    off = 0
+    for b in range(g.nslabs):
+        for q in range(g.steps(b)):
+            W = g.warps(b, q)
+            yield b, q, W, off
+            off += W * g.WB
+
+
+def slot_coords(g, b, q, W):
+    """Global (row, col) of every stored element of step (b, q), in storage order."""
+    per = g.LOADB // g.E
+    e = np.arange(W * g.WB // g.E)
+    cc = e % per
+    t = e // per
+    lane = t % 32
+    t //= 32
+    rt = t % g.RT
+    w = t // g.RT
+    rg, cg = lane >> 2, lane & 3
+    r = w * g.WROWS + rg * g.RT + rt
+    c = cg * g.CPT + cc
+    return b * g.SB * g.D + r, b * g.SB * g.D + q * g.SC + c
+
+
+CASES = [(2, 1, 0), (2, 3, 0), (5, 2, 1), (130, 3, 0), (131, 3, 1), (200, 3, 2), (257, 4, 0), (300, 1, 2), (513, 2, 0), (140, 4, 2)]
+
+
+@pytest.mark.parametrize("n,d,storage", CASES)
+def test_layout_is_a_bijection_and_rebuilds_AX(n, d, storage):
+    g = Geom(n, d, storage)
+    N = n * d
+    inst = synth.make_instance(n, d, 0.7, seed=n + d)
+    A = inst.dense()
+    Aoff = A.copy()
+    for i in range(n):
+        Aoff[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
+    hit = np.zeros((N, N), dtype=np.int64)
+    X = np.random.default_rng(0).standard_normal((N + 64, d))
+    X[N:] = 0.0
+    Y = np.zeros((N + 64, d))
+    xpad = N + 64
+    total = 0
+    for b, q, W, off in walk(g):
+        rows, cols = slot_coords(g, b, q, W)
+        assert rows.max() < (b + 1) * g.SB * d
+        # bulk copies: 16-byte aligned sources and sizes; X rows inside the padding
+        assert (g.header_bytes() + off) % 16 == 0 and (W * g.WB) % 16 == 0
+        xcol = b * g.SB * d + q * g.SC
+        assert (xcol * d * 4) % 16 == 0 and xcol + g.SC <= xpad
+        inside = (rows < N) & (cols < N)
+        ib = np.where(inside, rows // d, 0)
+        jb = np.where(inside, cols // d, 0)
+        upper = inside & (jb > ib)
+        np.add.at(hit, (rows[upper], cols[upper]), 1)
+        vals = np.zeros(rows.shape)
+        vals[upper] = Aoff[rows[upper], cols[upper]]
+        # stream-kernel walk: row partials -> Y[rows < N], column partials -> Y[cols] (padded)
+        for rr, cc_, v in zip(rows, cols, vals):
+            if v != 0.0:
+                Y[rr] += v * X[cc_]
+                Y[cc_] += v * X[rr]
+        total += W * g.WB
+    assert total == g.panel_bytes()
+    iu = np.zeros((N, N), dtype=bool)
+    for i in range(n):
+        iu[i * d : (i + 1) * d, (i + 1) * d :] = True
+    assert np.all(hit[iu] == 1), "an upper element is missing or duplicated"
+    assert np.all(hit[~iu] == 0)
+    assert np.allclose(Y[:N], Aoff @ X[:N], atol=1e-10)
+    assert np.all(Y[N:] == 0.0)
+
+
+@pytest.mark.parametrize("n,d,storage", CASES + [(10000, 3, 0), (10000, 3, 1), (10000, 3, 2), (2000, 4, 0)])
+def test_packed_bytes_match_library(n, d, storage):
+    L = pytest.importorskip("paper_2604_07372_gb300._lib")
+    try:
+        lib = L.lib()
+    except RuntimeError:
+        pytest.skip("libnsrgs.so not built")
+    g = Geom(n, d, storage)
+    assert lib.nsrgs_packed_bytes(n, d, storage) == g.header_bytes() + g.panel_bytes()
+
+
+def test_stored_bytes_close_to_algorithmic():
+    """At n = 10^4, d = 3 the stored panels exceed the packed triangle by < 0.5%."""
+    n, d = 10000, 3
+    for st in (0, 1, 2):
+        g = Geom(n, d, st)
+        alg = n * (n - 1) // 2 * d * d * g.E
+        assert g.panel_bytes() / alg - 1.0 < 0.005

@@ -337,3 +337,15 @@ def test_table1_relative_error(sigma, p):
     X, info = O.nsrgs(A, n, d, 1.0 / (n * p), g["max_iter"], g["Ts"], rel_tol=g["rel_tol"])
     err = O.rel_err(X, inst.Zstack(), d)
     assert abs(err - pt["rel_err"]) / pt["rel_err"] < 0.02
+
+
+def test_rows_update_matches_full_iteration():
+    n, d = 40, 3
+    inst, A = _config1(n=n)
+    X0, _ = O.spectral_init(A, n, d)
+    full = O.blocks(O.nsrgs_iteration(A, X0, n, d, 1.0 / n, 2), d)
+    idx = [0, 7, 39]
+    rows = np.stack([synth.block_row(inst.upper, n, d, i) for i in idx])
+    assert np.allclose(rows[1], A[7 * d : 8 * d]), "block_row must read A's block row"
+    part = O.nsrgs_rows_update(rows, X0, idx, n, d, 1.0 / n, 2)
+    assert np.allclose(part, full[idx], atol=1e-14)
