@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""NS-RGS benchmark on GB300: iterations/s and A-stream HBM GB/s at n = 10^4, d = 3.
+
+One step = one whole solve through the C ABI (nsrgs_solve): spectral
+initialisation (subspace iteration on the same A-stream kernel, exact
+blockwise sign) followed by T = 100 NS-RGS iterations with K = 2
+Newton-Schulz steps and step size 1/n, on a synthetic instance of the paper's
+model (A_ij = Z_i Z_j^T + sigma W_ij, sigma = 0.3 sqrt(n)/(sqrt(d) + sqrt(ln n))),
+packed once as the float32 block-upper triangle (1.80 GB, far larger than L2).
+
+value   = NS-RGS iterations per second of the whole job (spectral start included),
+e2e     = the same with the packed A copied from pinned host memory and X copied
+          back every step,
+roofline= the A-stream kernel's algorithmic bytes per launch / its mean launch
+          time, from CUDA events captured around every launch in the timed region.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (one
+oracle iteration of the same workload per step).
+
+Multi-GPU: every rank runs its own replica (independent instances, no
+collective on the data path); value sums the iterations of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NS-RGS iters/s & HBM GB/s (n=10k,d=3); batched solves/s, p50/p99 latency"
+UNIT = "iters/s"
+SMAX = 30  # spectral-init pass cap (converges to 1e-6 in ~15 passes here; later passes exit at once)
+WORKLOAD = "single instance n=10000 d=3 (A 30000x30000), sigma=0.3*sqrt(n)/(sqrt(d)+sqrt(ln n)), spectral init + T=100 iterations, K=2, eta=1/n"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--d", type=int, default=3)
+    ap.add_argument("--T", type=int, default=100)
+    ap.add_argument("--K", type=int, default=2)
+    ap.add_argument("--c", type=float, default=0.3)
+    ap.add_argument("--seed", type=int, default=20260)
+    ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if one matches the current kernel."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_iterations(inst, args, iters: int, budget_s: float = 25.0):
+    """Time oracle iterations of the same workload on the host cores."""
+    import numpy as np
+
+    import oracle as O
+
+    n, d = inst.n, inst.d
+    need = 3 * (n * d) ** 2 * 8
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = need
+    if avail < need:
+        raise MemoryError(f"host has {avail / 1e9:.0f} GB free, the dense float64 A needs ~{need / 1e9:.0f} GB")
+    t0 = time.perf_counter()
+    A = inst.dense()  # float64 nd x nd (the oracle's input form)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    X = O.sgn_blocks(rng.standard_normal((n * d, d)), d)
+    times = []
+    for _ in range(iters):
+        t = time.perf_counter()
+        X = O.nsrgs_iteration(A, X, n, d, 1.0 / n, args.K)
+        times.append(time.perf_counter() - t)
+        if sum(times) > budget_s:
+            break
+    del A
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return times, build_s, cores
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+
+    n, d = args.n, args.d
+    inst = synth.make_instance(n, d, synth.sigma_rule(args.c, n, d), seed=args.seed, dtype=np.float32)
+    times, build_s, cores = cpu_oracle_iterations(inst, args, args.warmup + args.steps, budget_s=240.0)
+    timed = times[args.warmup :] or times[-1:]
+    sec = sum(timed)
+    value = len(timed) / sec
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": len(timed),
+        "warmup": min(args.warmup, len(times)),
+        "ms_per_step": 1e3 * sec / len(timed),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "step": "one FP64 oracle iteration (A @ X, projection, NS) of the full instance"},
+        "cpu_baseline": {
+            "value": value,
+            "unit": UNIT,
+            "cores": cores,
+            "kind": "oracle",
+            "sample": f"{len(timed)} oracle iterations of the n={n} d={d} instance (dense float64 A built in {build_s:.1f} s, not timed)",
+        },
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2604_07372_gb300 as P
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, d, T, K = args.n, args.d, args.T, args.K
+    eta = 1.0 / n
+    sigma = synth.sigma_rule(args.c, n, d)
+    t0 = time.perf_counter()
+    inst = synth.make_instance(n, d, sigma, seed=args.seed + rank, dtype=np.float32)
+    gen_s = time.perf_counter() - t0
+    up = torch.from_numpy(inst.upper).cuda()
+    Zt = torch.from_numpy(inst.Zstack().astype(np.float32)).cuda()
+    packs = {"f32": P.nsrgs_pack_upper(up, n, d, P.F32)}
+    if not args.no_extras:
+        packs["bf16"] = P.nsrgs_pack_upper(up, n, d, P.BF16)
+        packs["fp8"] = P.nsrgs_pack_upper(up, n, d, P.FP8E4M3)
+    del up
+    torch.cuda.synchronize()
+    ws = P.workspace(n, d)
+    X = torch.empty(n * d, d, dtype=torch.float32, device="cuda")
+    pa = packs["f32"]
+    alg_bytes = n * (n - 1) // 2 * d * d * 4  # packed block-upper triangle, float32
+
+    P.nsrgs_set_kernel_timing(True)
+    for _ in range(args.warmup):
+        P.nsrgs_solve(pa, eta, T, K, init=True, spectral_max_iters=SMAX, X=X, ws=ws, info=False)
+    _, info = P.nsrgs_solve(pa, eta, T, K, init=True, spectral_max_iters=SMAX, X=X, ws=ws, info=True)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        P.nsrgs_solve(pa, eta, T, K, init=True, spectral_max_iters=SMAX, X=X, ws=ws, info=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches, kern_ms, nodes = P.nsrgs_kernel_timing()
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    value = world * args.steps * T / sec
+    dF_Z = P.nsrgs_dF(X, Zt, n, d, ws=ws)
+
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    tag = f"panel_stream_f32_n{n}_d{d}"
+    roofline = {
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": peaks["hbm_gbs"],
+        "unit": "GB/s",
+        "frac": achieved / peaks["hbm_gbs"],
+        "traffic": profiled_traffic(tag),
+        "kernel": f"panel_stream_kernel<D={d},F32> (symmetric A-stream, one launch per iteration)",
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "mean_launch_ms": kern_ms,
+        "launches_timed": launches,
+        "peak_kind": f"of {peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else 'fallback'})",
+    }
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "storage": "float32 packed block-upper triangle (symmetric read-once)",
+            "l2": "inputs larger than L2 (packed A 1.80 GB vs 129 MB L2); no flush needed",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": nodes * args.steps,
+        "hbm_gbs": achieved,
+        "iteration_ms": kern_ms,
+        "final_dF_to_truth": dF_Z,
+        "spectral_iters": info.spectral_iters,
+        "spectral_residual": info.spectral_residual,
+        "instance_gen_s": gen_s,
+    }
+
+    if not args.no_extras and rank == 0:
+        extras = {}
+        # iteration loop alone (no spectral start), from the solve's own X^0
+        X0 = X.clone()
+        reps = 5
+        P.nsrgs_solve(pa, eta, T, K, init=False, X=X0.clone(), ws=ws, info=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Xl = X0.clone()
+        e0.record()
+        for _ in range(reps):
+            P.nsrgs_solve(pa, eta, T, K, init=False, X=Xl, ws=ws, info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        extras["iteration_loop_only_iters_per_s"] = reps * T / (e0.elapsed_time(e1) / 1e3)
+        # reduced-precision storage: same workload, final d_F(X, Z) relative to float32
+        for name in ("bf16", "fp8"):
+            pk = packs[name]
+            Xs = torch.empty_like(X)
+            for _ in range(2):
+                P.nsrgs_solve(pk, eta, T, K, init=True, spectral_max_iters=SMAX, X=Xs, ws=ws, info=False)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                P.nsrgs_solve(pk, eta, T, K, init=True, spectral_max_iters=SMAX, X=Xs, ws=ws, info=False)
+            e1.record()
+            torch.cuda.synchronize()
+            sec_s = e0.elapsed_time(e1) / 1e3
+            lc, kms, _ = P.nsrgs_kernel_timing()
+            ebytes = {"bf16": 2, "fp8": 1}[name]
+            ab = n * (n - 1) // 2 * d * d * ebytes
+            dfs = P.nsrgs_dF(Xs, Zt, n, d, ws=ws)
+            extras[name] = {
+                "iters_per_s": reps * T / sec_s,
+                "kernel_gbs": ab / (kms / 1e3) / 1e9,
+                "kernel_frac_of_measured_hbm": ab / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "mean_launch_ms": kms,
+                "final_dF_to_truth": dfs,
+                "dF_rel_change_vs_f32": (dfs - dF_Z) / dF_Z,
+            }
+        # e2e: packed A from pinned host memory every step, X back to the host
+        host = torch.empty(pa.nbytes, dtype=torch.uint8, pin_memory=True)
+        host.copy_(pa.buf)
+        Xh = torch.empty(X.shape, dtype=torch.float32, pin_memory=True)
+        steps_e2e = 5
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps_e2e):
+            pa.buf.copy_(host, non_blocking=True)
+            P.nsrgs_solve(pa, eta, T, K, init=True, spectral_max_iters=SMAX, X=X, ws=ws, info=False)
+            Xh.copy_(X, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t) / steps_e2e
+        line["e2e"] = {
+            "value": world * T / e2e_s,
+            "unit": UNIT,
+            "h2d_bytes_per_step": pa.nbytes,
+            "d2h_bytes_per_step": X.numel() * 4,
+            "note": "host -> device copy of the packed A, solve, device -> host copy of X, every step",
+        }
+        del host
+        # plain form: dense float32 A (both triangles), no symmetric reuse
+        try:
+            Ad = torch.from_numpy(inst.dense(dtype=np.float32)).cuda()
+            pd = P.nsrgs_pack_dense(Ad, n, d, P.DENSE_F32)
+            del Ad
+            Xd = torch.empty_like(X)
+            P.nsrgs_solve(pd, eta, T, K, init=True, spectral_max_iters=SMAX, X=Xd, ws=ws, info=False)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(2):
+                P.nsrgs_solve(pd, eta, T, K, init=True, spectral_max_iters=SMAX, X=Xd, ws=ws, info=False)
+            e1.record()
+            torch.cuda.synchronize()
+            lc, kms, _ = P.nsrgs_kernel_timing()
+            extras["plain_dense_f32"] = {
+                "iters_per_s": 2 * T / (e0.elapsed_time(e1) / 1e3),
+                "mean_launch_ms": kms,
+                "kernel_gbs": pd.nbytes / (kms / 1e3) / 1e9,
+                "final_dF_to_truth": P.nsrgs_dF(Xd, Zt, n, d, ws=ws),
+            }
+            del pd
+        except Exception as e:  # pragma: no cover - reported, not fatal
+            extras["plain_dense_f32"] = {"error": str(e)[:200]}
+        line["extras"] = extras
+        # CPU oracle on the host cores, bounded sample
+        try:
+            times, build_s, cores = cpu_oracle_iterations(inst, args, 3)
+            line["cpu_baseline"] = {
+                "value": len(times) / sum(times),
+                "unit": UNIT,
+                "cores": cores,
+                "kind": "oracle",
+                "sample": f"{len(times)} FP64 oracle iterations of the same n={n} d={d} instance (dense A built in {build_s:.1f} s, untimed)",
+            }
+        except MemoryError as e:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": str(e)}
+    if rank == 0:
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -151,7 +151,20 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
 nsrgs_status nsrgs_dF(const float* X, const float* Y, int n, int d, double* out, void* ws,
                       size_t ws_bytes, void* st);
 
-/* Thread-local text of the last error on this thread ("" if none). */
+/* ------------------------------------------------------ measurement aids */
+
+/* Per-launch timing of the A-stream kernel inside nsrgs_solve.  While enabled
+ * (enable != 0), graphs captured by nsrgs_solve carry a CUDA event before and
+ * after every A-stream launch of the iteration loop; nsrgs_kernel_timing then
+ * reports, for the most recent replay on the calling device, how many such
+ * launches ran and their mean duration in milliseconds (it synchronises the
+ * device).  The events cost a few microseconds per iteration; the setting is
+ * process-wide and part of the graph-cache key.  No counterpart in the paper:
+ * this exists to measure the kernel against its memory roofline. */
+nsrgs_status nsrgs_set_kernel_timing(int enable);
+nsrgs_status nsrgs_kernel_timing(int* launches, double* mean_ms, int* graph_kernel_nodes);
+
+/* Thread-local text of the last error on this thread ("" if none). *//* Thread-local text of the last error on this thread ("" if none). */
 const char* nsrgs_last_error(void);
 
 /* Library version string. */

@@ -26,5 +26,7 @@ from ._lib import (  # noqa: F401
     nsrgs_solve,
     nsrgs_dF,
     nsrgs_version,
+    nsrgs_set_kernel_timing,
+    nsrgs_kernel_timing,
     workspace,
 )

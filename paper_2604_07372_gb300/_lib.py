@@ -77,6 +77,8 @@ def lib() -> ctypes.CDLL:
         "nsrgs_step": (i, [Ap, f, i, vp, vp, vp, vp, sz, vp]),
         "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
+        "nsrgs_set_kernel_timing": (i, [i]),
+        "nsrgs_kernel_timing": (i, [ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(i)]),
         "nsrgs_last_error": (ctypes.c_char_p, []),
         "nsrgs_version": (ctypes.c_char_p, []),
     }
@@ -241,3 +243,16 @@ def nsrgs_dF(X: torch.Tensor, Y: torch.Tensor, n: int, d: int, ws=None) -> float
     out = ctypes.c_double(0.0)
     _check(lib().nsrgs_dF(_ptr(X), _ptr(Y), n, d, ctypes.byref(out), _ptr(w), w.numel(), _stream()))
     return out.value
+
+
+def nsrgs_set_kernel_timing(enable: bool) -> None:
+    _check(lib().nsrgs_set_kernel_timing(1 if enable else 0))
+
+
+def nsrgs_kernel_timing() -> tuple[int, float, int]:
+    """(A-stream launches timed in the last solve replay, their mean ms, kernel nodes of that graph)."""
+    n = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    k = ctypes.c_int(0)
+    _check(lib().nsrgs_kernel_timing(ctypes.byref(n), ctypes.byref(ms), ctypes.byref(k)))
+    return n.value, ms.value, k.value

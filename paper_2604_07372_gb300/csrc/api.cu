@@ -175,12 +175,14 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
 }
 
 static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
-                                      int K, double tol, cudaStream_t st) {
+                                      int K, double tol, cudaStream_t st, const cudaEvent_t* ev = nullptr) {
   cudaError_t e;
   for (int t = 0; t < T; ++t) {
     const float* Xt = w.X[t & 1];
     float* Xn = w.X[(t + 1) & 1];
+    if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = stream_AX(A, g, Xt, w.Y, w.ctl, &w.ctl->stop, st)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -197,12 +199,14 @@ struct GraphKey {
   int init, smax;
   float* X;
   void* ws;
+  int timing;
   bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
 struct GraphEntry {
   GraphKey key;
   cudaGraphExec_t exec;
+  int kernel_nodes;
 };
 
 static std::mutex g_graph_mu;
@@ -217,6 +221,39 @@ static cudaError_t capture_stream(int dev, cudaStream_t* out) {
   }
   *out = g_capture_stream[dev];
   return cudaSuccess;
+}
+
+// ----------------------------------------------------- kernel timing aid
+static int g_timing = 0;
+struct TimingState {
+  std::vector<cudaEvent_t> ev;  // 2 per iteration (before / after the A stream)
+  int last_T = 0;               // pairs recorded by the most recently launched timed graph
+  int last_nodes = 0;           // kernel nodes of the most recently launched graph
+};
+static TimingState g_timing_state[64];
+
+static cudaError_t ensure_events(int dev, int T) {
+  std::vector<cudaEvent_t>& ev = g_timing_state[dev].ev;
+  while ((int)ev.size() < 2 * T) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+  }
+  return cudaSuccess;
+}
+
+static int count_kernel_nodes(cudaGraph_t graph) {
+  size_t num = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &num) != cudaSuccess || num == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(num);
+  if (cudaGraphGetNodes(graph, nodes.data(), &num) != cudaSuccess) return 0;
+  int k = 0;
+  for (size_t i = 0; i < num; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
 }  // namespace nsrgs
@@ -344,13 +381,16 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
   key.smax = init ? spectral_max_iters : 0;
   key.X = X;
   key.ws = ws;
+  key.timing = g_timing;
 
   cudaGraphExec_t exec = nullptr;
+  int kernel_nodes = 0;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (size_t k = 0; k < g_graphs.size(); ++k)
       if (g_graphs[k].key == key) {
         exec = g_graphs[k].exec;
+        kernel_nodes = g_graphs[k].kernel_nodes;
         GraphEntry e = g_graphs[k];
         g_graphs.erase(g_graphs.begin() + k);
         g_graphs.push_back(e);
@@ -360,6 +400,8 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
   if (!exec) {
     cudaStream_t cs;
     NSRGS_CUDA_TRY(capture_stream(dev, &cs));
+    if (key.timing) NSRGS_CUDA_TRY(ensure_events(dev, T));
+    const cudaEvent_t* ev = key.timing ? g_timing_state[dev].ev.data() : nullptr;
     // first launches configure kernel attributes outside of capture
     NSRGS_CUDA_TRY(cudaStreamSynchronize(cs));
     NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -368,7 +410,7 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
       if (init) e = enqueue_spectral(A, g, w, spectral_max_iters, 1e-6, w.X[0], cs);
       else e = cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, cs);
     }
-    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, cs);
+    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, cs, ev);
     if (e == cudaSuccess) e = launch_copy_out(w.X[0], w.X[1], X, (long long)n * d * d, w.ctl, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -377,6 +419,7 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
       set_error(std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
       return NSRGS_ERR_CUDA;
     }
+    kernel_nodes = count_kernel_nodes(graph);
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -384,13 +427,15 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
       return NSRGS_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lk(g_graph_mu);
-    g_graphs.push_back(GraphEntry{key, exec});
+    g_graphs.push_back(GraphEntry{key, exec, kernel_nodes});
     if (g_graphs.size() > 8) {
       cudaGraphExecDestroy(g_graphs.front().exec);
       g_graphs.erase(g_graphs.begin());
     }
   }
   NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  g_timing_state[dev].last_T = key.timing ? T : 0;
+  g_timing_state[dev].last_nodes = kernel_nodes;
   if (info) {
     Ctl c{};
     NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -409,6 +454,29 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
       return NSRGS_ERR_NONFINITE;
     }
   }
+  return NSRGS_OK;
+}
+
+nsrgs_status nsrgs_set_kernel_timing(int enable) {
+  g_timing = enable ? 1 : 0;
+  return NSRGS_OK;
+}
+
+nsrgs_status nsrgs_kernel_timing(int* launches, double* mean_ms, int* graph_kernel_nodes) {
+  NSRGS_CHECK_ARG(launches && mean_ms, "launches and mean_ms must be non-null");
+  int dev = 0;
+  NSRGS_CUDA_TRY(cudaGetDevice(&dev));
+  NSRGS_CUDA_TRY(cudaDeviceSynchronize());
+  TimingState& ts = g_timing_state[dev];
+  double sum = 0.0;
+  for (int t = 0; t < ts.last_T; ++t) {
+    float ms = 0.f;
+    NSRGS_CUDA_TRY(cudaEventElapsedTime(&ms, ts.ev[2 * t], ts.ev[2 * t + 1]));
+    sum += ms;
+  }
+  *launches = ts.last_T;
+  *mean_ms = ts.last_T ? sum / ts.last_T : 0.0;
+  if (graph_kernel_nodes) *graph_kernel_nodes = ts.last_nodes;
   return NSRGS_OK;
 }
 
