@@ -68,11 +68,21 @@ def measured_peaks():
 
 def profiled_traffic(kernel_tag: str):
     """Per-launch DRAM bytes from a committed ncu summary, if one matches the current kernel."""
+    import hashlib
+
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
+    csrc = os.path.join(ROOT, "paper_2604_07372_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("stream.cu", "common.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m_src or m_src.group(1) != h.hexdigest()[:16]:
+        return None  # the counters were taken on another build of the kernel
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
 
