@@ -132,6 +132,27 @@ nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, dou
 nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, float* X_out,
                         double* upd_norm, void* ws, size_t ws_bytes, void* st);
 
+/* nsrgs_step without a workspace argument, for callers that cannot allocate
+ * device memory where they run: e.g. code inside a host program whose memory
+ * manager owns the device heap and gives out no scratch buffers, or a
+ * latency-critical loop that must not enter an allocator.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *  - Scratch lives in one fixed 8 MiB (8388608-byte) device array inside the
+ *    library; every GPU on which this is called keeps that memory until the
+ *    process exits.  (n, d) whose nsrgs_workspace_bytes exceeds 8 MiB is
+ *    rejected with NSRGS_ERR_INVALID_ARG (about n <= 170000 at d = 3,
+ *    n <= 30000 at d = 4).
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - No device memory is allocated or freed by any call.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and give wrong results; serialise them.
+ *    Each call clears the parts that must start at zero.
+ *  Arguments, layouts and results are those of nsrgs_step. */
+nsrgs_status nsrgs_step_static(const nsrgs_A* A, float eta, int K, const float* X_in, float* X_out,
+                               double* upd_norm, void* st);
+
 /* Whole solve (Algorithm 2): when `init` != 0, spectral initialisation into X
  * first (spectral_max_iters passes, tolerance 1e-6); otherwise X holds X^0 on
  * entry.  Then T iterations with step eta and K Newton-Schulz steps; with

@@ -256,3 +256,14 @@ def nsrgs_kernel_timing() -> tuple[int, float, int]:
     k = ctypes.c_int(0)
     _check(lib().nsrgs_kernel_timing(ctypes.byref(n), ctypes.byref(ms), ctypes.byref(k)))
     return n.value, ms.value, k.value
+
+
+def nsrgs_step_static(A: PackedA, eta: float, K: int, X_in: torch.Tensor, X_out: torch.Tensor, upd_norm=None):
+    """nsrgs_step with the library's fixed 8 MiB scratch array instead of a workspace (no allocation)."""
+    L = lib()
+    fn = L.nsrgs_step_static
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(_A), ctypes.c_float, ctypes.c_int] + [ctypes.c_void_p] * 4
+    a = A.struct()
+    _check(fn(ctypes.byref(a), eta, K, _ptr(X_in), _ptr(X_out), _ptr(upd_norm), _stream()))
+    return X_out
