@@ -4,18 +4,20 @@
 // Each stored block A_ij (i < j) feeds both Y_i += A_ij X_j and
 // Y_j += A_ij^T X_i, so only the strict block-upper triangle is read.
 //
-// Kernel structure (persistent, one CTA per SM):
-//  * warp 8 (producer): lane 0 walks the CTA's contiguous range of steps and
+// Kernel structure (persistent, one CTA per SM, 10 warps):
+//  * warp NW (producer): lane 0 walks the CTA's contiguous range of steps and
 //    issues 1-D TMA bulk copies (cp.async.bulk) of each step's warp slices and
 //    of the X rows of the step's columns into a ring of shared-memory stages,
 //    completion tracked by mbarriers (expect_tx);
-//  * warps 0..7 (consumers): warp w owns slab rows [w*WROWS, (w+1)*WROWS); lane
-//    (rg, cg) owns RB whole block rows and CPT consecutive columns of each step.
-//    Row partials Y_i accumulate in registers across the whole walk through a
-//    slab (reduced over the 4 cg lanes and added to Y once per slab); column
-//    partials of a step are reduced over the 8 rg lanes with shuffles, then
-//    across the 8 warps through shared memory, and added to Y with one
-//    red.global.add.v4.f32 per 4 values.
+//  * warps 0..NW-1 (consumers): warp w owns slab rows [w*WROWS, (w+1)*WROWS);
+//    lane (rg, cg) owns RB whole block rows and CPT consecutive columns of each
+//    step.  Row partials of Y accumulate in registers across the whole walk
+//    through a slab (reduced over the 4 cg lanes and added to Y once per slab).
+//    Column partials of a step are reduced over the 8 rg lanes with shuffles
+//    and written to a slot of a small shared-memory ring;
+//  * warp NW+1 (reducer): sums a slot over the consumer warps and adds the
+//    step's column partials to Y with red.global.add.v4.f32, then frees the
+//    slot.  Consumers never wait for each other, only for data and slots.
 // Every wait is bounded (globaltimer); a timeout sets FLAG_TIMEOUT and ends the
 // kernel instead of hanging.
 #include "common.cuh"
@@ -31,19 +33,23 @@ struct PCfg {
   static constexpr int NW = 8;
   static constexpr int RT = RB * D;
   static constexpr int WROWS = 8 * RT;
+  static constexpr int SB = NW * 8 * RB;
+  static constexpr int RS = SB * D;
   static constexpr int WB = WROWS * SC * E;
   static constexpr int STAGE_A = NW * WB;
   static constexpr int STAGE_X = SC * D * 4;
   static constexpr int STAGE_BYTES = (STAGE_A + STAGE_X + 127) / 128 * 128;
-  static constexpr int NSTAGE_RAW = (160 * 1024) / STAGE_BYTES;
+  static constexpr int NSTAGE_RAW = (168 * 1024) / STAGE_BYTES;
   static constexpr int NSTAGE = NSTAGE_RAW > 12 ? 12 : (NSTAGE_RAW < 2 ? 2 : NSTAGE_RAW);
-  static constexpr int NV = CPT * D;          // column-partial values per thread and step
-  static constexpr int COLVALS = SC * D;      // column-partial values per warp and step
-  static constexpr int THREADS = (NW + 1) * 32;
-  // shared memory: stages | colbuf[2][NW][COLVALS] | full[NSTAGE] empty[NSTAGE] colbar[2]
-  static constexpr int OFF_COLBUF = NSTAGE * STAGE_BYTES;
-  static constexpr int OFF_BARS = OFF_COLBUF + 2 * NW * COLVALS * 4;
-  static constexpr int SMEM = OFF_BARS + (2 * NSTAGE + 2) * 8;
+  static constexpr int NV = CPT * D;      // column-partial values per thread and step
+  static constexpr int COLVALS = SC * D;  // column-partial values per warp and step
+  static constexpr int RING = 4;          // column-partial slots between consumers and reducer
+  static constexpr int THREADS = (NW + 2) * 32;
+  // shared memory: stages | ring[RING][NW][COLVALS] | full[NSTAGE] empty[NSTAGE] cfull[RING] cempty[RING]
+  static constexpr int OFF_RING = NSTAGE * STAGE_BYTES;
+  static constexpr int OFF_BARS = OFF_RING + RING * NW * COLVALS * 4;
+  static constexpr int SMEM = OFF_BARS + (2 * NSTAGE + 2 * RING) * 8;
+  static_assert(COLVALS % 4 == 0 && COLVALS / 4 <= 32, "reducer lanes");
 };
 
 // ---------------------------------------------------- column reduction
@@ -141,6 +147,57 @@ __device__ __forceinline__ int find_slab(const long long* step_start, int nslabs
   return lo;
 }
 
+// Position in the CTA's walk over steps, in 32-bit arithmetic with the
+// geometry's compile-time constants.  W (stored warp slices of the step) is
+// nondecreasing along a slab, so it is recomputed only until it reaches NW.
+template <class C, int D>
+struct Walk {
+  int b, q, Sb, W;
+  bool ragged;
+
+  __device__ __forceinline__ int warps(int n) const {
+    const int c_end = b * C::SB * D + (q + 1) * C::SC;
+    int jmax = (c_end - 1) / D;
+    jmax = jmax < n - 1 ? jmax : n - 1;
+    int rmax = (jmax - b * C::SB) * D;
+    const int rlim = (n - b * C::SB) * D;
+    rmax = rmax < rlim ? rmax : rlim;
+    rmax = rmax < C::RS ? rmax : C::RS;
+    rmax = rmax > 1 ? rmax : 1;
+    const int w = (rmax + C::WROWS - 1) / C::WROWS;
+    return w < C::NW ? w : C::NW;
+  }
+  __device__ __forceinline__ void refresh(int n) {
+    if (ragged) {
+      W = warps(n);
+      ragged = W < C::NW;
+    }
+  }
+  __device__ __forceinline__ void start(const long long* step_start, int nslabs, long long g0, int n) {
+    b = find_slab(step_start, nslabs, g0);
+    q = (int)(g0 - step_start[b]);
+    Sb = (int)(step_start[b + 1] - step_start[b]);
+    ragged = true;
+    refresh(n);
+  }
+  // Returns true when the walk left slab b (the caller flushes it).
+  __device__ __forceinline__ bool advance(const long long* step_start, int nslabs, int n) {
+    if (++q < Sb) {
+      refresh(n);
+      return false;
+    }
+    ++b;
+    q = 0;
+    if (b < nslabs) {
+      Sb = (int)(step_start[b + 1] - step_start[b]);
+      ragged = true;
+      refresh(n);
+    }
+    return true;
+  }
+  __device__ __forceinline__ int xcol() const { return b * C::SB * D + q * C::SC; }
+};
+
 template <int D, int RB, int ST>
 __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kernel(StreamArgs a) {
   using C = PCfg<D, RB, ST>;
@@ -151,18 +208,23 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
   const long long g0 = G * blockIdx.x / gridDim.x;
   const long long g1 = G * (blockIdx.x + 1) / gridDim.x;
   if (g0 >= g1) return;
+  const int nsteps = (int)(g1 - g0);
+  const int n = g.n;
 
-  float* colbuf = reinterpret_cast<float*>(smem + C::OFF_COLBUF);
+  float* ring = reinterpret_cast<float*>(smem + C::OFF_RING);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BARS);
   uint64_t* empty = full + C::NSTAGE;
-  uint64_t* colbar = empty + C::NSTAGE;
+  uint64_t* cfull = empty + C::NSTAGE;
+  uint64_t* cempty = cfull + C::RING;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::NSTAGE; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], C::NW);
     }
-    mbar_init(&colbar[0], C::NW);
-    mbar_init(&colbar[1], C::NW);
+    for (int s = 0; s < C::RING; ++s) {
+      mbar_init(&cfull[s], C::NW);
+      mbar_init(&cempty[s], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -171,54 +233,75 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
   const long long* byte_off = reinterpret_cast<const long long*>(a.packed + g.off_byte_off);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  Walk<C, D> wk;
 
   if (warp == C::NW) {
     // ------------------------------------------------------------- producer
     if (lane != 0) return;
     const uint8_t* panels = a.packed + g.header_bytes;
-    int b = find_slab(step_start, g.nslabs, g0);
-    long long q = g0 - step_start[b];
-    long long Sb = step_start[b + 1] - step_start[b];
-    long long off = byte_off[b] + panel_step_offset(g, b, q);
-    long long it = 0;
-    bool ok = true;
-    for (long long s = g0; s < g1; ++s, ++it) {
-      const int st = (int)(it % C::NSTAGE);
-      const uint32_t ph = (uint32_t)((it / C::NSTAGE) & 1);
-      if (it >= C::NSTAGE && !mbar_wait_bounded(&empty[st], ph ^ 1u, kWaitLimitNs)) {
+    wk.start(step_start, g.nslabs, g0, n);
+    long long off = byte_off[wk.b] + panel_step_offset(g, wk.b, wk.q);
+    int st = 0;
+    uint32_t ph = 0;
+    int issued = 0;
+    for (; issued < nsteps; ++issued) {
+      if (issued >= C::NSTAGE && !mbar_wait_bounded(&empty[st], ph ^ 1u, kWaitLimitNs)) {
         atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
-        ok = false;
         break;
       }
-      const int W = panel_warps(g, b, q);
-      const uint32_t bytesA = (uint32_t)W * C::WB;
+      const uint32_t bytesA = (uint32_t)wk.W * C::WB;
       uint8_t* stage = smem + st * C::STAGE_BYTES;
       mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
       bulk_g2s(stage, panels + off, bytesA, &full[st]);
-      const long long xcol = (long long)b * g.SB * D + q * C::SC;
-      bulk_g2s(stage + C::STAGE_A, a.X + xcol * D, C::STAGE_X, &full[st]);
+      bulk_g2s(stage + C::STAGE_A, a.X + (long long)wk.xcol() * D, C::STAGE_X, &full[st]);
       off += bytesA;
-      if (++q == Sb) {
-        ++b;
-        q = 0;
-        if (b < g.nslabs) {
-          Sb = step_start[b + 1] - step_start[b];
-          off = byte_off[b];
-        }
+      if (wk.advance(step_start, g.nslabs, n) && wk.b < g.nslabs) off = byte_off[wk.b];
+      if (++st == C::NSTAGE) {
+        st = 0;
+        ph ^= 1u;
       }
     }
     // Do not leave while copies into this CTA's shared memory may be in flight.
-    const long long issued = it;
-    const long long first = issued > C::NSTAGE ? issued - C::NSTAGE : 0;
-    for (long long k = first; k < issued; ++k) {
-      const int st = (int)(k % C::NSTAGE);
-      const uint32_t ph = (uint32_t)((k / C::NSTAGE) & 1);
-      if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
+    const int first = issued > C::NSTAGE ? issued - C::NSTAGE : 0;
+    for (int k = first; k < issued; ++k) {
+      if (!mbar_wait_bounded(&full[k % C::NSTAGE], (uint32_t)((k / C::NSTAGE) & 1), kWaitLimitNs)) {
         atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
         break;
       }
     }
-    (void)ok;
+    return;
+  }
+
+  if (warp == C::NW + 1) {
+    // -------------------------------------------------------------- reducer
+    wk.start(step_start, g.nslabs, g0, n);
+    int slot = 0;
+    uint32_t ph = 0;
+    for (int it = 0; it < nsteps; ++it) {
+      if (!mbar_wait_bounded(&cfull[slot], ph, kWaitLimitNs)) {
+        atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
+        return;
+      }
+      if (lane < C::COLVALS / 4) {
+        const float* base = ring + slot * C::NW * C::COLVALS + 4 * lane;
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < C::NW; ++w) {
+          if (w < wk.W) {
+            const float4 v = *reinterpret_cast<const float4*>(base + w * C::COLVALS);
+            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+          }
+        }
+        red_add_v4_f32(a.Y + (long long)wk.xcol() * D + 4 * lane, sum.x, sum.y, sum.z, sum.w);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cempty[slot]);
+      wk.advance(step_start, g.nslabs, n);
+      if (++slot == C::RING) {
+        slot = 0;
+        ph ^= 1u;
+      }
+    }
     return;
   }
 
@@ -226,12 +309,7 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
   using Vec = typename Unpack<ST, C::CPT>::V;
   const int rg = lane >> 2;
   const int cg = lane & 3;
-  const int n = g.n;
   const float* scale = (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(a.packed + g.off_scale) : nullptr;
-
-  int b = find_slab(step_start, g.nslabs, g0);
-  long long q = g0 - step_start[b];
-  long long Sb = step_start[b + 1] - step_start[b];
 
   float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
   float racc[C::RT][D];  // row partials
@@ -239,7 +317,7 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
   auto load_rows = [&](int bb) {
 #pragma unroll
     for (int rb = 0; rb < RB; ++rb) {
-      const long long i = (long long)bb * g.SB + (warp * 8 + rg) * RB + rb;
+      const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
       float s = 1.f;
       if (ST == NSRGS_FP8E4M3 && i < n) s = scale[i];
       rsc[rb] = s;
@@ -247,7 +325,7 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
       for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          xr[rb * D + r][k] = (i < n) ? a.X[(i * D + r) * D + k] * s : 0.f;
+          xr[rb * D + r][k] = (i < n) ? a.X[((long long)i * D + r) * D + k] * s : 0.f;
           racc[rb * D + r][k] = 0.f;
         }
     }
@@ -265,23 +343,23 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
     if (cg == 0) {
 #pragma unroll
       for (int rb = 0; rb < RB; ++rb) {
-        const long long i = (long long)bb * g.SB + (warp * 8 + rg) * RB + rb;
+        const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
         if (i < n) {
 #pragma unroll
           for (int r = 0; r < D; ++r)
 #pragma unroll
-            for (int k = 0; k < D; ++k) red_add_f32(a.Y + (i * D + r) * D + k, racc[rb * D + r][k] * rsc[rb]);
+            for (int k = 0; k < D; ++k)
+              red_add_f32(a.Y + ((long long)i * D + r) * D + k, racc[rb * D + r][k] * rsc[rb]);
         }
       }
     }
   };
 
-  load_rows(b);
-  long long it = 0;
-  for (long long s = g0; s < g1; ++s, ++it) {
-    const int st = (int)(it % C::NSTAGE);
-    const uint32_t ph = (uint32_t)((it / C::NSTAGE) & 1);
-    const int W = panel_warps(g, b, q);
+  wk.start(step_start, g.nslabs, g0, n);
+  load_rows(wk.b);
+  int st = 0, slot = 0;
+  uint32_t ph = 0, cph = 0;
+  for (int it = 0; it < nsteps; ++it) {
     if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
       atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
       return;
@@ -290,17 +368,19 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
     float cacc[C::NV];
 #pragma unroll
     for (int v = 0; v < C::NV; ++v) cacc[v] = 0.f;
-    if (warp < W) {
+    const bool active = warp < wk.W;
+    if (active) {
       Vec raw[C::RT];
 #pragma unroll
       for (int rt = 0; rt < C::RT; ++rt)
         raw[rt] = *reinterpret_cast<const Vec*>(stage + warp * C::WB + (rt * 32 + lane) * C::LOADB);
-      float xc[C::CPT][D];
-      const float* xs = reinterpret_cast<const float*>(stage + C::STAGE_A) + cg * C::CPT * D;
+      float xc[C::CPT * D];
+      const float4* xs = reinterpret_cast<const float4*>(stage + C::STAGE_A) + cg * (C::CPT * D / 4);
 #pragma unroll
-      for (int cc = 0; cc < C::CPT; ++cc)
-#pragma unroll
-        for (int k = 0; k < D; ++k) xc[cc][k] = xs[cc * D + k];
+      for (int v = 0; v < C::CPT * D / 4; ++v) {
+        const float4 t = xs[v];
+        xc[4 * v + 0] = t.x; xc[4 * v + 1] = t.y; xc[4 * v + 2] = t.z; xc[4 * v + 3] = t.w;
+      }
 #pragma unroll
       for (int rt = 0; rt < C::RT; ++rt) {
         float av[C::CPT];
@@ -309,7 +389,7 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
         for (int cc = 0; cc < C::CPT; ++cc) {
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            racc[rt][k] = fmaf(av[cc], xc[cc][k], racc[rt][k]);
+            racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
             cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
           }
         }
@@ -317,46 +397,39 @@ __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kern
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);  // stage fully read (values consumed above)
+    if (++st == C::NSTAGE) {
+      st = 0;
+      ph ^= 1u;
+    }
 
-    // column partials: 8 rg lanes -> owner lanes -> colbuf[it&1][warp]
+    // column partials: 8 rg lanes -> owner lanes -> ring slot -> reducer warp
     int col0 = 0;
     bool owner = true;
     RedLevel<C::NV, D, 0>::run(cacc, lane, col0, owner);
     constexpr int NF = RedLevel<C::NV, D, 0>::kFinal;
-    float* cb = colbuf + ((it & 1) * C::NW + warp) * C::COLVALS;
-    if (owner && warp < W) {
-#pragma unroll
-      for (int v = 0; v < NF; ++v) cb[(cg * C::CPT + col0) * D + v] = cacc[v];
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&colbar[it & 1]);
-    if (!mbar_wait_bounded(&colbar[it & 1], (uint32_t)((it >> 1) & 1), kWaitLimitNs)) {
+    if (it >= C::RING && !mbar_wait_bounded(&cempty[slot], cph ^ 1u, kWaitLimitNs)) {
       atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
       return;
     }
-    const int t = threadIdx.x;
-    if (t < C::COLVALS / 4) {
-      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float* base = colbuf + (it & 1) * C::NW * C::COLVALS + 4 * t;
-      for (int w = 0; w < W; ++w) {
-        const float4 v = *reinterpret_cast<const float4*>(base + w * C::COLVALS);
-        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-      }
-      const long long xcol = (long long)b * g.SB * D + q * C::SC;
-      red_add_v4_f32(a.Y + xcol * D + 4 * t, sum.x, sum.y, sum.z, sum.w);
+    if (owner && active) {
+      float* cb = ring + (slot * C::NW + warp) * C::COLVALS + (cg * C::CPT + col0) * D;
+#pragma unroll
+      for (int v = 0; v < NF; ++v) cb[v] = cacc[v];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&cfull[slot]);
+    if (++slot == C::RING) {
+      slot = 0;
+      cph ^= 1u;
     }
 
-    if (++q == Sb) {
-      flush_rows(b);
-      ++b;
-      q = 0;
-      if (b < g.nslabs) {
-        Sb = step_start[b + 1] - step_start[b];
-        if (s + 1 < g1) load_rows(b);
-      }
+    const int bcur = wk.b;
+    if (wk.advance(step_start, g.nslabs, n)) {
+      flush_rows(bcur);
+      if (it + 1 < nsteps) load_rows(wk.b);
     }
   }
-  if (q != 0) flush_rows(b);
+  if (wk.q != 0) flush_rows(wk.b);
 }
 
 // ------------------------------------------------------------ dense form

@@ -141,6 +141,18 @@ def test_packed_bytes_match_library(n, d, storage):
     assert lib.nsrgs_packed_bytes(n, d, storage) == g.header_bytes() + g.panel_bytes()
 
 
+@pytest.mark.parametrize("n,d,storage", CASES + [(10000, 3, 0), (10000, 3, 1), (2000, 4, 2)])
+def test_warp_count_nondecreasing_along_a_slab(n, d, storage):
+    """The stream kernel recomputes a step's stored warp count only until it reaches NW."""
+    g = Geom(n, d, storage)
+    for b in range(g.nslabs):
+        ws = [g.warps(b, q) for q in range(g.steps(b))]
+        assert all(x <= y for x, y in zip(ws, ws[1:]))
+        assert ws[0] >= 1
+        # 32-bit step arithmetic in the kernel: the last column index fits easily
+        assert b * g.SB * d + g.steps(b) * g.SC < 2**31
+
+
 def test_stored_bytes_close_to_algorithmic():
     """At n = 10^4, d = 3 the stored panels exceed the packed triangle by < 0.5%."""
     n, d = 10000, 3
