@@ -166,6 +166,36 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
                          int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
                          size_t ws_bytes, void* st);
 
+/* ------------------------------------------------------- batched form */
+
+/* One independent instance of a batch. */
+typedef struct nsrgs_batch_item {
+  const void* packed; /* device, written by nsrgs_pack_* for (n, d, storage) of the batch call */
+  int n;
+  float eta;          /* step size of this instance */
+  float* X;           /* device, nd x d: result; also X^0 on entry when init == 0 */
+} nsrgs_batch_item;
+
+/* Workspace bytes for a batch of `count` instances with sizes n[0..count-1] and
+ * block size d (1 <= d <= 4); 0 when unsupported. */
+size_t nsrgs_batch_workspace_bytes(const int* n, int count, int d);
+
+/* Solves `count` independent instances (Algorithm 2 for each: spectral start
+ * when init != 0, then T iterations with K Newton-Schulz steps; tol > 0 stops
+ * an instance after its first iteration with update norm below tol) in one
+ * CUDA-graph replay.  All instances share d (1..4) and the symmetric storage
+ * (F32, BF16 or FP8E4M3); n and eta differ per instance.  Each tick is one
+ * A-stream launch over every active instance (their steps concatenated and
+ * split evenly over the SMs) plus one launch with a CTA per instance for the
+ * d x d work, so instances in their spectral phase and in their iterations
+ * advance in the same tick.  `info` (host array of count, nullable) is filled
+ * after a synchronisation.  items, the packed buffers and X must stay valid
+ * until the work on `st` completes.  The batched form has no counterpart in
+ * the paper beyond running Algorithm 2 on each instance. */
+nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int count, int d, int storage, int T, int K,
+                               double tol, int init, int spectral_max_iters, nsrgs_info* info, void* ws,
+                               size_t ws_bytes, void* st);
+
 /* d_F(X, Y) = min_{Q in O(d)} ||X - Y Q||_F (§1.4) for two nd x d device stacks,
  * with Q = sgn(Y^T X) from a float64 Jacobi SVD and float64 accumulation.
  * `out` is a host double; the call synchronises `st`. */

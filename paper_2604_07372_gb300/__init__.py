@@ -29,4 +29,7 @@ from ._lib import (  # noqa: F401
     nsrgs_set_kernel_timing,
     nsrgs_kernel_timing,
     workspace,
+    nsrgs_batch_workspace_bytes,
+    nsrgs_batch_solve,
+    nsrgs_step_static,
 )

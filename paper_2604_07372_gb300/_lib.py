@@ -267,3 +267,53 @@ def nsrgs_step_static(A: PackedA, eta: float, K: int, X_in: torch.Tensor, X_out:
     a = A.struct()
     _check(fn(ctypes.byref(a), eta, K, _ptr(X_in), _ptr(X_out), _ptr(upd_norm), _stream()))
     return X_out
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("packed", ctypes.c_void_p), ("n", ctypes.c_int), ("eta", ctypes.c_float), ("X", ctypes.c_void_p)]
+
+
+def nsrgs_batch_workspace_bytes(ns, d: int) -> int:
+    arr = (ctypes.c_int * len(ns))(*ns)
+    fn = lib().nsrgs_batch_workspace_bytes
+    fn.restype = ctypes.c_size_t
+    fn.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int]
+    return int(fn(arr, len(ns), d))
+
+
+def nsrgs_batch_solve(
+    packs,
+    etas,
+    T: int,
+    K: int,
+    tol: float = 0.0,
+    init: bool = True,
+    spectral_max_iters: int = 50,
+    Xs=None,
+    ws=None,
+    info: bool = True,
+):
+    """Solve a batch of PackedA instances (same d and storage); returns (list of X, list of Info or None)."""
+    count = len(packs)
+    d = packs[0].d
+    storage = packs[0].storage
+    if Xs is None:
+        Xs = [torch.empty(p.n * d, d, dtype=torch.float32, device=p.buf.device) for p in packs]
+    items = (_BatchItem * count)()
+    for k, (p, e, X) in enumerate(zip(packs, etas, Xs)):
+        assert p.d == d and p.storage == storage
+        items[k] = _BatchItem(p.buf.data_ptr(), p.n, float(e), X.data_ptr())
+    if ws is None:
+        ws = torch.empty(nsrgs_batch_workspace_bytes([p.n for p in packs], d), dtype=torch.uint8, device=packs[0].buf.device)
+    infos = (Info * count)() if info else None
+    fn = lib().nsrgs_batch_solve
+    fn.restype = ctypes.c_int
+    fn.argtypes = [
+        ctypes.POINTER(_BatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Info), ctypes.c_void_p, ctypes.c_size_t,
+        ctypes.c_void_p,
+    ]
+    _check(
+        fn(items, count, d, storage, T, K, tol, 1 if init else 0, spectral_max_iters, infos, _ptr(ws), ws.numel(), _stream())
+    )
+    return Xs, (list(infos) if infos is not None else None)

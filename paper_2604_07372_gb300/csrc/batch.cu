@@ -1,0 +1,565 @@
+// Batched and served forms: many independent instances of different sizes
+// advanced together.  One "tick" is
+//   (1) one A-stream launch over every active instance's steps (the panel
+//       kernel with a device table of instances, split evenly over the SMs),
+//       each instance reading its own current X (spectral basis or iterate);
+//   (2) one phase launch, one CTA per instance: a spectral pass (W = A V,
+//       float64 Gram, Cholesky, V <- W R^{-1}, residual; on convergence the
+//       exact blockwise sign gives X^0, Algorithm 2's start) or an NS-RGS
+//       iteration (block_update for every block, update norm, stop test; on
+//       stop X is copied to the caller's buffer).
+// Instances therefore sit in different phases in the same tick.  A batch
+// solve is an admit launch followed by (spectral passes + T) ticks replayed
+// from a CUDA graph; the server (server.cu) runs ticks while it admits and
+// retires requests between them.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "batch.cuh"
+#include "blockops.cuh"
+#include "panel.cuh"
+
+namespace nsrgs {
+
+// ------------------------------------------------------------ the source
+struct BatchSrc {
+  const BatchDesc* descs;
+  const long long* base;  // count + 1 entries: first global step of each instance
+  int cnt;
+  __device__ __forceinline__ int count() const { return cnt; }
+  __device__ __forceinline__ const long long* bases() const { return base; }
+  __device__ __forceinline__ InstView view(int i) const {
+    const BatchDesc& d = descs[i];
+    const Ctl* c = d.ctl;
+    const int ph = c->phase;
+    InstView v;
+    v.packed = d.packed;
+    v.Y = d.Y;
+    v.ctl = d.ctl;
+    v.g = d.g;
+    if (ph == PHASE_SPEC) {
+      v.X = d.X[(c->spec_iters + 1) & 1];
+      v.skip = false;
+    } else if (ph == PHASE_ITER) {
+      v.X = d.X[c->iters_done & 1];
+      v.skip = false;
+    } else {
+      v.X = d.X[0];
+      v.skip = true;
+    }
+    return v;
+  }
+};
+
+template <int D, int RB, int ST>
+__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_batch_kernel(BatchSrc src) {
+  panel_stream_body<D, RB, ST>(src, src.base[src.cnt]);
+}
+
+// ------------------------------------------------ per-instance CTA kernels
+// W = Y + V (or W = V when Y is null), W^T W and V^T W in float64, Cholesky of
+// W^T W; Vn = W chol^{-1}; returns ||W - V H||^2 and ||H||^2 in thread 0.
+template <int D>
+__device__ void cta_subspace_step(const float* __restrict__ V, float* __restrict__ Y, float* __restrict__ W,
+                                  float* __restrict__ Vn, int rows, double* res_out, double* h2_out) {
+  __shared__ double sh[32];
+  __shared__ double WW[D * D], H[D * D], Rinv[D * D], Rtmp[D * D];
+  double ww[D][D], vw[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) ww[a][b] = vw[a][b] = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    float v[D], w[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = V[(long long)r * D + k];
+      w[k] = Y ? Y[(long long)r * D + k] + v[k] : v[k];
+      W[(long long)r * D + k] = w[k];
+      if (Y) Y[(long long)r * D + k] = 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        ww[a][b] += (double)w[a] * (double)w[b];
+        vw[a][b] += (double)v[a] * (double)w[b];
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double x1 = block_sum(ww[a][b], sh);
+      const double x2 = block_sum(vw[a][b], sh);
+      if (threadIdx.x == 0) {
+        WW[a * D + b] = x1;
+        H[a * D + b] = x2;
+      }
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    chol_inv(WW, Rinv, D, Rtmp);
+    double h2 = 0.0;
+    for (int o = 0; o < D * D; ++o) h2 += H[o] * H[o];
+    *h2_out = h2;
+  }
+  __syncthreads();
+  double res = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    double v[D], w[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = V[(long long)r * D + k];
+      w[k] = W[(long long)r * D + k];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double nv = 0.0, vh = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        nv += w[k] * Rinv[k * D + c];
+        vh += v[k] * H[k * D + c];
+      }
+      Vn[(long long)r * D + c] = (float)nv;
+      const double e = w[c] - vh;
+      res += e * e;
+    }
+  }
+  const double tot = block_sum(res, sh);
+  if (threadIdx.x == 0) *res_out = tot;
+  __syncthreads();
+}
+
+// X0_i = sgn(V_i) for every block of one instance (in place allowed).
+template <int D>
+__device__ void cta_polar(const float* V, float* X0, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double M[D][D], Q[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) M[r][c] = V[((long long)i * D + r) * D + c];
+    polar_fp64<D>(M, Q);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) X0[((long long)i * D + r) * D + c] = (float)Q[r][c];
+  }
+}
+
+__device__ __forceinline__ float v0_entry(long long e) {
+  unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+// Prepares every instance in PHASE_ADMIT: clears its scratch, then either takes
+// X^0 from the caller (start_given) or builds the orthonormal start basis of
+// the spectral subspace iteration.
+template <int D>
+__global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs) {
+  const BatchDesc& d = descs[blockIdx.x];
+  Ctl* c = d.ctl;
+  if (c->phase != PHASE_ADMIT) return;
+  const int n = d.g.n;
+  const int rows = n * D;
+  const long long vec = (long long)xpad_rows(n, D) * D;
+  for (long long e = threadIdx.x; e < vec; e += blockDim.x) {
+    d.Y[e] = 0.f;
+    if (e >= (long long)rows * D) {
+      d.X[0][e] = 0.f;
+      d.X[1][e] = 0.f;
+    }
+  }
+  __syncthreads();
+  if (d.start_given) {
+    for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = d.Xout[e];
+  } else {
+    for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = v0_entry(e);
+    __syncthreads();
+    double res, h2;
+    cta_subspace_step<D>(d.X[0], nullptr, d.W, d.X[1], rows, &res, &h2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c->upd_acc = 0.0;
+    c->last_upd = 0.0;
+    c->spec_res = 0.0;
+    c->counter = 0u;
+    c->iters_done = 0;
+    c->stop = 0;
+    c->flags = 0u;
+    c->spec_iters = 0;
+    c->spec_stop = 0;
+    c->phase = d.start_given ? (d.T > 0 ? PHASE_ITER : PHASE_DONE) : PHASE_SPEC;
+  }
+  if (d.start_given && d.T == 0) {
+    // nothing to iterate: X^0 is the answer (already in the caller's buffer)
+  }
+}
+
+// One phase step per instance (CTA per instance), after the tick's A-stream.
+template <int D>
+__global__ void __launch_bounds__(256) batch_phase_kernel(const BatchDesc* descs) {
+  __shared__ double sh[32];
+  __shared__ int fin;
+  __shared__ double s_res, s_h2;
+  const BatchDesc& d = descs[blockIdx.x];
+  Ctl* c = d.ctl;
+  const int ph = c->phase;  // uniform: written only by earlier launches
+  const int n = d.g.n;
+  const int rows = n * D;
+  if (ph == PHASE_SPEC) {
+    const int si = c->spec_iters;
+    const float* V = d.X[(si + 1) & 1];
+    float* Vn = d.X[si & 1];
+    cta_subspace_step<D>(V, d.Y, d.W, Vn, rows, &s_res, &s_h2);
+    if (threadIdx.x == 0) {
+      const double rel = sqrt(s_res / fmax(s_h2, 1e-300));
+      c->spec_res = rel;
+      c->spec_iters = si + 1;
+      if (rel <= d.spec_tol) c->spec_stop = 1;
+      fin = (rel <= d.spec_tol) || (si + 1 >= d.smax);
+    }
+    __syncthreads();
+    if (fin) {
+      cta_polar<D>(Vn, d.X[0], n);  // Algorithm 2's start X^0 = sgn_n(Y)
+      __syncthreads();
+      if (d.T == 0)
+        for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.Xout[e] = d.X[0][e];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        c->iters_done = 0;
+        c->phase = d.T > 0 ? PHASE_ITER : PHASE_DONE;
+      }
+    }
+  } else if (ph == PHASE_ITER) {
+    const int it = c->iters_done;
+    const float* Xc = d.X[it & 1];
+    float* Xn = d.X[(it + 1) & 1];
+    double diff2 = 0.0;
+    unsigned int flags = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) block_update<D>(Xc, d.Y, Xn, i, n, d.eta, d.K, diff2, flags);
+    if (flags) atomicOr(&c->flags, flags);
+    const double tot = block_sum(diff2, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double un = sqrt(tot / ((double)n * D));
+      c->last_upd = un;
+      c->iters_done = it + 1;
+      const bool conv = d.tol > 0.0 && un < d.tol;
+      if (conv) c->stop = 1;
+      fin = (it + 1 >= d.T) || conv || ((c->flags & FLAG_NONFINITE) != 0);
+    }
+    __syncthreads();
+    if (fin) {
+      for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.Xout[e] = Xn[e];
+      __syncthreads();
+      if (threadIdx.x == 0) c->phase = PHASE_DONE;
+    }
+  }
+}
+
+// Compact per-instance report (one device-to-host copy for the whole batch).
+__global__ void batch_report_kernel(const BatchDesc* descs, int count, BatchReport* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const Ctl* c = descs[i].ctl;
+  BatchReport r;
+  r.phase = c->phase;
+  r.spec_iters = c->spec_iters;
+  r.iters = c->iters_done;
+  r.flags = c->flags;
+  r.last_upd = c->last_upd;
+  r.spec_res = c->spec_res;
+  out[i] = r;
+}
+
+// Marks every instance of the table as admitted (start of a batch solve).
+__global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  Ctl* c = descs[i].ctl;
+  c->phase = PHASE_ADMIT;
+  c->flags = 0u;
+}
+
+// ------------------------------------------------------------- launchers
+template <int D, int ST>
+static cudaError_t launch_batch_stream_t(const BatchSrc& s, cudaStream_t st, bool prepare) {
+  constexpr int RB = PanelRB<D>::value;
+  using C = PCfg<D, RB, ST>;
+  if (prepare)
+    return cudaFuncSetAttribute(panel_stream_batch_kernel<D, RB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                C::SMEM);
+  panel_stream_batch_kernel<D, RB, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(s);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t launch_batch_stream_d(const BatchSrc& s, int storage, cudaStream_t st, bool prepare) {
+  switch (storage) {
+    case NSRGS_F32: return launch_batch_stream_t<D, NSRGS_F32>(s, st, prepare);
+    case NSRGS_BF16: return launch_batch_stream_t<D, NSRGS_BF16>(s, st, prepare);
+    case NSRGS_FP8E4M3: return launch_batch_stream_t<D, NSRGS_FP8E4M3>(s, st, prepare);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int count, int d, int storage,
+                         cudaStream_t st, bool prepare) {
+  BatchSrc s{descs, base, count};
+  switch (d) {
+    case 1: return launch_batch_stream_d<1>(s, storage, st, prepare);
+    case 2: return launch_batch_stream_d<2>(s, storage, st, prepare);
+    case 3: return launch_batch_stream_d<3>(s, storage, st, prepare);
+    case 4: return launch_batch_stream_d<4>(s, storage, st, prepare);
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define NSRGS_BATCH_D(d, F)                \
+  switch (d) {                             \
+    case 1: F(1); break;                   \
+    case 2: F(2); break;                   \
+    case 3: F(3); break;                   \
+    case 4: F(4); break;                   \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st) {
+#define L(DD) batch_admit_kernel<DD><<<count, 256, 0, st>>>(descs)
+  NSRGS_BATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t st) {
+#define L(DD) batch_phase_kernel<DD><<<count, 256, 0, st>>>(descs)
+  NSRGS_BATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st) {
+  batch_report_kernel<<<(count + 127) / 128, 128, 0, st>>>(descs, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_reset(const BatchDesc* descs, int count, cudaStream_t st) {
+  batch_reset_kernel<<<(count + 127) / 128, 128, 0, st>>>(descs, count);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ host layout
+size_t batch_instance_bytes(int n, int d) {
+  const size_t vec = ((size_t)xpad_rows(n, d) * d * sizeof(float) + 255) / 256 * 256;
+  return 256 + 4 * vec;
+}
+
+size_t batch_table_bytes(int count) {
+  const size_t t = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
+  const size_t b = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
+  const size_t r = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
+  return t + b + r;
+}
+
+void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d) {
+  const size_t vec = ((size_t)xpad_rows(n, d) * d * sizeof(float) + 255) / 256 * 256;
+  ds.ctl = reinterpret_cast<Ctl*>(region);
+  ds.X[0] = reinterpret_cast<float*>(region + 256);
+  ds.X[1] = reinterpret_cast<float*>(region + 256 + vec);
+  ds.Y = reinterpret_cast<float*>(region + 256 + 2 * vec);
+  ds.W = reinterpret_cast<float*>(region + 256 + 3 * vec);
+}
+
+}  // namespace nsrgs
+
+using namespace nsrgs;
+
+namespace {
+
+struct BatchGraphKey {
+  uint64_t hash;
+  int count, d, storage, T, K, init, smax;
+  double tol;
+  void* ws;
+  int dev;
+  bool operator==(const BatchGraphKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+std::mutex g_bmu;
+std::vector<std::pair<BatchGraphKey, cudaGraphExec_t>> g_bgraphs;
+cudaStream_t g_bcap[64] = {};
+
+uint64_t fnv(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+extern "C" size_t nsrgs_batch_workspace_bytes(const int* n, int count, int d) {
+  if (!n || count < 1 || d < 1 || d > 4) return 0;
+  size_t b = batch_table_bytes(count);
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 2) return 0;
+    b += batch_instance_bytes(n[i], d);
+  }
+  return b;
+}
+
+extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int count, int d, int storage, int T, int K,
+                                          double tol, int init, int spectral_max_iters, nsrgs_info* info, void* ws,
+                                          size_t ws_bytes, void* stv) {
+  NSRGS_CHECK_ARG(items != nullptr && count >= 1 && count <= (1 << 20), "items must be non-null, count >= 1");
+  NSRGS_CHECK_ARG(d >= 1 && d <= 4, "the batched form covers 1 <= d <= 4");
+  NSRGS_CHECK_ARG(storage >= NSRGS_F32 && storage <= NSRGS_FP8E4M3, "batched storage must be F32, BF16 or FP8E4M3");
+  NSRGS_CHECK_ARG(T >= 0 && T <= 100000 && K >= 0 && K <= 64, "T in [0, 100000], K in [0, 64]");
+  NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
+  NSRGS_CHECK_ARG(!init || (spectral_max_iters >= 1 && spectral_max_iters <= 10000),
+                  "spectral_max_iters must be in [1, 10000]");
+  NSRGS_CHECK_ARG(ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & 255u) == 0, "workspace must be 256-byte aligned");
+  std::vector<int> ns(count);
+  for (int i = 0; i < count; ++i) {
+    const nsrgs_batch_item& it = items[i];
+    NSRGS_CHECK_ARG(it.n >= 2 && (long long)it.n * d <= (1LL << 24), "every item needs n >= 2");
+    NSRGS_CHECK_ARG(it.packed && (reinterpret_cast<uintptr_t>(it.packed) & 15u) == 0, "item packed must be 16-byte aligned");
+    NSRGS_CHECK_ARG(it.X && (reinterpret_cast<uintptr_t>(it.X) & 15u) == 0, "item X must be 16-byte aligned");
+    NSRGS_CHECK_ARG(it.eta > 0.f && isfinite(it.eta), "item eta must be finite and > 0");
+    ns[i] = it.n;
+  }
+  const size_t need = nsrgs_batch_workspace_bytes(ns.data(), count, d);
+  if (ws_bytes < need) {
+    set_error("workspace smaller than nsrgs_batch_workspace_bytes");
+    return NSRGS_ERR_NOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stv;
+  // host image of the instance table
+  uint8_t* base = reinterpret_cast<uint8_t*>(ws);
+  const size_t tbytes = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
+  const size_t bbytes = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
+  BatchDesc* d_descs = reinterpret_cast<BatchDesc*>(base);
+  long long* d_base = reinterpret_cast<long long*>(base + tbytes);
+  BatchReport* d_rep = reinterpret_cast<BatchReport*>(base + tbytes + bbytes);
+  std::vector<BatchDesc> descs(count);
+  std::vector<long long> bases(count + 1);
+  size_t off = batch_table_bytes(count);
+  long long steps = 0;
+  for (int i = 0; i < count; ++i) {
+    BatchDesc& ds = descs[i];
+    memset(&ds, 0, sizeof(ds));
+    if (!make_panel_geom(items[i].n, d, storage, &ds.g)) {
+      set_error("unsupported (n, d, storage) in batch");
+      return NSRGS_ERR_UNSUPPORTED;
+    }
+    ds.packed = reinterpret_cast<const uint8_t*>(items[i].packed);
+    fill_instance(ds, base + off, items[i].n, d);
+    off += batch_instance_bytes(items[i].n, d);
+    ds.Xout = items[i].X;
+    ds.eta = items[i].eta;
+    ds.tol = tol;
+    ds.spec_tol = 1e-6;
+    ds.T = T;
+    ds.K = K;
+    ds.smax = init ? spectral_max_iters : 0;
+    ds.start_given = init ? 0 : 1;
+    bases[i] = steps;
+    steps += ds.g.total_steps;
+  }
+  bases[count] = steps;
+  NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(d_base, bases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
+
+  int dev = 0;
+  NSRGS_CUDA_TRY(cudaGetDevice(&dev));
+  BatchGraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.hash = fnv(descs.data(), sizeof(BatchDesc) * count);
+  key.count = count;
+  key.d = d;
+  key.storage = storage;
+  key.T = T;
+  key.K = K;
+  key.init = init ? 1 : 0;
+  key.smax = init ? spectral_max_iters : 0;
+  key.tol = tol;
+  key.ws = ws;
+  key.dev = dev;
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto& e : g_bgraphs)
+      if (e.first == key) exec = e.second;
+  }
+  if (!exec) {
+    if (!g_bcap[dev]) NSRGS_CUDA_TRY(cudaStreamCreateWithFlags(&g_bcap[dev], cudaStreamNonBlocking));
+    cudaStream_t cs = g_bcap[dev];
+    NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = batch_reset(d_descs, count, cs);
+    if (e == cudaSuccess) e = batch_admit(d_descs, count, d, cs);
+    const int ticks = (init ? spectral_max_iters : 0) + T;
+    for (int t = 0; t < ticks && e == cudaSuccess; ++t) {
+      e = batch_stream(d_descs, d_base, count, d, storage, cs, false);
+      if (e == cudaSuccess) e = batch_phase(d_descs, count, d, cs);
+    }
+    if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      set_error(std::string("batch graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      return NSRGS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      return NSRGS_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_bmu);
+    g_bgraphs.emplace_back(key, exec);
+    if (g_bgraphs.size() > 8) {
+      cudaGraphExecDestroy(g_bgraphs.front().second);
+      g_bgraphs.erase(g_bgraphs.begin());
+    }
+  }
+  NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  if (info) {
+    std::vector<BatchReport> rep(count);
+    NSRGS_CUDA_TRY(cudaMemcpyAsync(rep.data(), d_rep, sizeof(BatchReport) * count, cudaMemcpyDeviceToHost, st));
+    NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+    bool timeout = false, nonfinite = false;
+    for (int i = 0; i < count; ++i) {
+      info[i].spectral_iters = rep[i].spec_iters;
+      info[i].iters = rep[i].iters;
+      info[i].last_update_norm = rep[i].last_upd;
+      info[i].spectral_residual = rep[i].spec_res;
+      info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND)) |
+                      ((init && rep[i].spec_res > 1e-6) ? FLAG_SPEC_NOT_CONVERGED : 0u);
+      timeout = timeout || (rep[i].flags & FLAG_TIMEOUT);
+      nonfinite = nonfinite || (rep[i].flags & FLAG_NONFINITE);
+    }
+    if (timeout) {
+      set_error("a device-side wait timed out");
+      return NSRGS_ERR_TIMEOUT;
+    }
+    if (nonfinite) {
+      set_error("an iterate became non-finite in at least one instance");
+      return NSRGS_ERR_NONFINITE;
+    }
+  }
+  return NSRGS_OK;
+}

@@ -1,0 +1,46 @@
+// Instance table of the batched and served forms (shared by batch.cu and server.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace nsrgs {
+
+// One instance as the batched kernels see it (device memory, written by the host).
+struct BatchDesc {
+  const uint8_t* packed;  // packed A (panel layout)
+  float* X[2];            // ping-pong iterates / spectral bases, padded to n*d + 64 rows
+  float* Y;               // A-stream accumulator, padded
+  float* W;               // spectral scratch, padded
+  Ctl* ctl;               // control block: phase, counters, flags
+  float* Xout;            // caller's X: X^0 when start_given, the result when done
+  PanelGeom g;
+  float eta;
+  int T;
+  int K;
+  int smax;               // spectral passes cap
+  int start_given;        // 1: X^0 comes from Xout, no spectral initialisation
+  int pad;
+  double tol;             // stop when the update norm falls below it (0: run T iterations)
+  double spec_tol;        // spectral residual target
+};
+
+struct BatchReport {
+  int phase;
+  int spec_iters;
+  int iters;
+  unsigned int flags;
+  double last_upd;
+  double spec_res;
+};
+
+size_t batch_instance_bytes(int n, int d);
+size_t batch_table_bytes(int count);
+void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d);
+cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int count, int d, int storage,
+                         cudaStream_t st, bool prepare);
+cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st);
+cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t st);
+cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st);
+cudaError_t batch_reset(const BatchDesc* descs, int count, cudaStream_t st);
+
+}  // namespace nsrgs

@@ -47,7 +47,17 @@ struct Ctl {
   unsigned int flags;      // FLAG_* bits
   int spec_iters;          // subspace iterations run
   int spec_stop;           // set when the subspace residual fell below tol
-  int pad[2];
+  int phase;               // batched / served instances: PHASE_*
+  int pad;
+};
+
+// Phase of an instance in the batched and served forms.
+enum : int {
+  PHASE_IDLE = 0,   // slot unused
+  PHASE_ADMIT = 1,  // admitted, start not prepared yet
+  PHASE_SPEC = 2,   // spectral initialisation passes
+  PHASE_ITER = 3,   // NS-RGS iterations
+  PHASE_DONE = 4,   // finished; X copied to the caller
 };
 
 enum : unsigned int {

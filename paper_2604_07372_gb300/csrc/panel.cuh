@@ -1,0 +1,484 @@
+// The symmetric read-once A-stream (Y = A_off X), shared by the single-instance
+// and the batched launches.
+//
+// Each stored block A_ij (i < j) of the strict block-upper triangle feeds both
+// Y_i += A_ij X_j and Y_j += A_ij^T X_i (Algorithm 2's gradient needs
+// sum_{j != i} A_ij X_j), so A is read once per iteration.
+//
+// Kernel structure (persistent, one CTA per SM, 10 warps):
+//  * warp NW (producer): lane 0 walks the CTA's contiguous range of steps and
+//    issues 1-D TMA bulk copies (cp.async.bulk) of each step's warp slices and
+//    of the X rows of the step's columns into a ring of shared-memory stages,
+//    completion tracked by mbarriers (expect_tx);
+//  * warps 0..NW-1 (consumers): warp w owns slab rows [w*WROWS, (w+1)*WROWS);
+//    lane (rg, cg) owns RB whole block rows and CPT consecutive columns of each
+//    step.  Row partials of Y accumulate in registers across the whole walk
+//    through a slab (reduced over the 4 cg lanes and added to Y once per slab).
+//    Column partials of a step are reduced over the 8 rg lanes with shuffles
+//    and written to a slot of a small shared-memory ring;
+//  * warp NW+1 (reducer): sums a slot over the consumer warps and adds the
+//    step's column partials to Y with red.global.add.v4.f32, then frees the
+//    slot.  Consumers never wait for each other, only for data and slots.
+// A "source" supplies the instances: one instance (from the kernel parameters)
+// or a device table of instances whose steps are concatenated, so a batch of
+// instances of different sizes is one evenly split launch.
+// Every wait is bounded (globaltimer); a timeout sets FLAG_TIMEOUT in the
+// instance's control block and ends the kernel instead of hanging.
+#pragma once
+
+#include "common.cuh"
+
+namespace nsrgs {
+
+template <int D, int RB, int ST>
+struct PCfg {
+  static constexpr int E = ST == NSRGS_F32 ? 4 : (ST == NSRGS_BF16 ? 2 : 1);
+  static constexpr int LOADB = ST == NSRGS_FP8E4M3 ? 8 : 16;
+  static constexpr int CPT = LOADB / E;
+  static constexpr int SC = 4 * CPT;
+  static constexpr int NW = 8;
+  static constexpr int RT = RB * D;
+  static constexpr int WROWS = 8 * RT;
+  static constexpr int SB = NW * 8 * RB;
+  static constexpr int RS = SB * D;
+  static constexpr int WB = WROWS * SC * E;
+  static constexpr int STAGE_A = NW * WB;
+  static constexpr int STAGE_X = SC * D * 4;
+  static constexpr int STAGE_BYTES = (STAGE_A + STAGE_X + 127) / 128 * 128;
+  static constexpr int NSTAGE_RAW = (168 * 1024) / STAGE_BYTES;
+  static constexpr int NSTAGE = NSTAGE_RAW > 12 ? 12 : (NSTAGE_RAW < 2 ? 2 : NSTAGE_RAW);
+  static constexpr int NV = CPT * D;      // column-partial values per thread and step
+  static constexpr int COLVALS = SC * D;  // column-partial values per warp and step
+  static constexpr int RING = 4;          // column-partial slots between consumers and reducer
+  static constexpr int THREADS = (NW + 2) * 32;
+  // shared memory: stages | ring[RING][NW][COLVALS] | full[NSTAGE] empty[NSTAGE] cfull[RING] cempty[RING]
+  static constexpr int OFF_RING = NSTAGE * STAGE_BYTES;
+  static constexpr int OFF_BARS = OFF_RING + RING * NW * COLVALS * 4;
+  static constexpr int SMEM = OFF_BARS + (2 * NSTAGE + 2 * RING) * 8;
+  static_assert(COLVALS % 4 == 0 && COLVALS / 4 <= 32, "reducer lanes");
+};
+
+// Block rows per thread for each d (keeps every thread on whole block rows and
+// the register footprint near 110-130 registers).
+template <int D>
+struct PanelRB {
+  static constexpr int value = D == 1 ? 8 : (D == 2 ? 4 : (D == 3 ? 2 : 1));
+};
+
+// ---------------------------------------------------- column reduction
+// Transposed butterfly over the 8 rg lanes (lane bits 4, 3, 2).  While the
+// value count splits into whole columns the two partners exchange halves;
+// otherwise they do a full exchange (and only one of them remains the owner).
+template <int N, int D, int LVL>
+struct RedLevel {
+  static constexpr bool kSplit = (N % 2 == 0) && ((N / 2) % D == 0);
+  static constexpr int kNext = kSplit ? N / 2 : N;
+  static constexpr int kFinal = RedLevel<kNext, D, LVL + 1>::kFinal;
+  __device__ __forceinline__ static void run(float* v, int lane, int& col0, bool& owner) {
+    constexpr int mask = 16 >> LVL;
+    const bool bit = (lane & mask) != 0;
+    if constexpr (kSplit) {
+      constexpr int H = N / 2;
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        float send = bit ? v[k] : v[k + H];
+        float keep = bit ? v[k + H] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+      }
+      col0 += bit ? (H / D) : 0;
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], mask);
+      owner = owner && !bit;
+    }
+    RedLevel<kNext, D, LVL + 1>::run(v, lane, col0, owner);
+  }
+};
+
+template <int N, int D>
+struct RedLevel<N, D, 3> {
+  static constexpr int kFinal = N;
+  __device__ __forceinline__ static void run(float*, int, int&, bool&) {}
+};
+
+// ---------------------------------------------------- element unpacking
+template <int ST, int CPT>
+struct Unpack;
+
+template <int CPT>
+struct Unpack<NSRGS_F32, CPT> {
+  using V = float4;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+  }
+};
+
+template <int CPT>
+struct Unpack<NSRGS_BF16, CPT> {
+  using V = uint4;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+
+template <int CPT>
+struct Unpack<NSRGS_FP8E4M3, CPT> {
+  using V = uint2;
+  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
+    const uint32_t w[2] = {x.x, x.y};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
+      __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+      float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+      float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+      o[4 * k + 0] = a.x; o[4 * k + 1] = a.y; o[4 * k + 2] = b.x; o[4 * k + 3] = b.y;
+    }
+  }
+};
+
+__device__ __forceinline__ int find_first_leq(const long long* starts, int count, long long s) {
+  int lo = 0, hi = count - 1;  // last index with starts[idx] <= s
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One instance as the kernel sees it.
+struct InstView {
+  const uint8_t* packed;
+  const float* X;  // padded, n*D + 64 rows
+  float* Y;        // padded accumulator, zero on entry
+  Ctl* ctl;
+  PanelGeom g;
+  bool skip;
+};
+
+// Position in the walk over one instance's steps, in 32-bit arithmetic with
+// the geometry's compile-time constants.  W (stored warp slices of the step)
+// is nondecreasing along a slab, so it is recomputed only until it reaches NW.
+template <class C, int D>
+struct Walk {
+  const long long* step_start;
+  int nslabs, n;
+  int b, q, Sb, W;
+  bool ragged;
+
+  __device__ __forceinline__ int warps() const {
+    const int c_end = b * C::SB * D + (q + 1) * C::SC;
+    int jmax = (c_end - 1) / D;
+    jmax = jmax < n - 1 ? jmax : n - 1;
+    int rmax = (jmax - b * C::SB) * D;
+    const int rlim = (n - b * C::SB) * D;
+    rmax = rmax < rlim ? rmax : rlim;
+    rmax = rmax < C::RS ? rmax : C::RS;
+    rmax = rmax > 1 ? rmax : 1;
+    const int w = (rmax + C::WROWS - 1) / C::WROWS;
+    return w < C::NW ? w : C::NW;
+  }
+  __device__ __forceinline__ void refresh() {
+    if (ragged) {
+      W = warps();
+      ragged = W < C::NW;
+    }
+  }
+  __device__ __forceinline__ void start(const InstView& v, long long local_step) {
+    step_start = reinterpret_cast<const long long*>(v.packed + v.g.off_step_start);
+    nslabs = v.g.nslabs;
+    n = v.g.n;
+    b = find_first_leq(step_start, nslabs, local_step);
+    q = (int)(local_step - step_start[b]);
+    Sb = (int)(step_start[b + 1] - step_start[b]);
+    ragged = true;
+    refresh();
+  }
+  // Returns true when the walk left slab b (the caller flushes it).
+  __device__ __forceinline__ bool advance() {
+    if (++q < Sb) {
+      refresh();
+      return false;
+    }
+    ++b;
+    q = 0;
+    if (b < nslabs) {
+      Sb = (int)(step_start[b + 1] - step_start[b]);
+      ragged = true;
+      refresh();
+    }
+    return true;
+  }
+  __device__ __forceinline__ int xcol() const { return b * C::SB * D + q * C::SC; }
+};
+
+// Runs `fn(view, lo, hi)` for every instance segment [lo, hi) (local step
+// indices) of the global step range [g0, g1), in order.
+template <class Src, class Fn>
+__device__ __forceinline__ void for_segments(const Src& src, long long g0, long long g1, Fn&& fn) {
+  int inst = find_first_leq(src.bases(), src.count(), g0);
+  long long s = g0;
+  while (s < g1 && inst < src.count()) {
+    const long long base = src.bases()[inst];
+    const long long end = src.bases()[inst + 1];
+    const long long hi = end < g1 ? end : g1;
+    if (hi > s) {
+      const InstView v = src.view(inst);
+      if (!fn(v, s - base, hi - base)) return;
+    }
+    s = hi;
+    ++inst;
+  }
+}
+
+template <int D, int RB, int ST, class Src>
+__device__ __forceinline__ void panel_stream_body(const Src& src, long long total_steps) {
+  using C = PCfg<D, RB, ST>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const long long g0 = total_steps * blockIdx.x / gridDim.x;
+  const long long g1 = total_steps * (blockIdx.x + 1) / gridDim.x;
+  if (g0 >= g1) return;
+
+  float* ring = reinterpret_cast<float*>(smem + C::OFF_RING);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BARS);
+  uint64_t* empty = full + C::NSTAGE;
+  uint64_t* cfull = empty + C::NSTAGE;
+  uint64_t* cempty = cfull + C::RING;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::NW);
+    }
+    for (int s = 0; s < C::RING; ++s) {
+      mbar_init(&cfull[s], C::NW);
+      mbar_init(&cempty[s], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (warp == C::NW) {
+    // ------------------------------------------------------------- producer
+    if (lane != 0) return;
+    int st = 0;
+    uint32_t ph = 0;
+    int issued = 0;
+    bool ok = true;
+    for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
+      if (v.skip) return true;
+      Walk<C, D> wk;
+      wk.start(v, lo);
+      const long long* byte_off = reinterpret_cast<const long long*>(v.packed + v.g.off_byte_off);
+      const uint8_t* panels = v.packed + v.g.header_bytes;
+      long long off = byte_off[wk.b] + panel_step_offset(v.g, wk.b, wk.q);
+      for (long long s = lo; s < hi; ++s) {
+        if (issued >= C::NSTAGE && !mbar_wait_bounded(&empty[st], ph ^ 1u, kWaitLimitNs)) {
+          atomicOr(&v.ctl->flags, FLAG_TIMEOUT);
+          ok = false;
+          return false;
+        }
+        const uint32_t bytesA = (uint32_t)wk.W * C::WB;
+        uint8_t* stage = smem + st * C::STAGE_BYTES;
+        mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
+        bulk_g2s(stage, panels + off, bytesA, &full[st]);
+        bulk_g2s(stage + C::STAGE_A, v.X + (long long)wk.xcol() * D, C::STAGE_X, &full[st]);
+        off += bytesA;
+        if (wk.advance() && wk.b < wk.nslabs) off = byte_off[wk.b];
+        ++issued;
+        if (++st == C::NSTAGE) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      return true;
+    });
+    (void)ok;
+    // Do not leave while copies into this CTA's shared memory may be in flight.
+    const int first = issued > C::NSTAGE ? issued - C::NSTAGE : 0;
+    for (int k = first; k < issued; ++k)
+      if (!mbar_wait_bounded(&full[k % C::NSTAGE], (uint32_t)((k / C::NSTAGE) & 1), kWaitLimitNs)) break;
+    return;
+  }
+
+  if (warp == C::NW + 1) {
+    // -------------------------------------------------------------- reducer
+    int slot = 0;
+    uint32_t ph = 0;
+    for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
+      if (v.skip) return true;
+      Walk<C, D> wk;
+      wk.start(v, lo);
+      for (long long s = lo; s < hi; ++s) {
+        if (!mbar_wait_bounded(&cfull[slot], ph, kWaitLimitNs)) {
+          atomicOr(&v.ctl->flags, FLAG_TIMEOUT);
+          return false;
+        }
+        if (lane < C::COLVALS / 4) {
+          const float* base = ring + slot * C::NW * C::COLVALS + 4 * lane;
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int w = 0; w < C::NW; ++w) {
+            if (w < wk.W) {
+              const float4 x = *reinterpret_cast<const float4*>(base + w * C::COLVALS);
+              sum.x += x.x; sum.y += x.y; sum.z += x.z; sum.w += x.w;
+            }
+          }
+          red_add_v4_f32(v.Y + (long long)wk.xcol() * D + 4 * lane, sum.x, sum.y, sum.z, sum.w);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cempty[slot]);
+        wk.advance();
+        if (++slot == C::RING) {
+          slot = 0;
+          ph ^= 1u;
+        }
+      }
+      return true;
+    });
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumers
+  using Vec = typename Unpack<ST, C::CPT>::V;
+  const int rg = lane >> 2;
+  const int cg = lane & 3;
+  int st = 0, slot = 0;
+  uint32_t ph = 0, cph = 0;
+  int it = 0;  // steps consumed by this CTA so far (all segments)
+
+  for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
+    if (v.skip) return true;
+    const int n = v.g.n;
+    const float* scale =
+        (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(v.packed + v.g.off_scale) : nullptr;
+    float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
+    float racc[C::RT][D];  // row partials
+    float rsc[RB];         // FP8 row scales
+    auto load_rows = [&](int bb) {
+#pragma unroll
+      for (int rb = 0; rb < RB; ++rb) {
+        const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
+        float s = 1.f;
+        if (ST == NSRGS_FP8E4M3 && i < n) s = scale[i];
+        rsc[rb] = s;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            xr[rb * D + r][k] = (i < n) ? v.X[((long long)i * D + r) * D + k] * s : 0.f;
+            racc[rb * D + r][k] = 0.f;
+          }
+      }
+    };
+    auto flush_rows = [&](int bb) {
+#pragma unroll
+      for (int r = 0; r < C::RT; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float x = racc[r][k];
+          x += __shfl_xor_sync(0xffffffffu, x, 1);
+          x += __shfl_xor_sync(0xffffffffu, x, 2);
+          racc[r][k] = x;
+        }
+      if (cg == 0) {
+#pragma unroll
+        for (int rb = 0; rb < RB; ++rb) {
+          const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
+          if (i < n) {
+#pragma unroll
+            for (int r = 0; r < D; ++r)
+#pragma unroll
+              for (int k = 0; k < D; ++k)
+                red_add_f32(v.Y + ((long long)i * D + r) * D + k, racc[rb * D + r][k] * rsc[rb]);
+          }
+        }
+      }
+    };
+
+    Walk<C, D> wk;
+    wk.start(v, lo);
+    load_rows(wk.b);
+    for (long long s = lo; s < hi; ++s, ++it) {
+      if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
+        atomicOr(&v.ctl->flags, FLAG_TIMEOUT);
+        return false;
+      }
+      const uint8_t* stage = smem + st * C::STAGE_BYTES;
+      float cacc[C::NV];
+#pragma unroll
+      for (int k = 0; k < C::NV; ++k) cacc[k] = 0.f;
+      const bool active = warp < wk.W;
+      if (active) {
+        Vec raw[C::RT];
+#pragma unroll
+        for (int rt = 0; rt < C::RT; ++rt)
+          raw[rt] = *reinterpret_cast<const Vec*>(stage + warp * C::WB + (rt * 32 + lane) * C::LOADB);
+        float xc[C::CPT * D];
+        const float4* xs = reinterpret_cast<const float4*>(stage + C::STAGE_A) + cg * (C::CPT * D / 4);
+#pragma unroll
+        for (int k = 0; k < C::CPT * D / 4; ++k) {
+          const float4 t = xs[k];
+          xc[4 * k + 0] = t.x; xc[4 * k + 1] = t.y; xc[4 * k + 2] = t.z; xc[4 * k + 3] = t.w;
+        }
+#pragma unroll
+        for (int rt = 0; rt < C::RT; ++rt) {
+          float av[C::CPT];
+          Unpack<ST, C::CPT>::run(raw[rt], av);
+#pragma unroll
+          for (int cc = 0; cc < C::CPT; ++cc) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
+              cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);  // stage fully read (values consumed above)
+      if (++st == C::NSTAGE) {
+        st = 0;
+        ph ^= 1u;
+      }
+
+      // column partials: 8 rg lanes -> owner lanes -> ring slot -> reducer warp
+      int col0 = 0;
+      bool owner = true;
+      RedLevel<C::NV, D, 0>::run(cacc, lane, col0, owner);
+      constexpr int NF = RedLevel<C::NV, D, 0>::kFinal;
+      if (it >= C::RING && !mbar_wait_bounded(&cempty[slot], cph ^ 1u, kWaitLimitNs)) {
+        atomicOr(&v.ctl->flags, FLAG_TIMEOUT);
+        return false;
+      }
+      if (owner && active) {
+        float* cb = ring + (slot * C::NW + warp) * C::COLVALS + (cg * C::CPT + col0) * D;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) cb[k] = cacc[k];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cfull[slot]);
+      if (++slot == C::RING) {
+        slot = 0;
+        cph ^= 1u;
+      }
+
+      const int bcur = wk.b;
+      if (wk.advance()) {
+        flush_rows(bcur);
+        if (s + 1 < hi) load_rows(wk.b);
+      }
+    }
+    if (wk.q != 0) flush_rows(wk.b);
+    return true;
+  });
+}
+
+}  // namespace nsrgs

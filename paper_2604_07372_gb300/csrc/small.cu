@@ -6,119 +6,15 @@
 //  * the distance d_F(X, Y) of §1.4.
 #include <math.h>
 
-#include "common.cuh"
+#include "blockops.cuh"
 
 namespace nsrgs {
 
 constexpr int kDmaxSmall = 8;  // thread-per-block kernels are instantiated for d <= 8
 
-// ------------------------------------------------------ float64 d x d polar
-// One-sided Jacobi (Hestenes) SVD: rotate column pairs of U = M until they are
-// orthogonal, accumulating the rotations in V; then U Sigma = M V and
-// sgn(M) = (U Sigma) Sigma^{-1} V^T (§2.1's matrix sign, exact up to rounding).
-template <int D>
-__device__ void polar_fp64(const double (&M)[D][D], double (&Q)[D][D]) {
-  double U[D][D], V[D][D];
-#pragma unroll
-  for (int r = 0; r < D; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      U[r][c] = M[r][c];
-      V[r][c] = (r == c) ? 1.0 : 0.0;
-    }
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0;
-#pragma unroll
-    for (int p = 0; p < D - 1; ++p)
-#pragma unroll
-      for (int q = p + 1; q < D; ++q) {
-        double al = 0.0, be = 0.0, ga = 0.0;
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-          al += U[r][p] * U[r][p];
-          be += U[r][q] * U[r][q];
-          ga += U[r][p] * U[r][q];
-        }
-        const double nrm = sqrt(al * be);
-        if (nrm == 0.0 || fabs(ga) <= 1e-17 * nrm) continue;
-        off = fmax(off, fabs(ga) / nrm);
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-          const double up = U[r][p], uq = U[r][q];
-          U[r][p] = c * up - s * uq;
-          U[r][q] = s * up + c * uq;
-          const double vp = V[r][p], vq = V[r][q];
-          V[r][p] = c * vp - s * vq;
-          V[r][q] = s * vp + c * vq;
-        }
-      }
-    if (off < 1e-15) break;
-  }
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    double s2 = 0.0;
-#pragma unroll
-    for (int r = 0; r < D; ++r) s2 += U[r][c] * U[r][c];
-    const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-#pragma unroll
-    for (int r = 0; r < D; ++r) U[r][c] *= inv;
-  }
-#pragma unroll
-  for (int r = 0; r < D; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      double acc = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc += U[r][k] * V[c][k];
-      Q[r][c] = acc;
-    }
-}
-
-// ------------------------------------------------- block reductions (fp64)
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the CTA; result valid in thread 0.
-__device__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-    r = warp_sum(r);
-  }
-  return r;
-}
-
-// Last-CTA election: returns true in every thread of the CTA that finishes last.
-__device__ bool last_block(unsigned int* counter) {
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int prev = atomicAdd(counter, 1u);
-    is_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (is_last) __threadfence();
-  return is_last;
-}
-
 // ------------------------------------------------------ iteration epilogue
-// Thread i handles block i (Algorithm 2's loop body, §2.2 projection):
-//   G = (n-1) X_i - Y_i,  P = (G - X_i G^T X_i)/2,  F = X_i - eta P,
-//   S <- S (3I - S^T S)/2 applied K times (Algorithm 1), X_i^{t+1} = S.
-// It also zeroes Y_i for the next pass and adds ||X^{t+1}_i - X_i||^2 to the
-// iteration's update norm; the last CTA finishes the norm and the stop test.
+// Thread i handles block i (block_update: Algorithm 2's loop body); the last
+// CTA finishes the update norm ||X^{t+1} - X^t||_F / sqrt(nd) and the stop test.
 template <int D>
 __global__ void __launch_bounds__(128) epilogue_kernel(const float* __restrict__ X, float* __restrict__ Y,
                                                        float* __restrict__ Xout, int n, float eta, int K,
@@ -128,94 +24,7 @@ __global__ void __launch_bounds__(128) epilogue_kernel(const float* __restrict__
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double diff2 = 0.0;
   unsigned int flags = 0;
-  if (i < n) {
-    float x[D][D], gm[D][D];
-    const float nm1 = (float)(n - 1);
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const long long e = ((long long)i * D + r) * D + c;
-        x[r][c] = X[e];
-        gm[r][c] = nm1 * x[r][c] - Y[e];
-        Y[e] = 0.f;
-      }
-    // T = G^T X
-    float t[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc = fmaf(gm[k][r], x[k][c], acc);
-        t[r][c] = acc;
-      }
-    // F = X - eta/2 (G - X T)
-    float s[D][D];
-    const float h = 0.5f * eta;
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        float xt = 0.f;
-#pragma unroll
-        for (int k = 0; k < D; ++k) xt = fmaf(x[r][k], t[k][c], xt);
-        s[r][c] = x[r][c] - h * (gm[r][c] - xt);
-      }
-    // Lemma 2.1 precondition, checked with ||I - F^T F||_F (>= the spectral norm)
-    {
-      float e2 = 0.f;
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float acc = (r == c) ? 1.f : 0.f;
-#pragma unroll
-          for (int k = 0; k < D; ++k) acc = fmaf(-s[k][r], s[k][c], acc);
-          e2 = fmaf(acc, acc, e2);
-        }
-      if (!(e2 < 1.f)) flags |= FLAG_NS_PRECOND;
-    }
-    for (int k = 0; k < K; ++k) {
-      float m[D][D];  // 3I - S^T S
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float acc = (r == c) ? 3.f : 0.f;
-#pragma unroll
-          for (int l = 0; l < D; ++l) acc = fmaf(-s[l][r], s[l][c], acc);
-          m[r][c] = acc;
-        }
-      float sn[D][D];
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float acc = 0.f;
-#pragma unroll
-          for (int l = 0; l < D; ++l) acc = fmaf(s[r][l], m[l][c], acc);
-          sn[r][c] = 0.5f * acc;
-        }
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) s[r][c] = sn[r][c];
-    }
-    bool finite = true;
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const float v = s[r][c];
-        finite = finite && isfinite(v);
-        Xout[((long long)i * D + r) * D + c] = v;
-        const double dd = (double)v - (double)x[r][c];
-        diff2 += dd * dd;
-      }
-    if (!finite) flags |= FLAG_NONFINITE;
-  }
+  if (i < n) block_update<D>(X, Y, Xout, i, n, eta, K, diff2, flags);
   if (flags) atomicOr(&ctl->flags, flags);
   const double bs = block_sum(diff2, sh);
   if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
@@ -244,30 +53,6 @@ __global__ void spec_v0_kernel(float* V, long long rows, int D) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     V[e] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
-  }
-}
-
-// Cholesky G = R^T R (R upper) and R^{-1}, float64, one thread, D <= 64.
-__device__ void chol_inv(const double* G, double* Rinv, int D, double* Rtmp) {
-  for (int j = 0; j < D; ++j) {
-    double s = G[j * D + j];
-    for (int k = 0; k < j; ++k) s -= Rtmp[k * D + j] * Rtmp[k * D + j];
-    const double rjj = sqrt(fmax(s, 1e-300));
-    Rtmp[j * D + j] = rjj;
-    for (int i = j + 1; i < D; ++i) {
-      double t = G[j * D + i];
-      for (int k = 0; k < j; ++k) t -= Rtmp[k * D + j] * Rtmp[k * D + i];
-      Rtmp[j * D + i] = t / rjj;
-    }
-    for (int i = 0; i < j; ++i) Rtmp[j * D + i] = 0.0;
-  }
-  // upper-triangular inverse by back substitution, column by column
-  for (int c = 0; c < D; ++c) {
-    for (int r = D - 1; r >= 0; --r) {
-      double t = (r == c) ? 1.0 : 0.0;
-      for (int k = r + 1; k < D; ++k) t -= Rtmp[r * D + k] * Rinv[k * D + c];
-      Rinv[r * D + c] = (r <= c) ? t / Rtmp[r * D + r] : 0.0;
-    }
   }
 }
 
