@@ -126,6 +126,11 @@ nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* p
 nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, double tol,
                                  double* residual, void* ws, size_t ws_bytes, void* st);
 
+/* The block product of Algorithm 2's gradient on its own: Y_i = sum_{j != i} A_ij X_j
+ * for every i, i.e. Y = A_off X (device, nd x d each, no overlap), streaming the
+ * packed A once.  Useful for power/subspace iterations built on this library. */
+nsrgs_status nsrgs_product(const nsrgs_A* A, const float* X, float* Y, void* ws, size_t ws_bytes, void* st);
+
 /* One iteration of Algorithm 2 for all blocks: X_out = NS_K(X_in - eta P(G)).
  * X_in and X_out (device, nd x d) must not overlap.  When `upd_norm` (device,
  * one double) is non-null it receives ||X_out - X_in||_F / sqrt(nd). */
@@ -195,6 +200,65 @@ size_t nsrgs_batch_workspace_bytes(const int* n, int count, int d);
 nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int count, int d, int storage, int T, int K,
                                double tol, int init, int spectral_max_iters, nsrgs_info* info, void* ws,
                                size_t ws_bytes, void* st);
+
+/* -------------------------------------------------------- served form */
+
+/* Continuous batching of solves (no counterpart in the paper beyond running
+ * Algorithm 2 per request).  A server holds `max_slots` slots and carves every
+ * admitted request's packed A and scratch out of a device arena that the
+ * caller allocates and keeps alive until nsrgs_server_destroy: admission is by
+ * arena (HBM) budget, in arrival order.  Each nsrgs_server_step admits what
+ * fits, replays `ticks_per_step` ticks of the batched form over all occupied
+ * slots (requests in their spectral phase and in their iterations share each
+ * tick), and retires every request that finished (update norm below its
+ * tolerance, T_max iterations, or a non-finite iterate); its X is then in the
+ * caller's buffer.  A server is used by one host thread at a time. */
+typedef struct nsrgs_server nsrgs_server;
+
+typedef struct nsrgs_server_config {
+  int d;                   /* block size of every request, 1..4 */
+  int storage;             /* NSRGS_F32, NSRGS_BF16 or NSRGS_FP8E4M3 */
+  int max_slots;           /* requests in flight at most */
+  int K;                   /* Newton-Schulz steps per iteration */
+  int spectral_max_iters;  /* subspace-iteration passes cap per request */
+  double spectral_tol;     /* subspace residual target (e.g. 1e-6) */
+  int ticks_per_step;      /* ticks per nsrgs_server_step call */
+} nsrgs_server_config;
+
+typedef struct nsrgs_server_result {
+  uint64_t id;             /* the id nsrgs_server_submit returned */
+  int status;              /* NSRGS_OK, NSRGS_ERR_NONFINITE or NSRGS_ERR_TIMEOUT */
+  int iters;               /* NS-RGS iterations run */
+  int spectral_iters;      /* spectral passes run */
+  double last_update_norm; /* ||X^{t+1} - X^t||_F / sqrt(nd) of the last iteration */
+  uint32_t flags;          /* as nsrgs_info.flags */
+} nsrgs_server_result;
+
+/* Bytes at the start of the arena that the server keeps for its slot table. */
+size_t nsrgs_server_table_bytes(int max_slots);
+
+/* Creates a server over `arena` (device, 256-byte aligned, arena_bytes long)
+ * working on stream `st`.  *out receives the handle (host object). */
+nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void* arena, size_t arena_bytes, void* st,
+                                 nsrgs_server** out);
+
+/* Queues a request: `upper` (device, float32 canonical upper-block list of an
+ * n-node instance, as for nsrgs_pack_upper) must stay valid until the request
+ * is admitted; X (device, nd x d) receives the result.  Iterations stop when
+ * the update norm falls below tol (> 0) or after T_max.  NSRGS_ERR_NOMEM when
+ * the request could never fit in the arena. */
+nsrgs_status nsrgs_server_submit(nsrgs_server* s, const float* upper, int n, float eta, int T_max, double tol,
+                                 float* X, uint64_t* id);
+
+/* Admits, runs ticks_per_step ticks, retires; synchronises `st`.  active and
+ * queued (nullable) receive the requests in flight and waiting afterwards. */
+nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* queued);
+
+/* Moves up to `max` finished results into out (host array); *count receives how many. */
+nsrgs_status nsrgs_server_poll(nsrgs_server* s, nsrgs_server_result* out, int max, int* count);
+
+/* Releases the server (not the arena, which the caller owns). */
+void nsrgs_server_destroy(nsrgs_server* s);
 
 /* d_F(X, Y) = min_{Q in O(d)} ||X - Y Q||_F (§1.4) for two nd x d device stacks,
  * with Q = sgn(Y^T X) from a float64 Jacobi SVD and float64 accumulation.

@@ -32,4 +32,7 @@ from ._lib import (  # noqa: F401
     nsrgs_batch_workspace_bytes,
     nsrgs_batch_solve,
     nsrgs_step_static,
+    Server,
+    nsrgs_product,
+    ServerResult,
 )

@@ -317,3 +317,101 @@ def nsrgs_batch_solve(
         fn(items, count, d, storage, T, K, tol, 1 if init else 0, spectral_max_iters, infos, _ptr(ws), ws.numel(), _stream())
     )
     return Xs, (list(infos) if infos is not None else None)
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("max_slots", ctypes.c_int),
+        ("K", ctypes.c_int),
+        ("spectral_max_iters", ctypes.c_int),
+        ("spectral_tol", ctypes.c_double),
+        ("ticks_per_step", ctypes.c_int),
+    ]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_uint64),
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("spectral_iters", ctypes.c_int),
+        ("last_update_norm", ctypes.c_double),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class Server:
+    """nsrgs_server_* over a caller-owned device arena (a torch uint8 tensor)."""
+
+    def __init__(self, d: int, storage: int, max_slots: int, arena_bytes: int, K: int = 2,
+                 spectral_max_iters: int = 60, spectral_tol: float = 1e-6, ticks_per_step: int = 4, device=None):
+        L = lib()
+        for name, res, args in [
+            ("nsrgs_server_table_bytes", ctypes.c_size_t, [ctypes.c_int]),
+            ("nsrgs_server_create", ctypes.c_int, [ctypes.POINTER(_ServerConfig), ctypes.c_void_p, ctypes.c_size_t,
+                                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+            ("nsrgs_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                                   ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                   ctypes.POINTER(ctypes.c_uint64)]),
+            ("nsrgs_server_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            ("nsrgs_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerResult), ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int)]),
+            ("nsrgs_server_destroy", None, [ctypes.c_void_p]),
+        ]:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        self._L = L
+        self.d = d
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=device or "cuda")
+        self._keep = {}
+        cfg = _ServerConfig(d, storage, max_slots, K, spectral_max_iters, spectral_tol, ticks_per_step)
+        h = ctypes.c_void_p(0)
+        _check(L.nsrgs_server_create(ctypes.byref(cfg), _ptr(self.arena), self.arena.numel(), _stream(), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, upper: torch.Tensor, n: int, eta: float, T_max: int, tol: float, X: torch.Tensor) -> int:
+        rid = ctypes.c_uint64(0)
+        _check(self._L.nsrgs_server_submit(self._h, _ptr(upper), n, eta, T_max, tol, _ptr(X), ctypes.byref(rid)))
+        self._keep[rid.value] = (upper, X)
+        return rid.value
+
+    def step(self) -> tuple[int, int]:
+        a, q = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self._L.nsrgs_server_step(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_results: int = 4096) -> list[ServerResult]:
+        out = (ServerResult * max_results)()
+        c = ctypes.c_int(0)
+        _check(self._L.nsrgs_server_poll(self._h, out, max_results, ctypes.byref(c)))
+        res = [out[i] for i in range(c.value)]
+        for r in res:
+            self._keep.pop(r.id, None)
+        return res
+
+    def close(self):
+        if self._h:
+            self._L.nsrgs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nsrgs_product(A: PackedA, X: torch.Tensor, Y: torch.Tensor | None = None, ws=None) -> torch.Tensor:
+    """Y = A_off X (Y_i = sum_{j != i} A_ij X_j), streaming the packed A once."""
+    if Y is None:
+        Y = torch.empty_like(X)
+    w = _ws(A, ws)
+    fn = lib().nsrgs_product
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(_A), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    a = A.struct()
+    _check(fn(ctypes.byref(a), _ptr(X), _ptr(Y), _ptr(w), w.numel(), _stream()))
+    return Y

@@ -322,6 +322,22 @@ nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, dou
   return NSRGS_OK;
 }
 
+nsrgs_status nsrgs_product(const nsrgs_A* A, const float* X, float* Y, void* ws, size_t ws_bytes, void* stv) {
+  PanelGeom g{};
+  nsrgs_status s = check_A(A, &g);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(X && Y && aligned16(X) && aligned16(Y), "X/Y must be 16-byte aligned device pointers");
+  const size_t bytes = (size_t)A->n * A->d * A->d * sizeof(float);
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, st));
+  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w.Y, w.ctl, &w.ctl->stop, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(Y, w.Y, bytes, cudaMemcpyDeviceToDevice, st));
+  return NSRGS_OK;
+}
+
 nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, float* X_out, double* upd_norm,
                         void* ws, size_t ws_bytes, void* stv) {
   PanelGeom g{};

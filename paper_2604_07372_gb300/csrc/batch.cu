@@ -28,10 +28,11 @@ namespace nsrgs {
 // ------------------------------------------------------------ the source
 struct BatchSrc {
   const BatchDesc* descs;
-  const long long* base;  // count + 1 entries: first global step of each instance
+  const long long* bases_;  // count + 1 entries: first global step of each instance
   int cnt;
   __device__ __forceinline__ int count() const { return cnt; }
-  __device__ __forceinline__ const long long* bases() const { return base; }
+  __device__ __forceinline__ int find(long long s) const { return find_first_leq(bases_, cnt, s); }
+  __device__ __forceinline__ long long base(int i) const { return bases_[i]; }
   __device__ __forceinline__ InstView view(int i) const {
     const BatchDesc& d = descs[i];
     const Ctl* c = d.ctl;
@@ -57,7 +58,7 @@ struct BatchSrc {
 
 template <int D, int RB, int ST>
 __global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_batch_kernel(BatchSrc src) {
-  panel_stream_body<D, RB, ST>(src, src.base[src.cnt]);
+  panel_stream_body<D, RB, ST>(src, src.base(src.cnt));
 }
 
 // ------------------------------------------------ per-instance CTA kernels

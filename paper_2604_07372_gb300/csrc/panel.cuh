@@ -221,11 +221,11 @@ struct Walk {
 // indices) of the global step range [g0, g1), in order.
 template <class Src, class Fn>
 __device__ __forceinline__ void for_segments(const Src& src, long long g0, long long g1, Fn&& fn) {
-  int inst = find_first_leq(src.bases(), src.count(), g0);
+  int inst = src.find(g0);
   long long s = g0;
   while (s < g1 && inst < src.count()) {
-    const long long base = src.bases()[inst];
-    const long long end = src.bases()[inst + 1];
+    const long long base = src.base(inst);
+    const long long end = src.base(inst + 1);
     const long long hi = end < g1 ? end : g1;
     if (hi > s) {
       const InstView v = src.view(inst);

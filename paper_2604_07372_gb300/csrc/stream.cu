@@ -15,20 +15,26 @@ struct StreamArgs {
 
 // One instance taken from the kernel parameters.
 struct SingleSrc {
-  InstView v;
-  long long b[2];
+  const StreamArgs* a;
   __device__ __forceinline__ int count() const { return 1; }
-  __device__ __forceinline__ const long long* bases() const { return b; }
-  __device__ __forceinline__ InstView view(int) const { return v; }
+  __device__ __forceinline__ int find(long long) const { return 0; }
+  __device__ __forceinline__ long long base(int i) const { return i == 0 ? 0 : a->g.total_steps; }
+  __device__ __forceinline__ InstView view(int) const {
+    InstView v;
+    v.packed = a->packed;
+    v.X = a->X;
+    v.Y = a->Y;
+    v.ctl = a->ctl;
+    v.g = a->g;
+    v.skip = false;
+    return v;
+  }
 };
 
 template <int D, int RB, int ST>
-__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kernel(StreamArgs a) {
+__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kernel(const __grid_constant__ StreamArgs a) {
   if (*a.skip) return;  // written only by earlier launches: uniform
-  SingleSrc src;
-  src.v = InstView{a.packed, a.X, a.Y, a.ctl, a.g, false};
-  src.b[0] = 0;
-  src.b[1] = a.g.total_steps;
+  SingleSrc src{&a};
   panel_stream_body<D, RB, ST>(src, a.g.total_steps);
 }
 

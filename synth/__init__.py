@@ -148,6 +148,38 @@ class Instance:
         return self.Z.reshape(self.n * self.d, self.d)
 
 
+def device_upper(n: int, d: int, sigma: float, seed: int, p: float = 1.0, device="cuda"):
+    """The same measurement model generated on a GPU with torch's seeded RNG.
+
+    Returns (Z (n, d, d) float32, canonical upper-block list (n(n-1)/2, d, d)
+    float32) as torch tensors on ``device``.  The random stream differs from
+    ``make_instance``'s NumPy stream (so results differ draw by draw, not in
+    distribution); it exists for workloads too large to build on the host
+    quickly (hundreds of instances, serving streams), where no oracle
+    comparison is made.
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    G = torch.randn((n, d, d), generator=g, device=device, dtype=torch.float64)
+    U, _, Vh = torch.linalg.svd(G)
+    Z = (U @ Vh).to(torch.float32)
+    iu, ju = torch.triu_indices(n, n, offset=1, device=device)
+    nb = iu.numel()
+    out = torch.empty((nb, d, d), dtype=torch.float32, device=device)
+    chunk = max(1, (1 << 24) // (d * d))
+    for s in range(0, nb, chunk):
+        e = min(nb, s + chunk)
+        blk = Z[iu[s:e]] @ Z[ju[s:e]].transpose(1, 2)
+        blk += sigma * torch.randn((e - s, d, d), generator=g, device=device, dtype=torch.float32)
+        if p < 1.0:
+            keep = torch.rand((e - s,), generator=g, device=device) < p
+            blk *= keep[:, None, None].to(blk.dtype)
+        out[s:e] = blk
+    return Z, out
+
+
 def make_instance(n: int, d: int, sigma: float, seed: int, p: float = 1.0, dtype=np.float64) -> Instance:
     if n < 2 or d < 1:
         raise ValueError("need n >= 2 and d >= 1")

@@ -41,6 +41,28 @@ def to64(t):
     return t.detach().double().cpu().numpy()
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8", "dense_f32"])
+@pytest.mark.parametrize("n,d", [(2, 3), (5, 2), (131, 3), (257, 4), (513, 1), (2000, 3), (1537, 4)])
+def test_product_matches_dense_matmul(P, n, d, storage):
+    """a2 alone: Y = A_off X through nsrgs_product vs the float64 product of the same stored values."""
+    inst = make(n, d, c=0.5, seed=n + 7 * d)
+    A = inst.dense()
+    for i in range(n):
+        A[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
+    X = np.random.default_rng(n).standard_normal((n * d, d)).astype(np.float32)
+    pa = packed(P, inst, P.STORAGE[storage])
+    Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    ref = A @ X.astype(np.float64)
+    scale = np.abs(A) @ np.abs(X.astype(np.float64))  # sum of |terms| per output
+    got = to64(Y)
+    if storage in ("f32", "dense_f32"):
+        assert np.all(np.abs(got - ref) <= 1e-6 * scale + 1e-6)
+    else:  # rounding of the stored A: 2^-8 (bf16) and 2^-4 relative per element (fp8, plus the row scale)
+        rel = {"bf16": 2.0**-8, "fp8": 2.0**-3}[storage]
+        assert np.all(np.abs(got - ref) <= rel * scale + 1e-5)
+
+
 STEP_CASES = [(2, 3), (3, 1), (5, 2), (130, 3), (200, 3), (257, 4), (131, 2), (513, 1), (700, 3), (1025, 4)]
 
 

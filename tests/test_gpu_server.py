@@ -1,0 +1,107 @@
+"""GPU tests of the served form (nsrgs_server_*): continuous batching.
+
+Requests arrive while others are in flight; each result must equal the same
+request solved alone (nsrgs_solve with the same tolerance) to
+d_F/sqrt(nd) <= 1e-5, and admission must respect slots and the arena budget.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2604_07372_gb300 as P
+
+    return P
+
+
+def to64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _requests(d, specs):
+    out = []
+    for k, (n, c, p) in enumerate(specs):
+        I = synth.make_instance(n, d, synth.sigma_rule(c, n, d), seed=500 + k, p=p, dtype=np.float32)
+        out.append(I)
+    return out
+
+
+def test_each_request_same_alone_and_in_the_mix(P):
+    d, tol, Tmax = 3, 1e-6, 400
+    specs = [(120, 0.3, 1.0), (300, 0.3, 1.0), (64, 0.2, 1.0), (500, 0.3, 0.5), (200, 0.4, 1.0),
+             (90, 0.3, 0.8), (257, 0.25, 1.0), (150, 0.3, 0.6), (333, 0.2, 1.0), (75, 0.35, 1.0)]
+    insts = _requests(d, specs)
+    ups = [torch.from_numpy(I.upper).cuda() for I in insts]
+    srv = P.Server(d, P.F32, max_slots=4, arena_bytes=256 << 20, ticks_per_step=3)
+    Xs = [torch.empty(I.n * d, d, device="cuda") for I in insts]
+    ids = {}
+    done = {}
+    # staggered arrivals: two new requests before every step
+    pending = list(range(len(insts)))
+    steps = 0
+    while (pending or len(done) < len(insts)) and steps < 2000:
+        for _ in range(2):
+            if pending:
+                k = pending.pop(0)
+                ids[srv.submit(ups[k], insts[k].n, 1.0 / insts[k].n, Tmax, tol, Xs[k])] = k
+        active, queued = srv.step()
+        assert active <= 4
+        for r in srv.poll():
+            done[ids[r.id]] = r
+        steps += 1
+    assert len(done) == len(insts)
+    torch.cuda.synchronize()
+    for k, I in enumerate(insts):
+        r = done[k]
+        assert r.status == 0 and r.last_update_norm < tol, (k, r.status, r.iters, r.last_update_norm)
+        pa = P.nsrgs_pack_upper(ups[k], I.n, d, P.F32)
+        Xa, ia = P.nsrgs_solve(pa, 1.0 / I.n, Tmax, 2, tol=tol, spectral_max_iters=60)
+        torch.cuda.synchronize()
+        assert abs(r.iters - ia.iters) <= 1
+        assert O.dF(to64(Xs[k]), to64(Xa), d) / math.sqrt(I.n * d) <= 1e-5
+    srv.close()
+
+
+def test_admission_respects_the_arena_budget(P):
+    d = 4
+    insts = _requests(d, [(700, 0.3, 1.0), (700, 0.3, 1.0), (700, 0.3, 1.0)])
+    ups = [torch.from_numpy(I.upper).cuda() for I in insts]
+    one = P.nsrgs_packed_bytes(700, d, P.BF16) + 4 * (700 * d + 64) * d * 4 + 8192
+    table = P.lib().nsrgs_server_table_bytes(8)
+    srv = P.Server(d, P.BF16, max_slots=8, arena_bytes=table + 256 * 8 + int(1.6 * one), ticks_per_step=2)
+    Xs = [torch.empty(700 * d, d, device="cuda") for _ in insts]
+    for k, I in enumerate(insts):
+        srv.submit(ups[k], I.n, 1.0 / I.n, 50, 1e-6, Xs[k])
+    active, queued = srv.step()
+    assert active == 1 and queued == 2  # only one request fits at a time
+    finished = []
+    for _ in range(500):
+        active, queued = srv.step()
+        finished += srv.poll()
+        assert active <= 1
+        if len(finished) == 3:
+            break
+    assert len(finished) == 3 and all(r.status == 0 for r in finished)
+    srv.close()
+
+
+def test_request_that_can_never_fit_is_refused(P):
+    srv = P.Server(3, P.F32, max_slots=2, arena_bytes=4 << 20)
+    n = 1200  # packed A alone is ~26 MB
+    I = synth.make_instance(n, 3, 1.0, seed=1, dtype=np.float32)
+    with pytest.raises(P.NsrgsError) as e:
+        srv.submit(torch.from_numpy(I.upper).cuda(), n, 1.0 / n, 10, 0.0, torch.empty(3 * n, 3, device="cuda"))
+    assert e.value.status == 3
+    srv.close()
