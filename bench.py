@@ -175,6 +175,174 @@ def cpu_oracle_iterations(inst, args, iters: int, budget_s: float = 25.0):
     return times, build_s, cores
 
 
+# ------------------------------------------------------------ batched leg
+def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, reps: int = 2, seq_subset: int = 64):
+    """512 independent instances, n ~ U[50, 2000], d = 3, c ~ U[0.1, 0.5], own seeds,
+    spectral start + T = 60 iterations, one graph-replayed batch launch sequence."""
+    import numpy as np
+    import torch
+
+    d = 3
+    rng = np.random.default_rng(seed)
+    ns = [int(x) for x in rng.integers(50, 2001, count)]
+    cs = rng.uniform(0.1, 0.5, count)
+    t0 = time.perf_counter()
+    packs = {P.F32: [], P.BF16: [], P.FP8E4M3: []}
+    Zs = []
+    for k, n in enumerate(ns):
+        Z, up = synth.device_upper(n, d, synth.sigma_rule(float(cs[k]), n, d), seed=seed + 1 + k)
+        for st in packs:
+            packs[st].append(P.nsrgs_pack_upper(up, n, d, st))
+        Zs.append(Z.reshape(n * d, d))
+        del up
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    etas = [1.0 / n for n in ns]
+    out = {"instances": count, "n_range": [50, 2000], "T": T, "K": K, "generation_s": gen_s}
+    dF = {}
+    for st, name in ((P.BF16, "bf16"), (P.FP8E4M3, "fp8"), (P.F32, "f32")):
+        ws = torch.empty(P.nsrgs_batch_workspace_bytes(ns, d), dtype=torch.uint8, device="cuda")
+        Xs = [torch.empty(n * d, d, device="cuda") for n in ns]
+        P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        bytes_A = sum(p.nbytes for p in packs[st])
+        dF[name] = np.array([P.nsrgs_dF(X, Z, n, d, ws=None) for X, Z, n in zip(Xs, Zs, ns)])
+        out[name] = {"solves_per_s": count / sec, "batch_ms": 1e3 * sec, "packed_GB": bytes_A / 1e9}
+        del ws
+    for name in ("bf16", "fp8"):
+        rel = np.abs(dF[name] - dF["f32"]) / dF["f32"]
+        out[name]["dF_rel_vs_f32_max"] = float(rel.max())
+        out[name]["dF_rel_vs_f32_mean"] = float(rel.mean())
+    # plain sequential form: one nsrgs_solve per instance (float32, single-instance path)
+    sub = list(range(seq_subset))
+    ws1 = P.workspace(max(ns[k] for k in sub), d)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in sub:
+        n = ns[k]
+        X = torch.empty(n * d, d, device="cuda")
+        P.nsrgs_solve(packs[P.F32][k], 1.0 / n, T, K, init=True, spectral_max_iters=SMAX, X=X,
+                      ws=ws1[: P.nsrgs_workspace_bytes(n, d)], info=False)
+    torch.cuda.synchronize()
+    seq = (time.perf_counter() - t) / len(sub)
+    out["sequential_f32_single_instance"] = {"solves_per_s": 1.0 / seq, "sample": f"first {len(sub)} instances, one nsrgs_solve each (graph capture included)"}
+    return out
+
+
+# ------------------------------------------------------------ serving leg
+def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0, pool_per_d: int = 16,
+                tol: float = 1e-6, T_max: int = 1000, slots: int = 48):
+    """Poisson arrivals (rate req/s) of requests n ~ log-U[100, 8000], d in {3, 4}, half
+    dense and half block-sparse (pair kept with p ~ U[0.05, 0.5]); continuous batching
+    with BF16 storage; a request retires when its update norm falls below 1e-6 (cap T_max)."""
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(seed)
+    pool = []
+    t0 = time.perf_counter()
+    for d in (3, 4):
+        for k in range(pool_per_d):
+            n = int(round(math.exp(rng.uniform(math.log(100), math.log(8000)))))
+            sparse = (k % 2) == 1
+            p = float(rng.uniform(0.05, 0.5)) if sparse else 1.0
+            _, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + 100 * d + k, p=p)
+            pool.append({"n": n, "d": d, "p": p, "upper": up})
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    servers = {d: P.Server(d, P.BF16, max_slots=slots, arena_bytes=24 << 30, K=2, spectral_max_iters=SMAX,
+                           spectral_tol=1e-6, ticks_per_step=4) for d in (3, 4)}
+    # arrival schedule
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        arrivals.append((t, int(rng.integers(0, len(pool)))))
+    outs = {}
+    lat = []
+    iters = []
+    meta = {}
+    nxt = 0
+    done = 0
+    start = time.perf_counter()
+    last_finish = 0.0
+    while done < len(arrivals):
+        now = time.perf_counter() - start
+        while nxt < len(arrivals) and arrivals[nxt][0] <= now:
+            ta, k = arrivals[nxt]
+            q = pool[k]
+            X = torch.empty(q["n"] * q["d"], q["d"], device="cuda")
+            rid = servers[q["d"]].submit(q["upper"], q["n"], 1.0 / q["n"], T_max, tol, X)
+            meta[(q["d"], rid)] = (ta, X)
+            nxt += 1
+        busy = False
+        for d, srv in servers.items():
+            a, qd = srv.step()
+            busy = busy or a > 0 or qd > 0
+            for r in srv.poll():
+                ta, X = meta.pop((d, r.id))
+                fin = time.perf_counter() - start
+                lat.append(fin - ta)
+                iters.append(r.iters)
+                last_finish = max(last_finish, fin)
+                done += 1
+        if not busy and nxt < len(arrivals):
+            wait = arrivals[nxt][0] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(min(wait, 0.002))
+    for srv in servers.values():
+        srv.close()
+    lat = np.array(lat)
+    res = {
+        "requests": len(arrivals),
+        "offered_rate_per_s": rate,
+        "solves_per_s": len(arrivals) / last_finish,
+        "p50_ms": float(1e3 * np.percentile(lat, 50)),
+        "p99_ms": float(1e3 * np.percentile(lat, 99)),
+        "mean_iters": float(np.mean(iters)),
+        "max_iters": int(np.max(iters)),
+        "pool": f"{len(pool)} distinct requests (device-generated), n log-uniform [100, 8000], d in {{3, 4}}, half block-sparse",
+        "generation_s": gen_s,
+        "storage": "bf16",
+    }
+    # plain sequential FP32 form: one request at a time (single-instance solve), same arrivals
+    solve_s = {}
+    for k, q in enumerate(pool):
+        pa = P.nsrgs_pack_upper(q["upper"], q["n"], q["d"], P.F32)
+        ws = P.workspace(q["n"], q["d"])
+        X = torch.empty(q["n"] * q["d"], q["d"], device="cuda")
+        P.nsrgs_solve(pa, 1.0 / q["n"], T_max, 2, tol=tol, spectral_max_iters=SMAX, X=X, ws=ws, info=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        P.nsrgs_solve(pa, 1.0 / q["n"], T_max, 2, tol=tol, spectral_max_iters=SMAX, X=X, ws=ws, info=False)
+        torch.cuda.synchronize()
+        solve_s[k] = time.perf_counter() - t
+        del pa, ws
+    free_at = 0.0
+    lat_seq = []
+    for ta, k in arrivals:
+        st = max(ta, free_at)
+        free_at = st + solve_s[k]
+        lat_seq.append(free_at - ta)
+    lat_seq = np.array(lat_seq)
+    res["sequential_f32"] = {
+        "solves_per_s": len(arrivals) / free_at,
+        "p50_ms": float(1e3 * np.percentile(lat_seq, 50)),
+        "p99_ms": float(1e3 * np.percentile(lat_seq, 99)),
+        "note": "each pool request's solve time measured alone (graph cached), then the same arrival sequence queued FIFO",
+    }
+    return res
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -419,6 +587,17 @@ def run_ours(args, world, rank, local):
         except Exception as e:  # pragma: no cover - reported, not fatal
             extras["plain_dense_f32"] = {"error": str(e)[:200]}
         line["extras"] = extras
+        packs.clear()
+        torch.cuda.empty_cache()
+        # batched and served forms (the metric's second half)
+        for key, fn in (("batched", batched_leg), ("serving", serving_leg)):
+            try:
+                t = time.perf_counter()
+                line[key] = fn(P, synth, seed=args.seed + (1 if key == "batched" else 2))
+                line[key]["leg_wall_s"] = time.perf_counter() - t
+            except Exception as e:  # reported in the line, the main metric stands
+                line[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+            torch.cuda.empty_cache()
         # CPU oracle on the host cores, bounded sample
         try:
             times, build_s, cores = cpu_oracle_iterations(inst, args, 3)

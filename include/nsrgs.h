@@ -260,6 +260,15 @@ nsrgs_status nsrgs_server_poll(nsrgs_server* s, nsrgs_server_result* out, int ma
 /* Releases the server (not the arena, which the caller owns). */
 void nsrgs_server_destroy(nsrgs_server* s);
 
+/* The comparison method of the paper (§1.1, §4.1), the generalised power
+ * method, on the same A stream: X_i <- sgn(sum_j A_ij X_j) with A_ii = I, the
+ * sign computed exactly per block (float32 one-sided Jacobi SVD).  Same start,
+ * stop rule, graph replay and info as nsrgs_solve; the paper cites GPM but
+ * does not write it out, so this is the reading stated above.  A baseline:
+ * NS-RGS replaces exactly this per-block SVD with K Newton-Schulz products. */
+nsrgs_status nsrgs_gpm_solve(const nsrgs_A* A, int T, double tol, int init, int spectral_max_iters, float* X,
+                             nsrgs_info* info, void* ws, size_t ws_bytes, void* st);
+
 /* d_F(X, Y) = min_{Q in O(d)} ||X - Y Q||_F (§1.4) for two nd x d device stacks,
  * with Q = sgn(Y^T X) from a float64 Jacobi SVD and float64 accumulation.
  * `out` is a host double; the call synchronises `st`. */

@@ -34,5 +34,6 @@ from ._lib import (  # noqa: F401
     nsrgs_step_static,
     Server,
     nsrgs_product,
+    nsrgs_gpm_solve,
     ServerResult,
 )

@@ -415,3 +415,20 @@ def nsrgs_product(A: PackedA, X: torch.Tensor, Y: torch.Tensor | None = None, ws
     a = A.struct()
     _check(fn(ctypes.byref(a), _ptr(X), _ptr(Y), _ptr(w), w.numel(), _stream()))
     return Y
+
+
+def nsrgs_gpm_solve(A: PackedA, T: int, tol: float = 0.0, init: bool = True, spectral_max_iters: int = 50,
+                    X: torch.Tensor | None = None, ws=None, info: bool = True):
+    """Generalised power method baseline on the same A stream; returns (X, Info or None)."""
+    if X is None:
+        X = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    a = A.struct()
+    inf = Info() if info else None
+    fn = lib().nsrgs_gpm_solve
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(_A), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                   ctypes.POINTER(Info), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    _check(fn(ctypes.byref(a), T, tol, 1 if init else 0, spectral_max_iters, _ptr(X),
+              ctypes.byref(inf) if inf is not None else None, _ptr(w), w.numel(), _stream()))
+    return X, inf

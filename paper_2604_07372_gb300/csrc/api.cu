@@ -35,6 +35,7 @@ cudaError_t stream_panel_prepare(const PanelGeom& g);
 
 int reduce_grid(long long rows);
 cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, double, Ctl*, double*, cudaStream_t);
+cudaError_t launch_gpm_epilogue(const float*, float*, float*, int, int, double, Ctl*, cudaStream_t);
 cudaError_t launch_spec_v0(float*, long long, int, cudaStream_t);
 cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
                              cudaStream_t);
@@ -44,6 +45,7 @@ cudaError_t launch_polar_blocks(const float*, float*, int, int, cudaStream_t);
 cudaError_t launch_dF(const float*, const float*, long long, int, const SpecScratch&, Ctl*, cudaStream_t);
 cudaError_t launch_copy_out(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
 cudaError_t launch_select_copy(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
+cudaError_t generic_prepare(int d);
 
 constexpr int kMaxReduceGrid = 512;
 constexpr int kMaxSmallD = 8;
@@ -97,11 +99,10 @@ static nsrgs_status check_nd(int n, int d) {
   return NSRGS_OK;
 }
 
+// Every d in [1, 64] has per-block kernels: registers for d <= 8, shared memory
+// (generic.cu) above; their launch attributes are set here, outside any capture.
 static nsrgs_status check_small_d(int d) {
-  if (d > kMaxSmallD) {
-    set_error("per-block kernels of this build cover d <= 8");
-    return NSRGS_ERR_UNSUPPORTED;
-  }
+  if (d > kMaxSmallD) NSRGS_CUDA_TRY(generic_prepare(d));
   return NSRGS_OK;
 }
 
@@ -174,8 +175,11 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
   return launch_polar_blocks(w.W, out, n, d, st);
 }
 
+enum { METHOD_NSRGS = 0, METHOD_GPM = 1 };
+
 static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
-                                      int K, double tol, cudaStream_t st, const cudaEvent_t* ev = nullptr) {
+                                      int K, double tol, int method, cudaStream_t st,
+                                      const cudaEvent_t* ev = nullptr) {
   cudaError_t e;
   for (int t = 0; t < T; ++t) {
     const float* Xt = w.X[t & 1];
@@ -183,7 +187,11 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = stream_AX(A, g, Xt, w.Y, w.ctl, &w.ctl->stop, st)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st)) != cudaSuccess) return e;
+    if (method == METHOD_GPM)
+      e = launch_gpm_epilogue(Xt, w.Y, Xn, A->n, A->d, tol, w.ctl, st);
+    else
+      e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -200,6 +208,7 @@ struct GraphKey {
   float* X;
   void* ws;
   int timing;
+  int method;
   bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -361,12 +370,31 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
   return NSRGS_OK;
 }
 
+static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
+                               int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
+                               void* stv, int method);
+
 nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, int init, int spectral_max_iters,
                          float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  return solve_impl(A, eta, T, K, tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv, METHOD_NSRGS);
+}
+
+nsrgs_status nsrgs_gpm_solve(const nsrgs_A* A, int T, double tol, int init, int spectral_max_iters, float* X,
+                             nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  return solve_impl(A, 1.0f, T, 0, tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv, METHOD_GPM);
+}
+
+static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
+                               int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
+                               void* stv, int method) {
   PanelGeom g{};
   nsrgs_status s = check_A(A, &g);
   if (s != NSRGS_OK) return s;
   if ((s = check_small_d(A->d)) != NSRGS_OK) return s;
+  if (method == METHOD_GPM && A->d > kMaxSmallD) {
+    set_error("the GPM baseline covers d <= 8");
+    return NSRGS_ERR_UNSUPPORTED;
+  }
   if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
   NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
   NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");
@@ -398,6 +426,7 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
   key.X = X;
   key.ws = ws;
   key.timing = g_timing;
+  key.method = method;
 
   cudaGraphExec_t exec = nullptr;
   int kernel_nodes = 0;
@@ -426,7 +455,7 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
       if (init) e = enqueue_spectral(A, g, w, spectral_max_iters, 1e-6, w.X[0], cs);
       else e = cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, cs);
     }
-    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, cs, ev);
+    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, method, cs, ev);
     if (e == cudaSuccess) e = launch_copy_out(w.X[0], w.X[1], X, (long long)n * d * d, w.ctl, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

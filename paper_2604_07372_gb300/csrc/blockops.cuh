@@ -75,6 +75,70 @@ __device__ inline void polar_fp64(const double (&M)[D][D], double (&Q)[D][D]) {
     }
 }
 
+// Same one-sided Jacobi in float32 (the GPU baseline of the generalised power
+// method uses a float32 batched per-block SVD, like the float32 NS-RGS path).
+template <int D>
+__device__ inline void polar_fp32(const float (&M)[D][D], float (&Q)[D][D]) {
+  float U[D][D], V[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      U[r][c] = M[r][c];
+      V[r][c] = (r == c) ? 1.f : 0.f;
+    }
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    float off = 0.f;
+#pragma unroll
+    for (int p = 0; p < D - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < D; ++q) {
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          al = fmaf(U[r][p], U[r][p], al);
+          be = fmaf(U[r][q], U[r][q], be);
+          ga = fmaf(U[r][p], U[r][q], ga);
+        }
+        const float nrm = sqrtf(al * be);
+        if (nrm == 0.f || fabsf(ga) <= 1e-8f * nrm) continue;
+        off = fmaxf(off, fabsf(ga) / nrm);
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = rsqrtf(1.f + t * t);
+        const float s = c * t;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          const float up = U[r][p], uq = U[r][q];
+          U[r][p] = c * up - s * uq;
+          U[r][q] = s * up + c * uq;
+          const float vp = V[r][p], vq = V[r][q];
+          V[r][p] = c * vp - s * vq;
+          V[r][q] = s * vp + c * vq;
+        }
+      }
+    if (off < 1e-7f) break;
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < D; ++r) s2 = fmaf(U[r][c], U[r][c], s2);
+    const float inv = s2 > 0.f ? rsqrtf(s2) : 0.f;
+#pragma unroll
+    for (int r = 0; r < D; ++r) U[r][c] *= inv;
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fmaf(U[r][k], V[c][k], acc);
+      Q[r][c] = acc;
+    }
+}
+
 // ------------------------------------------------- block reductions (fp64)
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -1,0 +1,371 @@
+// Per-block d x d work for block sizes above 8 (runtime d <= 64): one CTA per
+// block with the d x d matrices in shared memory.  Same arithmetic as the
+// register kernels of small.cu:
+//   * iteration epilogue (Algorithm 2's loop body, §2.2 projection, Algorithm 1);
+//   * spectral subspace step (float64 Gram / Cholesky / V <- W R^{-1} / residual);
+//   * exact blockwise sign for X^0 and for d_F: Newton-Schulz run to convergence in
+//     float64 on M / ||M||_F (all singular values in (0, 1], so the iteration
+//     converges to the polar factor U V^T of any full-rank M);
+//   * d_F(X, Y) (§1.4).
+#include <math.h>
+
+#include "blockops.cuh"
+
+namespace nsrgs {
+
+// C = alpha * op(A) * B + beta * C0 for D x D row-major matrices in shared memory
+// (op(A) = A or A^T); every thread computes a strided subset of the entries.
+template <typename T>
+__device__ void cta_mm(const T* A, bool transA, const T* B, T* C, int D, T alpha, const T* C0, T beta) {
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+    const int r = e / D, c = e % D;
+    T acc = 0;
+    for (int k = 0; k < D; ++k) acc += (transA ? A[k * D + r] : A[r * D + k]) * B[k * D + c];
+    C[e] = alpha * acc + (C0 ? beta * C0[e] : T(0));
+  }
+}
+
+// ------------------------------------------------------------ epilogue
+// Dynamic shared memory: 5 D x D float matrices.
+__global__ void __launch_bounds__(256) epilogue_generic_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                                               float* __restrict__ Xout, int n, int D, float eta,
+                                                               int K, double tol, Ctl* ctl, double* upd_out) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double sh[32];
+  if (ctl->stop) return;
+  const int DD = D * D;
+  float* x = sm;
+  float* g = sm + DD;
+  float* t = sm + 2 * DD;
+  float* s = sm + 3 * DD;
+  float* m = sm + 4 * DD;
+  const long long base = (long long)blockIdx.x * DD;
+  const float nm1 = (float)(n - 1);
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+    x[e] = X[base + e];
+    g[e] = nm1 * x[e] - Y[base + e];
+    Y[base + e] = 0.f;
+  }
+  __syncthreads();
+  cta_mm<float>(g, true, x, t, D, 1.f, nullptr, 0.f);  // t = G^T X
+  __syncthreads();
+  cta_mm<float>(x, false, t, m, D, 1.f, nullptr, 0.f);  // m = X G^T X
+  __syncthreads();
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) s[e] = x[e] - 0.5f * eta * (g[e] - m[e]);  // F
+  __syncthreads();
+  // Lemma 2.1 precondition (||I - F^T F||_F >= 1 flags it)
+  cta_mm<float>(s, true, s, m, D, 1.f, nullptr, 0.f);
+  __syncthreads();
+  double e2 = 0.0;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+    const double v = ((e / D == e % D) ? 1.0 : 0.0) - (double)m[e];
+    e2 += v * v;
+  }
+  e2 = block_sum(e2, sh);
+  if (threadIdx.x == 0 && !(e2 < 1.0)) atomicOr(&ctl->flags, FLAG_NS_PRECOND);
+  for (int k = 0; k < K; ++k) {
+    __syncthreads();
+    cta_mm<float>(s, true, s, m, D, 1.f, nullptr, 0.f);  // S^T S
+    __syncthreads();
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) m[e] = ((e / D == e % D) ? 3.f : 0.f) - m[e];
+    __syncthreads();
+    cta_mm<float>(s, false, m, g, D, 0.5f, nullptr, 0.f);  // S (3I - S^T S) / 2
+    __syncthreads();
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) s[e] = g[e];
+  }
+  __syncthreads();
+  double diff2 = 0.0;
+  bool finite = true;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+    finite = finite && isfinite(s[e]);
+    Xout[base + e] = s[e];
+    const double dd = (double)s[e] - (double)x[e];
+    diff2 += dd * dd;
+  }
+  if (!finite) atomicOr(&ctl->flags, FLAG_NONFINITE);
+  const double bs = block_sum(diff2, sh);
+  if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&ctl->upd_acc, 0.0);
+      const double un = sqrt(tot / ((double)n * D));
+      ctl->last_upd = un;
+      ctl->iters_done += 1;
+      if (tol > 0.0 && un < tol) ctl->stop = 1;
+      ctl->upd_acc = 0.0;
+      ctl->counter = 0u;
+      if (upd_out) *upd_out = un;
+    }
+  }
+}
+
+// ------------------------------------------------- exact sign (float64)
+// S <- M / ||M||_F, then S <- S (3I - S^T S)/2 until ||I - S^T S||_F < 1e-14.
+// Shared scratch: 3 D x D doubles (S, T, U).  Result in S.
+__device__ void cta_polar_ns64(const double* M, double* S, double* T, double* U, int D, double* sh) {
+  const int DD = D * D;
+  double f2 = 0.0;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) f2 += M[e] * M[e];
+  f2 = block_sum(f2, sh);
+  __shared__ double s_norm;
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_norm = f2 > 0.0 ? 1.0 / sqrt(f2) : 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) S[e] = M[e] * s_norm;
+  for (int it = 0; it < 100; ++it) {
+    __syncthreads();
+    cta_mm<double>(S, true, S, T, D, 1.0, nullptr, 0.0);  // S^T S
+    __syncthreads();
+    double err = 0.0;
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+      const double v = ((e / D == e % D) ? 1.0 : 0.0) - T[e];
+      err += v * v;
+      T[e] = ((e / D == e % D) ? 3.0 : 0.0) - T[e];
+    }
+    err = block_sum(err, sh);
+    // converged to rounding level (a few ulps times d), or out of iterations
+    if (threadIdx.x == 0) s_done = (err < 16.0 * D * D * 4.9e-32) || (it == 99);
+    __syncthreads();
+    if (s_done) break;
+    cta_mm<double>(S, false, T, U, D, 0.5, nullptr, 0.0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) S[e] = U[e];
+  }
+  __syncthreads();
+}
+
+// X0_i = sgn(V_i), CTA per block.  Dynamic shared memory: 4 D x D doubles.
+__global__ void __launch_bounds__(256) polar_generic_kernel(const float* __restrict__ V, float* __restrict__ X0, int D) {
+  extern __shared__ __align__(16) double smd[];
+  __shared__ double sh[32];
+  const int DD = D * D;
+  double* M = smd;
+  const long long base = (long long)blockIdx.x * DD;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) M[e] = V[base + e];
+  __syncthreads();
+  cta_polar_ns64(M, smd + DD, smd + 2 * DD, smd + 3 * DD, D, sh);
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) X0[base + e] = (float)smd[DD + e];
+}
+
+// ----------------------------------------------------- Gram reductions
+// Partial sums over a chunk of rows of P^T Q (and, when W_out is given,
+// W = Y + shift V first: then P = W, Q = W and a second product V^T W).
+// Outputs o in [0, nout): o < D*D -> (P^T Q)[o]; o >= D*D -> (V^T W)[o - D*D].
+constexpr int kRowsPerCta = 64;
+
+__global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restrict__ V, float* __restrict__ Yv,
+                                                           float* __restrict__ W, const float* __restrict__ Xq,
+                                                           long long rows, int D, float shift, int mode,
+                                                           SpecScratch s, Ctl* ctl) {
+  // mode 0: spectral Gram (W = Y + shift V; outputs W^T W and V^T W); mode 1: M = Yv^T Xq.
+  extern __shared__ __align__(16) float smg[];
+  if (mode == 0 && ctl->spec_stop) return;
+  const int DD = D * D;
+  const int nout = mode == 0 ? 2 * DD : DD;
+  float* P = smg;                     // kRowsPerCta x D
+  float* Q = smg + kRowsPerCta * D;   // kRowsPerCta x D
+  double acc[32];  // outputs o = threadIdx.x + k * 256, k < nout / 256 <= 2 * 64 * 64 / 256
+  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+  for (long long r0 = (long long)blockIdx.x * kRowsPerCta; r0 < rows; r0 += (long long)gridDim.x * kRowsPerCta) {
+    const int nr = (int)min((long long)kRowsPerCta, rows - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * D; e += blockDim.x) {
+      const long long ge = r0 * D + e;
+      if (mode == 0) {
+        const float v = V[ge];
+        const float w = Yv[ge] + shift * v;
+        W[ge] = w;
+        Yv[ge] = 0.f;
+        P[e] = v;
+        Q[e] = w;
+      } else {
+        P[e] = Yv[ge];
+        Q[e] = Xq[ge];
+      }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x, ++k) {
+      const int oo = o % DD;
+      const int a = oo / D, b = oo % D;
+      double sum = 0.0;
+      if (mode == 0 && o < DD) {
+        for (int r = 0; r < nr; ++r) sum += (double)Q[r * D + a] * (double)Q[r * D + b];
+      } else {
+        for (int r = 0; r < nr; ++r) sum += (double)P[r * D + a] * (double)Q[r * D + b];
+      }
+      acc[k] += sum;
+    }
+  }
+  double* part = s.partials + (long long)blockIdx.x * nout;
+  {
+    int k = 0;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x, ++k) part[o] = acc[k];
+  }
+  if (last_block(&ctl->counter)) {
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      double a = 0.0;
+      for (unsigned int bb = 0; bb < gridDim.x; ++bb) a += s.partials[(long long)bb * nout + o];
+      if (mode == 0) {
+        if (o < DD) s.WW[o] = a; else s.H[o - DD] = a;
+      } else {
+        s.M[o] = a;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (mode == 0) {
+        double h2 = 0.0;
+        for (int o = 0; o < DD; ++o) h2 += s.H[o] * s.H[o];
+        s.scal[0] = h2;
+        chol_inv(s.WW, s.Rinv, D, s.Q);  // s.Q as Cholesky scratch here
+        s.scal[2] = 0.0;
+      } else {
+        s.scal[1] = 0.0;
+      }
+      ctl->counter = 0u;
+    }
+  }
+}
+
+// Vnew = W Rinv and the residual ||W - V H||^2 (thread per row); the last CTA
+// finishes ||A V - V H||_F / ||H||_F.  Dynamic shared memory: Rinv and H (float64).
+__global__ void __launch_bounds__(256) update_generic_kernel(const float* __restrict__ V, const float* __restrict__ W,
+                                                             float* __restrict__ Vnew, long long rows, int D,
+                                                             SpecScratch s, double tol, int count_pass, Ctl* ctl) {
+  extern __shared__ __align__(16) double smu[];
+  __shared__ double sh[32];
+  if (ctl->spec_stop) return;
+  const int DD = D * D;
+  double* rinv = smu;
+  double* hh = smu + DD;
+  for (int o = threadIdx.x; o < DD; o += blockDim.x) {
+    rinv[o] = s.Rinv[o];
+    hh[o] = s.H[o];
+  }
+  __syncthreads();
+  double res = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+    const float* w = W + r * D;
+    const float* v = V + r * D;
+    for (int c = 0; c < D; ++c) {
+      double nv = 0.0, vh = 0.0;
+      for (int k = 0; k < D; ++k) {
+        nv += (double)w[k] * rinv[k * D + c];
+        vh += (double)v[k] * hh[k * D + c];
+      }
+      Vnew[r * D + c] = (float)nv;
+      const double e = (double)w[c] - vh;
+      res += e * e;
+    }
+  }
+  const double bs = block_sum(res, sh);
+  if (threadIdx.x == 0) atomicAdd(&s.scal[2], bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&s.scal[2], 0.0);
+      ctl->counter = 0u;
+      if (count_pass) {
+        const double rel = sqrt(tot / fmax(s.scal[0], 1e-300));
+        ctl->spec_res = rel;
+        ctl->spec_iters += 1;
+        if (rel <= tol) ctl->spec_stop = 1;
+      }
+    }
+  }
+}
+
+// Q = sgn(M) for the d_F minimiser (one CTA).  Dynamic shared memory: 4 D x D doubles.
+__global__ void __launch_bounds__(256) polar_single_kernel(SpecScratch s, int D) {
+  extern __shared__ __align__(16) double smp[];
+  __shared__ double sh[32];
+  const int DD = D * D;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) smp[e] = s.M[e];
+  __syncthreads();
+  cta_polar_ns64(smp, smp + DD, smp + 2 * DD, smp + 3 * DD, D, sh);
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) s.Q[e] = smp[DD + e];
+}
+
+__global__ void __launch_bounds__(256) dist_generic_kernel(const float* __restrict__ X, const float* __restrict__ Yv,
+                                                           long long rows, int D, SpecScratch s, Ctl* ctl) {
+  extern __shared__ __align__(16) double smq[];
+  __shared__ double sh[32];
+  const int DD = D * D;
+  for (int o = threadIdx.x; o < DD; o += blockDim.x) smq[o] = s.Q[o];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+    for (int c = 0; c < D; ++c) {
+      double yq = 0.0;
+      for (int k = 0; k < D; ++k) yq += (double)Yv[r * D + k] * smq[k * D + c];
+      const double e = (double)X[r * D + c] - yq;
+      acc += e * e;
+    }
+  }
+  const double bs = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(&s.scal[1], bs);
+  if (last_block(&ctl->counter))
+    if (threadIdx.x == 0) ctl->counter = 0u;
+}
+
+// ------------------------------------------------------------- launchers
+int reduce_grid(long long rows);
+
+static cudaError_t set_smem(const void* k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t generic_prepare(int d) {
+  cudaError_t e;
+  if ((e = set_smem((const void*)epilogue_generic_kernel, 5 * d * d * sizeof(float))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)polar_generic_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)polar_single_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)update_generic_kernel, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)dist_generic_kernel, d * d * sizeof(double))) != cudaSuccess) return e;
+  return set_smem((const void*)gram_generic_kernel, 2 * kRowsPerCta * d * sizeof(float));
+}
+
+static int gram_grid(long long rows) {
+  long long g = (rows + kRowsPerCta - 1) / kRowsPerCta;
+  return (int)(g < 256 ? (g < 1 ? 1 : g) : 256);
+}
+
+cudaError_t launch_epilogue_generic(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, double tol,
+                                    Ctl* ctl, double* upd_out, cudaStream_t st) {
+  epilogue_generic_kernel<<<n, 256, 5 * d * d * sizeof(float), st>>>(X, Y, Xout, n, d, eta, K, tol, ctl, upd_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_gram_generic(const float* V, float* Y, float* W, long long rows, int d, float shift,
+                                     const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(float), st>>>(V, Y, W, nullptr, rows, d,
+                                                                                        shift, 0, s, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_update_generic(const float* V, const float* W, float* Vnew, long long rows, int d,
+                                       const SpecScratch& s, double tol, int count_pass, Ctl* ctl, cudaStream_t st) {
+  update_generic_kernel<<<reduce_grid(rows), 256, 2 * d * d * sizeof(double), st>>>(V, W, Vnew, rows, d, s, tol,
+                                                                                   count_pass, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polar_generic(const float* V, float* X0, int n, int d, cudaStream_t st) {
+  polar_generic_kernel<<<n, 256, 4 * d * d * sizeof(double), st>>>(V, X0, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dF_generic(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
+                              cudaStream_t st) {
+  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(float), st>>>(nullptr, const_cast<float*>(Yv),
+                                                                                        nullptr, X, rows, d, 0.f, 1, s,
+                                                                                        ctl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  polar_single_kernel<<<1, 256, 4 * d * d * sizeof(double), st>>>(s, d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  dist_generic_kernel<<<reduce_grid(rows), 256, d * d * sizeof(double), st>>>(X, Yv, rows, d, s, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace nsrgs

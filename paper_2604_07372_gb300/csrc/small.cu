@@ -42,6 +42,59 @@ __global__ void __launch_bounds__(128) epilogue_kernel(const float* __restrict__
   }
 }
 
+// ------------------------------------------------ GPM (comparison method)
+// Generalised power method step, the paper's comparison method (read as
+// X_i <- sgn(sum_j A_ij X_j) with A_ii = I): M = Y_i + X_i, then the exact
+// per-block sign by a float32 one-sided Jacobi SVD (a batched per-block SVD,
+// the cost NS-RGS removes).  Same update-norm / stop bookkeeping as the epilogue.
+template <int D>
+__global__ void __launch_bounds__(128) gpm_epilogue_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                                           float* __restrict__ Xout, int n, double tol, Ctl* ctl) {
+  __shared__ double sh[32];
+  if (ctl->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double diff2 = 0.0;
+  unsigned int flags = 0;
+  if (i < n) {
+    float M[D][D], x[D][D], Q[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const long long e = ((long long)i * D + r) * D + c;
+        x[r][c] = X[e];
+        M[r][c] = Y[e] + x[r][c];
+        Y[e] = 0.f;
+      }
+    polar_fp32<D>(M, Q);
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        finite = finite && isfinite(Q[r][c]);
+        Xout[((long long)i * D + r) * D + c] = Q[r][c];
+        const double dd = (double)Q[r][c] - (double)x[r][c];
+        diff2 += dd * dd;
+      }
+    if (!finite) flags |= FLAG_NONFINITE;
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+  const double bs = block_sum(diff2, sh);
+  if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&ctl->upd_acc, 0.0);
+      const double un = sqrt(tot / ((double)n * D));
+      ctl->last_upd = un;
+      ctl->iters_done += 1;
+      if (tol > 0.0 && un < tol) ctl->stop = 1;
+      ctl->upd_acc = 0.0;
+      ctl->counter = 0u;
+    }
+  }
+}
+
 // ------------------------------------------- spectral init: subspace steps
 // Deterministic start V0 (any full-rank start works; entries uniform in (-1, 1)).
 __global__ void spec_v0_kernel(float* V, long long rows, int D) {
@@ -297,10 +350,30 @@ __global__ void select_copy_kernel(const float* __restrict__ B0, const float* __
     default: return cudaErrorInvalidValue; \
   }
 
+// Runtime-d versions for 8 < d <= 64 (generic.cu).
+cudaError_t launch_epilogue_generic(const float*, float*, float*, int, int, float, int, double, Ctl*, double*,
+                                    cudaStream_t);
+cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
+                                     cudaStream_t);
+cudaError_t launch_spec_update_generic(const float*, const float*, float*, long long, int, const SpecScratch&,
+                                       double, int, Ctl*, cudaStream_t);
+cudaError_t launch_polar_generic(const float*, float*, int, int, cudaStream_t);
+cudaError_t launch_dF_generic(const float*, const float*, long long, int, const SpecScratch&, Ctl*, cudaStream_t);
+
 cudaError_t launch_epilogue(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, double tol,
                             Ctl* ctl, double* upd_out, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_epilogue_generic(X, Y, Xout, n, d, eta, K, tol, ctl, upd_out, st);
   const int grid = (n + 127) / 128;
 #define L(DD) epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, eta, K, tol, ctl, upd_out)
+  NSRGS_DISPATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gpm_epilogue(const float* X, float* Y, float* Xout, int n, int d, double tol, Ctl* ctl,
+                                cudaStream_t st) {
+  const int grid = (n + 127) / 128;
+#define L(DD) gpm_epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, tol, ctl)
   NSRGS_DISPATCH_D(d, L)
 #undef L
   return cudaGetLastError();
@@ -321,6 +394,7 @@ cudaError_t launch_spec_v0(float* V, long long rows, int d, cudaStream_t st) {
 
 cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows, int d, float shift,
                              const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_spec_gram_generic(V, Y, W, rows, d, shift, s, ctl, st);
   const int grid = reduce_grid(rows);
 #define L(DD) spec_gram_kernel<DD><<<grid, 256, 0, st>>>(V, Y, W, rows, shift, s, ctl)
   NSRGS_DISPATCH_D(d, L)
@@ -330,6 +404,7 @@ cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows,
 
 cudaError_t launch_spec_update(const float* V, const float* W, float* Vnew, long long rows, int d,
                                const SpecScratch& s, double tol, int count_pass, Ctl* ctl, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_spec_update_generic(V, W, Vnew, rows, d, s, tol, count_pass, ctl, st);
   const int grid = reduce_grid(rows);
 #define L(DD) spec_update_kernel<DD><<<grid, 256, 0, st>>>(V, W, Vnew, rows, s, tol, count_pass, ctl)
   NSRGS_DISPATCH_D(d, L)
@@ -338,6 +413,7 @@ cudaError_t launch_spec_update(const float* V, const float* W, float* Vnew, long
 }
 
 cudaError_t launch_polar_blocks(const float* V, float* X0, int n, int d, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_polar_generic(V, X0, n, d, st);
   const int grid = (n + 127) / 128;
 #define L(DD) polar_blocks_kernel<DD><<<grid, 128, 0, st>>>(V, X0, n)
   NSRGS_DISPATCH_D(d, L)
@@ -347,6 +423,7 @@ cudaError_t launch_polar_blocks(const float* V, float* X0, int n, int d, cudaStr
 
 cudaError_t launch_dF(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
                       cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_dF_generic(X, Yv, rows, d, s, ctl, st);
   const int grid = reduce_grid(rows);
 #define L(DD) cross_gram_kernel<DD><<<grid, 256, 0, st>>>(X, Yv, rows, s, ctl)
   NSRGS_DISPATCH_D(d, L)

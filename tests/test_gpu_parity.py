@@ -221,3 +221,24 @@ def test_full_size_sampled_blocks(P):
     # spectral start: Y spans the top-d subspace, X0 blocks orthogonal
     Xb = O.blocks(X0h, d)
     assert np.max(np.abs(np.swapaxes(Xb, 1, 2) @ Xb - np.eye(d))) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f32", "dense_f32"])
+def test_gpm_baseline_matches_oracle(P, storage):
+    """The GPM baseline (per-block exact sign) against the oracle's GPM, same start."""
+    n, d, T = 200, 3, 30
+    inst = make(n, d, seed=44)
+    A = inst.dense()
+    X0, _ = O.spectral_init(A, n, d)
+    ref = O.gpm(A, n, d, T, X0=X0)
+    pa = packed(P, inst, P.STORAGE[storage])
+    X = torch.from_numpy(X0.astype(np.float32)).cuda()
+    X, info = P.nsrgs_gpm_solve(pa, T, init=False, X=X)
+    torch.cuda.synchronize()
+    assert info.iters == T
+    assert O.dF(to64(X), ref, d) / math.sqrt(n * d) <= 1e-5
+    # GPM and NS-RGS reach the same fixed point (the oracle pins this too)
+    Xn, _ = P.nsrgs_solve(pa, 1.0 / n, 120, 2)
+    Xg, _ = P.nsrgs_gpm_solve(pa, 120)
+    torch.cuda.synchronize()
+    assert O.dF(to64(Xn), to64(Xg), d) / math.sqrt(n * d) <= 1e-5
