@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--c", type=float, default=0.3)
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
     return ap.parse_args()
 
 
@@ -77,7 +78,7 @@ def profiled_traffic(kernel_tag: str):
         return None
     csrc = os.path.join(ROOT, "paper_2604_07372_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("stream.cu", "common.cuh"):
+    for name in ("stream.cu", "panel.cuh", "common.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -134,6 +135,22 @@ class ClockSampler:
             "reasons": sorted(reasons),
             "samples": len(sm),
         }
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time: every rank contributes its own, all receive the maximum."""
+    import torch
+
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, iters_per_step: int, seconds: float) -> float:
+    """Replicas: every rank runs its own instance, so the job's rate sums over ranks."""
+    return world * steps * iters_per_step / seconds
 
 
 def dist_setup(args):
@@ -414,16 +431,19 @@ def run_ours(args, world, rank, local):
     gen_s = time.perf_counter() - t0
     up = torch.from_numpy(inst.upper).cuda()
     Zt = torch.from_numpy(inst.Zstack().astype(np.float32)).cuda()
-    packs = {"f32": P.nsrgs_pack_upper(up, n, d, P.F32)}
+    main_st = args.storage
+    packs = {main_st: P.nsrgs_pack_upper(up, n, d, P.STORAGE[main_st])}
     if not args.no_extras:
-        packs["bf16"] = P.nsrgs_pack_upper(up, n, d, P.BF16)
-        packs["fp8"] = P.nsrgs_pack_upper(up, n, d, P.FP8E4M3)
+        for extra in ("f32", "bf16", "fp8"):
+            if extra not in packs:
+                packs[extra] = P.nsrgs_pack_upper(up, n, d, P.STORAGE[extra])
     del up
     torch.cuda.synchronize()
     ws = P.workspace(n, d)
     X = torch.empty(n * d, d, dtype=torch.float32, device="cuda")
-    pa = packs["f32"]
-    alg_bytes = n * (n - 1) // 2 * d * d * 4  # packed block-upper triangle, float32
+    pa = packs[main_st]
+    ebytes = {"f32": 4, "bf16": 2, "fp8": 1}[main_st]
+    alg_bytes = n * (n - 1) // 2 * d * d * ebytes  # packed block-upper triangle
 
     P.nsrgs_set_kernel_timing(True)
     for _ in range(args.warmup):
@@ -447,17 +467,14 @@ def run_ours(args, world, rank, local):
     ms = ev0.elapsed_time(ev1)
     launches, kern_ms, nodes = P.nsrgs_kernel_timing()
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     sec = ms / 1e3
-    value = world * args.steps * T / sec
+    value = whole_job_rate(world, args.steps, T, sec)
     dF_Z = P.nsrgs_dF(X, Zt, n, d, ws=ws)
 
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    tag = f"panel_stream_f32_n{n}_d{d}"
+    tag = f"panel_stream_{main_st}_n{n}_d{d}"
     roofline = {
         "bound": "hbm",
         "achieved": achieved,
@@ -465,7 +482,7 @@ def run_ours(args, world, rank, local):
         "unit": "GB/s",
         "frac": achieved / peaks["hbm_gbs"],
         "traffic": profiled_traffic(tag),
-        "kernel": f"panel_stream_kernel<D={d},F32> (symmetric A-stream, one launch per iteration)",
+        "kernel": f"panel_stream_kernel<D={d},{main_st.upper()}> (symmetric A-stream, one launch per iteration)",
         "algorithmic_bytes_per_launch": alg_bytes,
         "mean_launch_ms": kern_ms,
         "launches_timed": launches,
@@ -486,7 +503,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
-            "storage": "float32 packed block-upper triangle (symmetric read-once)",
+            "storage": f"{main_st} packed block-upper triangle (symmetric read-once), float32 arithmetic",
             "l2": "inputs larger than L2 (packed A 1.80 GB vs 129 MB L2); no flush needed",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
