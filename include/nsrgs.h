@@ -62,12 +62,16 @@ typedef enum {
  *            the paper does not discuss reduced precision.
  *  DENSE_F32: the full nd x nd float32 matrix, both triangles, no symmetric reuse
  *            (twice the bytes of F32).  Works for every d; it is the plain form the
- *            symmetric layouts are measured against. */
+ *            symmetric layouts are measured against.
+ *  DENSE_BF16: the full matrix in bfloat16 for d in {16, 32, 64}, multiplied on the
+ *            tensor cores (tcgen05, float32 accumulation in TMEM) with X rounded to
+ *            bfloat16 for the product; the d x d work stays float32. */
 typedef enum {
   NSRGS_F32 = 0,
   NSRGS_BF16 = 1,
   NSRGS_FP8E4M3 = 2,
-  NSRGS_DENSE_F32 = 3
+  NSRGS_DENSE_F32 = 3,
+  NSRGS_DENSE_BF16 = 4
 } nsrgs_storage;
 
 /* A packed measurement matrix.  `packed` is the device buffer written by

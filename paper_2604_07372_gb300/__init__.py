@@ -11,6 +11,7 @@ from ._lib import (  # noqa: F401
     BF16,
     FP8E4M3,
     DENSE_F32,
+    DENSE_BF16,
     STORAGE,
     NsrgsError,
     PackedA,

@@ -12,8 +12,8 @@ from dataclasses import dataclass
 
 import torch
 
-F32, BF16, FP8E4M3, DENSE_F32 = 0, 1, 2, 3
-STORAGE = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "dense_f32": DENSE_F32}
+F32, BF16, FP8E4M3, DENSE_F32, DENSE_BF16 = 0, 1, 2, 3, 4
+STORAGE = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "dense_f32": DENSE_F32, "dense_bf16": DENSE_BF16}
 _STATUS = {
     0: "NSRGS_OK",
     1: "NSRGS_ERR_INVALID_ARG",

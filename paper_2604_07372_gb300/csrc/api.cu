@@ -46,6 +46,11 @@ cudaError_t launch_dF(const float*, const float*, long long, int, const SpecScra
 cudaError_t launch_copy_out(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
 cudaError_t launch_select_copy(const float*, const float*, float*, long long, const Ctl*, cudaStream_t);
 cudaError_t generic_prepare(int d);
+long long dense_bf16_pitch(int n, int d);
+bool tc_dense_supported(int d);
+cudaError_t tc_dense_prepare(int d);
+cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, __nv_bfloat16* XT, float* Y, Ctl* ctl,
+                             const int* skip, cudaStream_t st);
 
 constexpr int kMaxReduceGrid = 512;
 constexpr int kMaxSmallD = 8;
@@ -57,6 +62,7 @@ struct Workspace {
   float* Y;
   float* W;
   SpecScratch s;
+  __nv_bfloat16* XT;  // X^T in bfloat16 for the tensor-core stream (d >= 16 only)
   size_t bytes;
 };
 
@@ -85,6 +91,7 @@ static Workspace map_workspace(void* base, int n, int d) {
   w.s.Q = reinterpret_cast<double*>(take(dd));
   w.s.scal = reinterpret_cast<double*>(take(8 * sizeof(double)));
   w.s.partials = reinterpret_cast<double*>(take((size_t)kMaxReduceGrid * 2 * dd));
+  if (d >= 16) w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)d * dense_bf16_pitch(n, d) * 2));
   w.bytes = off;
   return w;
 }
@@ -112,6 +119,14 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
   if (s != NSRGS_OK) return s;
   NSRGS_CHECK_ARG(A->packed != nullptr && aligned16(A->packed), "A->packed must be a 16-byte aligned device pointer");
   if (A->storage == NSRGS_DENSE_F32) return NSRGS_OK;
+  if (A->storage == NSRGS_DENSE_BF16) {
+    if (!tc_dense_supported(A->d)) {
+      set_error("NSRGS_DENSE_BF16 (tensor-core stream) covers d in {16, 32, 64}");
+      return NSRGS_ERR_UNSUPPORTED;
+    }
+    NSRGS_CUDA_TRY(tc_dense_prepare(A->d));
+    return NSRGS_OK;
+  }
   NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
     set_error("symmetric storage needs 1 <= d <= 4 in this build (use NSRGS_DENSE_F32)");
@@ -133,10 +148,11 @@ static nsrgs_status check_ws(void* ws, size_t ws_bytes, int n, int d) {
 }
 
 // ---------------------------------------------------------------- pieces
-static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
+static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* X, const Workspace& w,
                              const int* skip, cudaStream_t st) {
-  if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, Y, skip, st);
-  return stream_panel(A->packed, g, X, Y, ctl, skip, st);
+  if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, w.Y, skip, st);
+  if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
+  return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
 }
 
 // Resets the control block and zeroes Y and the padding of the X buffers.
@@ -166,7 +182,7 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
   for (int k = 0; k < max_iters; ++k) {
     const float* V = w.X[(k + 1) & 1];
     float* Vn = w.X[k & 1];
-    if ((e = stream_AX(A, g, V, w.Y, w.ctl, &w.ctl->spec_stop, st)) != cudaSuccess) return e;
+    if ((e = stream_AX(A, g, V, w, &w.ctl->spec_stop, st)) != cudaSuccess) return e;
     if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, w.s, w.ctl, st)) != cudaSuccess) return e;
     if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, 1, w.ctl, st)) != cudaSuccess) return e;
   }
@@ -185,7 +201,7 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
     const float* Xt = w.X[t & 1];
     float* Xn = w.X[(t + 1) & 1];
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = stream_AX(A, g, Xt, w.Y, w.ctl, &w.ctl->stop, st)) != cudaSuccess) return e;
+    if ((e = stream_AX(A, g, Xt, w, &w.ctl->stop, st)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (method == METHOD_GPM)
       e = launch_gpm_epilogue(Xt, w.Y, Xn, A->n, A->d, tol, w.ctl, st);
@@ -278,6 +294,8 @@ const char* nsrgs_version(void) { return "nsrgs-gb300 0.1 (sm_103a)"; }
 size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (n < 2 || d < 1 || d > 64) return 0;
   if (storage == NSRGS_DENSE_F32) return (size_t)n * d * (size_t)dense_pitch(n, d) * sizeof(float);
+  if (storage == NSRGS_DENSE_BF16)
+    return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) return 0;
   return (size_t)(g.header_bytes + g.panel_bytes);
@@ -342,7 +360,7 @@ nsrgs_status nsrgs_product(const nsrgs_A* A, const float* X, float* Y, void* ws,
   Workspace w = map_workspace(ws, A->n, A->d);
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, st));
-  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w.Y, w.ctl, &w.ctl->stop, st));
+  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(Y, w.Y, bytes, cudaMemcpyDeviceToDevice, st));
   return NSRGS_OK;
 }
@@ -365,7 +383,7 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
   Workspace w = map_workspace(ws, A->n, A->d);
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X_in, bytes, cudaMemcpyDeviceToDevice, st));
-  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w.Y, w.ctl, &w.ctl->stop, st));
+  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
   NSRGS_CUDA_TRY(launch_epilogue(w.X[0], w.Y, X_out, A->n, A->d, eta, K, 0.0, w.ctl, upd_norm, st));
   return NSRGS_OK;
 }

@@ -164,9 +164,14 @@ __global__ void pack_panel_kernel(Src src, PanelGeom g, uint8_t* packed) {
   }
 }
 
-// Dense layout: row pitch = round_up(nd, 4) floats, diagonal blocks zeroed.
-template <class Src>
-__global__ void pack_dense_kernel(Src src, int n, int d, int pitch, float* out) {
+__device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Dense layouts: row pitch = round_up(nd, 4) floats (float32) or round_up(nd, 64)
+// bfloat16 values (whole 128-byte rows for the tensor-core stream); diagonal
+// blocks zeroed.
+template <class Src, class T>
+__global__ void pack_dense_kernel(Src src, int n, int d, int pitch, T* out) {
   long long N = (long long)n * d;
   long long total = N * pitch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -178,17 +183,24 @@ __global__ void pack_dense_kernel(Src src, int n, int d, int pitch, float* out) 
       if (i < j) v = src(r, c);
       else if (i > j) v = src(c, r);  // A_ij = A_ji^T: element (r, c) = (c, r) of the upper part
     }
-    out[e] = v;
+    store_as(out + e, v);
   }
 }
 
 long long dense_pitch(int n, int d) { return ((long long)n * d + 3) / 4 * 4; }
+long long dense_bf16_pitch(int n, int d);
 
 template <class Src>
 static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, cudaStream_t st) {
   if (storage == NSRGS_DENSE_F32) {
     long long pitch = dense_pitch(n, d);
     pack_dense_kernel<<<4 * num_sms(), 256, 0, st>>>(src, n, d, (int)pitch, (float*)packed);
+    NSRGS_CUDA_TRY(cudaGetLastError());
+    return NSRGS_OK;
+  }
+  if (storage == NSRGS_DENSE_BF16) {
+    long long pitch = dense_bf16_pitch(n, d);
+    pack_dense_kernel<<<4 * num_sms(), 256, 0, st>>>(src, n, d, (int)pitch, (__nv_bfloat16*)packed);
     NSRGS_CUDA_TRY(cudaGetLastError());
     return NSRGS_OK;
   }

@@ -1,0 +1,63 @@
+"""Tensor-core (tcgen05) A stream for d in {16, 32, 64}: NSRGS_DENSE_BF16.
+
+The product is checked against an exact float64 product of the same
+bfloat16-rounded A and X (the kernel rounds X to bfloat16 for the multiply and
+accumulates in float32), then whole solves against the float32 path: final
+d_F(X, Z) within 1%.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2604_07372_gb300 as P
+
+    return P
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("n,d", [(20, 16), (9, 32), (5, 64), (300, 16), (130, 32), (70, 64)])
+def test_tensor_core_product(P, n, d):
+    inst = synth.make_instance(n, d, 0.5, seed=n + d, dtype=np.float32)
+    A = inst.dense()
+    for i in range(n):
+        A[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
+    X = np.random.default_rng(d).standard_normal((n * d, d)).astype(np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.DENSE_BF16)
+    Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    Ab, Xb = bf16_round(A), bf16_round(X)
+    ref = Ab @ Xb
+    scale = np.abs(Ab) @ np.abs(Xb)
+    got = Y.double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-6), np.max(np.abs(got - ref) / (scale + 1e-6))
+
+
+@pytest.mark.parametrize("n,d", [(200, 16), (80, 32)])
+def test_tensor_core_solve_within_one_percent(P, n, d):
+    T, K = 40, 2
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=7 * d, dtype=np.float32)
+    up = torch.from_numpy(inst.upper).cuda()
+    Xf, _ = P.nsrgs_solve(P.nsrgs_pack_upper(up, n, d, P.DENSE_F32), 1.0 / n, T, K)
+    Xb, info = P.nsrgs_solve(P.nsrgs_pack_upper(up, n, d, P.DENSE_BF16), 1.0 / n, T, K)
+    torch.cuda.synchronize()
+    Z = inst.Zstack()
+    ef = O.dF(Xf.double().cpu().numpy(), Z, d)
+    eb = O.dF(Xb.double().cpu().numpy(), Z, d)
+    assert info.iters == T
+    assert abs(eb - ef) / ef <= 0.01, (ef, eb)
