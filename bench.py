@@ -253,6 +253,64 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
     return out
 
 
+# ------------------------------------------------------- dimension sweep
+def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps: int = 5, T: int = 20):
+    """n = 2000, d in {3, 8, 16, 32, 64}, c = 0.3: the A-stream product per storage
+    (ms, algorithmic GB/s), and short solves (T = 20) for iterations/s and final d_F."""
+    import numpy as np
+    import torch
+
+    out = {}
+    for d in dims:
+        Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
+        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 4 else []) + (["dense_bf16"] if d in (16, 32, 64) else [])
+        res = {}
+        Zs = Z.reshape(n * d, d)
+        nb = n * (n - 1) // 2 * d * d
+        for name in storages:
+            try:
+                pa = P.nsrgs_pack_upper(up, n, d, P.STORAGE[name])
+                X = torch.randn(n * d, d, device="cuda")
+                Y = torch.empty_like(X)
+                ws = P.workspace(n, d)
+                P.nsrgs_product(pa, X, Y, ws=ws)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    P.nsrgs_product(pa, X, Y, ws=ws)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                alg = {"dense_f32": 2 * nb * 4, "dense_bf16": 2 * nb * 2, "f32": nb * 4, "bf16": nb * 2}[name]
+                ent = {"product_ms": ms, "alg_GB": alg / 1e9, "GBps": alg / (ms / 1e3) / 1e9,
+                       "flops_TFs": 2 * 2 * nb * d / (ms / 1e3) / 1e12}
+                Xs, info = P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, ws=ws)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                Xs, info = P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, X=Xs, ws=ws)
+                torch.cuda.synchronize()
+                ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
+                ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
+                if d <= 8 and name in ("dense_f32", "f32"):
+                    Xg, _ = P.nsrgs_gpm_solve(pa, T, spectral_max_iters=SMAX, ws=ws)
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    Xg, _ = P.nsrgs_gpm_solve(pa, T, spectral_max_iters=SMAX, X=Xg, ws=ws)
+                    torch.cuda.synchronize()
+                    ent["gpm_solve_ms"] = 1e3 * (time.perf_counter() - t)
+                    ent["gpm_final_dF_to_truth"] = P.nsrgs_dF(Xg, Zs, n, d, ws=ws)
+                res[name] = ent
+                del pa, ws, X, Y
+            except Exception as e:
+                res[name] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+            torch.cuda.empty_cache()
+        out[f"d{d}"] = res
+        del up, Z
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------ serving leg
 def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0, pool_per_d: int = 16,
                 tol: float = 1e-6, T_max: int = 1000, slots: int = 48):
@@ -607,10 +665,10 @@ def run_ours(args, world, rank, local):
         packs.clear()
         torch.cuda.empty_cache()
         # batched and served forms (the metric's second half)
-        for key, fn in (("batched", batched_leg), ("serving", serving_leg)):
+        for key, fn in (("batched", batched_leg), ("serving", serving_leg), ("dimension_sweep", dsweep_leg)):
             try:
                 t = time.perf_counter()
-                line[key] = fn(P, synth, seed=args.seed + (1 if key == "batched" else 2))
+                line[key] = fn(P, synth, seed=args.seed + {"batched": 1, "serving": 2, "dimension_sweep": 3}[key])
                 line[key]["leg_wall_s"] = time.perf_counter() - t
             except Exception as e:  # reported in the line, the main metric stands
                 line[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
