@@ -51,6 +51,9 @@ bool tc_dense_supported(int d);
 cudaError_t tc_dense_prepare(int d);
 cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, __nv_bfloat16* XT, float* Y, Ctl* ctl,
                              const int* skip, cudaStream_t st);
+cudaError_t tc_dense_tune(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
+                          cudaStream_t st);
+int tc_dense_splits(int n, int d);
 
 constexpr int kMaxReduceGrid = 512;
 constexpr int kMaxSmallD = 8;
@@ -153,6 +156,16 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
   if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, w.Y, skip, st);
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
   return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
+}
+
+// Tensor-core storage: pick the split-K for this shape once (timed, outside any
+// capture).  Clobbers Y and the control block; callers reset both afterwards.
+static cudaError_t maybe_tune(const nsrgs_A* A, const Workspace& w, cudaStream_t st) {
+  if (A->storage != NSRGS_DENSE_BF16) return cudaSuccess;
+  if (tc_dense_splits(A->n, A->d) > 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st);
+  if (e != cudaSuccess) return e;
+  return tc_dense_tune(A->packed, A->n, A->d, w.XT, w.Y, w.ctl, &w.ctl->stop, st);
 }
 
 // Resets the control block and zeroes Y and the padding of the X buffers.
@@ -332,6 +345,7 @@ nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, dou
   NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
   cudaStream_t st = (cudaStream_t)stv;
   Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(maybe_tune(A, w, st));
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(enqueue_spectral(A, g, w, max_iters, tol, X0, st));
   Ctl c{};
@@ -358,6 +372,7 @@ nsrgs_status nsrgs_product(const nsrgs_A* A, const float* X, float* Y, void* ws,
   const size_t bytes = (size_t)A->n * A->d * A->d * sizeof(float);
   cudaStream_t st = (cudaStream_t)stv;
   Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(maybe_tune(A, w, st));
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, st));
   NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
@@ -381,6 +396,7 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
   NSRGS_CHECK_ARG(a0 + bytes <= b0 || b0 + bytes <= a0, "X_in and X_out overlap");
   cudaStream_t st = (cudaStream_t)stv;
   Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(maybe_tune(A, w, st));
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X_in, bytes, cudaMemcpyDeviceToDevice, st));
   NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
@@ -465,7 +481,9 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     NSRGS_CUDA_TRY(capture_stream(dev, &cs));
     if (key.timing) NSRGS_CUDA_TRY(ensure_events(dev, T));
     const cudaEvent_t* ev = key.timing ? g_timing_state[dev].ev.data() : nullptr;
-    // first launches configure kernel attributes outside of capture
+    // tuning and kernel attributes happen outside of capture
+    NSRGS_CUDA_TRY(maybe_tune(A, w, st));
+    NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
     NSRGS_CUDA_TRY(cudaStreamSynchronize(cs));
     NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = reset_ws(w, n, d, cs);

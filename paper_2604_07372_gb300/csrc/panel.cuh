@@ -359,8 +359,13 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     const int n = v.g.n;
     const float* scale =
         (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(v.packed + v.g.off_scale) : nullptr;
+    // Reduced-precision storage does twice (BF16) or four times (FP8) the FMAs per
+    // byte; there the FMAs run in pairs (fma.rn.f32x2 on adjacent columns) and the
+    // row partials are kept as (even-column, odd-column) pairs.
+    constexpr bool kPair = (ST != NSRGS_F32) && (C::CPT % 2 == 0);
     float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
-    float racc[C::RT][D];  // row partials
+    float racc[C::RT][D];  // row partials (unpaired path)
+    float2 racc2[kPair ? C::RT : 1][D];  // row partials (paired path)
     float rsc[RB];         // FP8 row scales
     auto load_rows = [&](int bb) {
 #pragma unroll
@@ -375,6 +380,7 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           for (int k = 0; k < D; ++k) {
             xr[rb * D + r][k] = (i < n) ? v.X[((long long)i * D + r) * D + k] * s : 0.f;
             racc[rb * D + r][k] = 0.f;
+            if constexpr (kPair) racc2[rb * D + r][k] = make_float2(0.f, 0.f);
           }
       }
     };
@@ -384,6 +390,7 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           float x = racc[r][k];
+          if constexpr (kPair) x = racc2[r][k].x + racc2[r][k].y;
           x += __shfl_xor_sync(0xffffffffu, x, 1);
           x += __shfl_xor_sync(0xffffffffu, x, 2);
           racc[r][k] = x;
@@ -428,16 +435,41 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           const float4 t = xs[k];
           xc[4 * k + 0] = t.x; xc[4 * k + 1] = t.y; xc[4 * k + 2] = t.z; xc[4 * k + 3] = t.w;
         }
+        if constexpr (kPair) {
+          float2 xc2[C::CPT / 2][D];  // (X row of column 2j, of column 2j+1), per component
 #pragma unroll
-        for (int rt = 0; rt < C::RT; ++rt) {
-          float av[C::CPT];
-          Unpack<ST, C::CPT>::run(raw[rt], av);
+          for (int j = 0; j < C::CPT / 2; ++j)
 #pragma unroll
-          for (int cc = 0; cc < C::CPT; ++cc) {
+            for (int k = 0; k < D; ++k) xc2[j][k] = make_float2(xc[(2 * j) * D + k], xc[(2 * j + 1) * D + k]);
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
-              cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
+          for (int rt = 0; rt < C::RT; ++rt) {
+            float av[C::CPT];
+            Unpack<ST, C::CPT>::run(raw[rt], av);
+#pragma unroll
+            for (int j = 0; j < C::CPT / 2; ++j) {
+              const float2 a2 = make_float2(av[2 * j], av[2 * j + 1]);
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                racc2[rt][k] = __ffma2_rn(a2, xc2[j][k], racc2[rt][k]);
+                float2 c = make_float2(cacc[(2 * j) * D + k], cacc[(2 * j + 1) * D + k]);
+                c = __ffma2_rn(a2, make_float2(xr[rt][k], xr[rt][k]), c);
+                cacc[(2 * j) * D + k] = c.x;
+                cacc[(2 * j + 1) * D + k] = c.y;
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int rt = 0; rt < C::RT; ++rt) {
+            float av[C::CPT];
+            Unpack<ST, C::CPT>::run(raw[rt], av);
+#pragma unroll
+            for (int cc = 0; cc < C::CPT; ++cc) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
+                cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
+              }
             }
           }
         }

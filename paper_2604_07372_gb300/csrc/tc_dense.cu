@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -302,6 +304,99 @@ cudaError_t tc_dense_prepare(int d) {
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------ autotuner
+// Split-K (K chunks per 128-row tile) per (n, d): the first call for a shape made
+// outside any stream capture times a few candidates and keeps the fastest; until
+// then (and inside captures) the heuristic of about two work units per SM is used.
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tuned_splits;
+
+static int heuristic_splits(int row_tiles, int ksteps) {
+  int s = (2 * num_sms() + row_tiles - 1) / row_tiles;
+  if (s < 1) s = 1;
+  if (s > ksteps) s = ksteps;
+  return s;
+}
+
+static cudaError_t launch_tc_any(int d, const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a,
+                                 cudaStream_t st) {
+  switch (d) {
+    case 16: return launch_tc<16>(ta, tb, a, st, false);
+    case 32: return launch_tc<32>(ta, tb, a, st, false);
+    case 64: return launch_tc<64>(ta, tb, a, st, false);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static bool build_launch(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
+                         CUtensorMap* ta, CUtensorMap* tb, TcArgs* a) {
+  const int rows = n * d;
+  const long long pitch = dense_bf16_pitch(n, d);
+  if (!make_map(ta, packed, (uint64_t)pitch, (uint64_t)rows, (uint64_t)pitch * 2, 64, 128) ||
+      !make_map(tb, XT, (uint64_t)pitch, (uint64_t)d, (uint64_t)pitch * 2, 64, (uint32_t)d))
+    return false;
+  a->Y = Y;
+  a->skip = skip;
+  a->ctl = ctl;
+  a->rows = rows;
+  a->row_tiles = (rows + 127) / 128;
+  a->ksteps = (int)(pitch / 64);
+  a->splits = heuristic_splits(a->row_tiles, a->ksteps);
+  return true;
+}
+
+// Times candidate splits with the caller's buffers (Y is left with garbage: the
+// caller clears it before use).  No-op when the shape is already tuned or `st`
+// is capturing.
+cudaError_t tc_dense_tune(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
+                          cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tuned_splits.count({n, d})) return cudaSuccess;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+  CUtensorMap ta, tb;
+  TcArgs a;
+  if (!build_launch(packed, n, d, XT, Y, ctl, skip, &ta, &tb, &a)) return cudaErrorInvalidValue;
+  const int base = heuristic_splits(a.row_tiles, a.ksteps);
+  int best = base;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) return e;
+  const int cands[5] = {base / 2, base, 2 * base, 4 * base, 8 * base};
+  for (int c : cands) {
+    if (c < 1 || c > a.ksteps) continue;
+    a.splits = c;
+    if ((e = launch_tc_any(d, ta, tb, a, st)) != cudaSuccess) break;  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r)
+      if ((e = launch_tc_any(d, ta, tb, a, st)) != cudaSuccess) break;
+    cudaEventRecord(e1, st);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_splits[{n, d}] = best;
+  return cudaSuccess;
+}
+
+int tc_dense_splits(int n, int d) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_splits.find({n, d});
+  return it == g_tuned_splits.end() ? 0 : it->second;
+}
+
 // XT: workspace buffer of d * pitch bf16.
 cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, __nv_bfloat16* XT, float* Y, Ctl* ctl,
                              const int* skip, cudaStream_t st) {
@@ -311,26 +406,11 @@ cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, _
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, packed, (uint64_t)pitch, (uint64_t)rows, (uint64_t)pitch * 2, 64, 128) ||
-      !make_map(&tb, XT, (uint64_t)pitch, (uint64_t)d, (uint64_t)pitch * 2, 64, (uint32_t)d))
-    return cudaErrorInvalidValue;
   TcArgs a;
-  a.Y = Y;
-  a.skip = skip;
-  a.ctl = ctl;
-  a.rows = rows;
-  a.row_tiles = (rows + 127) / 128;
-  a.ksteps = (int)(pitch / 64);
-  int splits = (2 * num_sms() + a.row_tiles - 1) / a.row_tiles;
-  if (splits < 1) splits = 1;
-  if (splits > a.ksteps) splits = a.ksteps;
-  a.splits = splits;
-  switch (d) {
-    case 16: return launch_tc<16>(ta, tb, a, st, false);
-    case 32: return launch_tc<32>(ta, tb, a, st, false);
-    case 64: return launch_tc<64>(ta, tb, a, st, false);
-  }
-  return cudaErrorInvalidValue;
+  if (!build_launch(packed, n, d, XT, Y, ctl, skip, &ta, &tb, &a)) return cudaErrorInvalidValue;
+  const int tuned = tc_dense_splits(n, d);
+  if (tuned > 0) a.splits = tuned;
+  return launch_tc_any(d, ta, tb, a, st);
 }
 
 }  // namespace nsrgs
