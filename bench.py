@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
+    ap.add_argument("--leg", default="all", choices=["all", "sweep"],
+                    help="sweep: only the dimension sweep (no JSON metric line), for profiling")
+    ap.add_argument("--sweep-dims", default="3,8,16,32,64")
+    ap.add_argument("--sweep-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -698,6 +702,19 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.leg == "sweep":
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_2604_07372_gb300 as P
+        import synth
+
+        torch.cuda.set_device(local)
+        dims = tuple(int(x) for x in args.sweep_dims.split(","))
+        print(json.dumps({"dimension_sweep": dsweep_leg(P, synth, seed=args.seed + 3, dims=dims, reps=args.sweep_reps)}))
         return
     run_ours(args, world, rank, local)
 

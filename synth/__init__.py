@@ -160,11 +160,10 @@ def device_upper(n: int, d: int, sigma: float, seed: int, p: float = 1.0, device
     """
     import torch
 
+    # ground truth on the host (n small d x d polar factors), noise on the device
+    Z = torch.from_numpy(haar_orthogonal(np.random.default_rng(int(seed)), n, d).astype(np.float32)).to(device)
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    G = torch.randn((n, d, d), generator=g, device=device, dtype=torch.float64)
-    U, _, Vh = torch.linalg.svd(G)
-    Z = (U @ Vh).to(torch.float32)
     iu, ju = torch.triu_indices(n, n, offset=1, device=device)
     nb = iu.numel()
     out = torch.empty((nb, d, d), dtype=torch.float32, device=device)
