@@ -55,8 +55,9 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
-    ap.add_argument("--leg", default="all", choices=["all", "sweep"],
-                    help="sweep: only the dimension sweep (no JSON metric line), for profiling")
+    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving"],
+                    help="run only one extra leg (prints its JSON, no metric line), for profiling")
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
     return ap.parse_args()
@@ -267,7 +268,7 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     out = {}
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
-        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 4 else []) + (["dense_bf16"] if d in (16, 32, 64) else [])
+        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 8 else []) + (["dense_bf16"] if d in (16, 32, 64) else [])
         res = {}
         Zs = Z.reshape(n * d, d)
         nb = n * (n - 1) // 2 * d * d
@@ -703,7 +704,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.leg == "sweep":
+    if args.leg != "all":
         import torch
 
         import __graft_entry__
@@ -713,8 +714,14 @@ def main():
         import synth
 
         torch.cuda.set_device(local)
-        dims = tuple(int(x) for x in args.sweep_dims.split(","))
-        print(json.dumps({"dimension_sweep": dsweep_leg(P, synth, seed=args.seed + 3, dims=dims, reps=args.sweep_reps)}))
+        if args.leg == "sweep":
+            dims = tuple(int(x) for x in args.sweep_dims.split(","))
+            out = dsweep_leg(P, synth, seed=args.seed + 3, dims=dims, reps=args.sweep_reps)
+        elif args.leg == "batched":
+            out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
+        else:
+            out = serving_leg(P, synth, seed=args.seed + 2)
+        print(json.dumps({args.leg: out}))
         return
     run_ours(args, world, rank, local)
 
