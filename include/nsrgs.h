@@ -99,7 +99,8 @@ typedef struct nsrgs_info {
 /* ---------------------------------------------------------------- sizes */
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
- * supported (symmetric layouts need d <= 4 in this build; DENSE_F32 any d <= 64). */
+ * supported (F32 and BF16 symmetric layouts: d <= 8; FP8E4M3: d <= 4;
+ * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
 
 /* Bytes of scratch workspace that every call below accepts for (n, d). */

@@ -132,7 +132,7 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
   }
   NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
-    set_error("symmetric storage needs 1 <= d <= 4 in this build (use NSRGS_DENSE_F32)");
+    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4); use NSRGS_DENSE_F32 or NSRGS_DENSE_BF16");
     return NSRGS_ERR_UNSUPPORTED;
   }
   NSRGS_CUDA_TRY(stream_panel_prepare(*g));

@@ -22,18 +22,20 @@ static int storage_elem_bytes(int storage) {
 }
 
 bool make_panel_geom(int n, int d, int storage, PanelGeom* g) {
-  if (d < 1 || d > 4 || n < 2) return false;
+  if (d < 1 || d > 8 || n < 2) return false;
   int E = storage_elem_bytes(storage);
   if (E == 0) return false;
+  if (d > 4 && storage == NSRGS_FP8E4M3) return false;
   PanelGeom G{};
   G.n = n;
   G.D = d;
   G.storage = storage;
   G.E = E;
   static const int rb_for_d[5] = {0, 8, 4, 2, 1};
-  G.RB = rb_for_d[d];
+  G.RB = d <= 4 ? rb_for_d[d] : 1;
   G.RT = G.RB * d;
-  G.LOADB = (storage == NSRGS_FP8E4M3) ? 8 : 16;
+  // 16-byte row loads (8 for FP8) up to d = 4; two columns per thread above
+  G.LOADB = d <= 4 ? ((storage == NSRGS_FP8E4M3) ? 8 : 16) : 2 * E;
   G.CPT = G.LOADB / E;
   G.SC = 4 * G.CPT;
   G.NW = 8;
@@ -206,7 +208,7 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
   }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
-    set_error("symmetric storage needs 1 <= d <= 4 in this build (use NSRGS_DENSE_F32)");
+    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4); use NSRGS_DENSE_F32 or NSRGS_DENSE_BF16");
     return NSRGS_ERR_UNSUPPORTED;
   }
   std::vector<long long> tab;

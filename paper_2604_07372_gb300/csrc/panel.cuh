@@ -33,7 +33,10 @@ namespace nsrgs {
 template <int D, int RB, int ST>
 struct PCfg {
   static constexpr int E = ST == NSRGS_F32 ? 4 : (ST == NSRGS_BF16 ? 2 : 1);
-  static constexpr int LOADB = ST == NSRGS_FP8E4M3 ? 8 : 16;
+  // bytes per row and step loaded by one thread: 16 (8 for FP8) up to d = 4; for
+  // 5 <= d <= 8 two columns per thread (8 bytes FP32, 4 bytes BF16) keep the
+  // d x d register blocks within the budget
+  static constexpr int LOADB = D <= 4 ? (ST == NSRGS_FP8E4M3 ? 8 : 16) : (ST == NSRGS_F32 ? 8 : (ST == NSRGS_BF16 ? 4 : 2));
   static constexpr int CPT = LOADB / E;
   static constexpr int SC = 4 * CPT;
   static constexpr int NW = 8;
@@ -102,42 +105,60 @@ struct RedLevel<N, D, 3> {
 };
 
 // ---------------------------------------------------- element unpacking
-template <int ST, int CPT>
-struct Unpack;
-
-template <int CPT>
-struct Unpack<NSRGS_F32, CPT> {
-  using V = float4;
-  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
-    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
-  }
-};
-
-template <int CPT>
-struct Unpack<NSRGS_BF16, CPT> {
+// One thread's row load (LOADB bytes) as 32-bit words.
+template <int LOADB>
+struct RawVec;
+template <>
+struct RawVec<16> {
   using V = uint4;
-  __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
-    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      o[2 * k] = __uint_as_float(w[k] << 16);
-      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-  }
+  static constexpr int W = 4;
+  __device__ __forceinline__ static void words(const V& x, uint32_t (&w)[W]) { w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w; }
+};
+template <>
+struct RawVec<8> {
+  using V = uint2;
+  static constexpr int W = 2;
+  __device__ __forceinline__ static void words(const V& x, uint32_t (&w)[W]) { w[0] = x.x; w[1] = x.y; }
+};
+template <>
+struct RawVec<4> {
+  using V = uint32_t;
+  static constexpr int W = 1;
+  __device__ __forceinline__ static void words(const V& x, uint32_t (&w)[W]) { w[0] = x; }
+};
+template <>
+struct RawVec<2> {
+  using V = uint16_t;
+  static constexpr int W = 1;
+  __device__ __forceinline__ static void words(const V& x, uint32_t (&w)[W]) { w[0] = x; }
 };
 
-template <int CPT>
-struct Unpack<NSRGS_FP8E4M3, CPT> {
-  using V = uint2;
+// The CPT stored values of one thread's row load, widened to float32.
+template <int ST, int CPT, int LOADB>
+struct Unpack {
+  using R = RawVec<LOADB>;
+  using V = typename R::V;
   __device__ __forceinline__ static void run(const V& x, float (&o)[CPT]) {
-    const uint32_t w[2] = {x.x, x.y};
+    uint32_t w[R::W];
+    R::words(x, w);
+    if constexpr (ST == NSRGS_F32) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
-      __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
-      float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
-      float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
-      o[4 * k + 0] = a.x; o[4 * k + 1] = a.y; o[4 * k + 2] = b.x; o[4 * k + 3] = b.y;
+      for (int k = 0; k < CPT; ++k) o[k] = __uint_as_float(w[k]);
+    } else if constexpr (ST == NSRGS_BF16) {
+#pragma unroll
+      for (int k = 0; k < CPT / 2; ++k) {
+        o[2 * k] = __uint_as_float(w[k] << 16);
+        o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < CPT / 2; ++k) {
+        const uint32_t pair = (w[k / 2] >> (16 * (k & 1))) & 0xffffu;
+        __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
+        const float2 a = __half22float2(*reinterpret_cast<__half2*>(&h));
+        o[2 * k] = a.x;
+        o[2 * k + 1] = a.y;
+      }
     }
   }
 };
@@ -347,7 +368,8 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
   }
 
   // ---------------------------------------------------------------- consumers
-  using Vec = typename Unpack<ST, C::CPT>::V;
+  using Unp = Unpack<ST, C::CPT, C::LOADB>;
+  using Vec = typename Unp::V;
   const int rg = lane >> 2;
   const int cg = lane & 3;
   int st = 0, slot = 0;
@@ -359,13 +381,8 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     const int n = v.g.n;
     const float* scale =
         (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(v.packed + v.g.off_scale) : nullptr;
-    // Reduced-precision storage does twice (BF16) or four times (FP8) the FMAs per
-    // byte; there the FMAs run in pairs (fma.rn.f32x2 on adjacent columns) and the
-    // row partials are kept as (even-column, odd-column) pairs.
-    constexpr bool kPair = (ST != NSRGS_F32) && (C::CPT % 2 == 0);
     float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
-    float racc[C::RT][D];  // row partials (unpaired path)
-    float2 racc2[kPair ? C::RT : 1][D];  // row partials (paired path)
+    float racc[C::RT][D];  // row partials
     float rsc[RB];         // FP8 row scales
     auto load_rows = [&](int bb) {
 #pragma unroll
@@ -380,7 +397,6 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           for (int k = 0; k < D; ++k) {
             xr[rb * D + r][k] = (i < n) ? v.X[((long long)i * D + r) * D + k] * s : 0.f;
             racc[rb * D + r][k] = 0.f;
-            if constexpr (kPair) racc2[rb * D + r][k] = make_float2(0.f, 0.f);
           }
       }
     };
@@ -390,7 +406,6 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           float x = racc[r][k];
-          if constexpr (kPair) x = racc2[r][k].x + racc2[r][k].y;
           x += __shfl_xor_sync(0xffffffffu, x, 1);
           x += __shfl_xor_sync(0xffffffffu, x, 2);
           racc[r][k] = x;
@@ -428,48 +443,32 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
 #pragma unroll
         for (int rt = 0; rt < C::RT; ++rt)
           raw[rt] = *reinterpret_cast<const Vec*>(stage + warp * C::WB + (rt * 32 + lane) * C::LOADB);
-        float xc[C::CPT * D];
-        const float4* xs = reinterpret_cast<const float4*>(stage + C::STAGE_A) + cg * (C::CPT * D / 4);
+        float xc[C::NV];
+        if constexpr (C::NV % 4 == 0) {
+          const float4* xs = reinterpret_cast<const float4*>(stage + C::STAGE_A) + cg * (C::NV / 4);
 #pragma unroll
-        for (int k = 0; k < C::CPT * D / 4; ++k) {
-          const float4 t = xs[k];
-          xc[4 * k + 0] = t.x; xc[4 * k + 1] = t.y; xc[4 * k + 2] = t.z; xc[4 * k + 3] = t.w;
-        }
-        if constexpr (kPair) {
-          float2 xc2[C::CPT / 2][D];  // (X row of column 2j, of column 2j+1), per component
-#pragma unroll
-          for (int j = 0; j < C::CPT / 2; ++j)
-#pragma unroll
-            for (int k = 0; k < D; ++k) xc2[j][k] = make_float2(xc[(2 * j) * D + k], xc[(2 * j + 1) * D + k]);
-#pragma unroll
-          for (int rt = 0; rt < C::RT; ++rt) {
-            float av[C::CPT];
-            Unpack<ST, C::CPT>::run(raw[rt], av);
-#pragma unroll
-            for (int j = 0; j < C::CPT / 2; ++j) {
-              const float2 a2 = make_float2(av[2 * j], av[2 * j + 1]);
-#pragma unroll
-              for (int k = 0; k < D; ++k) {
-                racc2[rt][k] = __ffma2_rn(a2, xc2[j][k], racc2[rt][k]);
-                float2 c = make_float2(cacc[(2 * j) * D + k], cacc[(2 * j + 1) * D + k]);
-                c = __ffma2_rn(a2, make_float2(xr[rt][k], xr[rt][k]), c);
-                cacc[(2 * j) * D + k] = c.x;
-                cacc[(2 * j + 1) * D + k] = c.y;
-              }
-            }
+          for (int k = 0; k < C::NV / 4; ++k) {
+            const float4 t = xs[k];
+            xc[4 * k + 0] = t.x; xc[4 * k + 1] = t.y; xc[4 * k + 2] = t.z; xc[4 * k + 3] = t.w;
           }
         } else {
+          const float2* xs = reinterpret_cast<const float2*>(stage + C::STAGE_A) + cg * (C::NV / 2);
 #pragma unroll
-          for (int rt = 0; rt < C::RT; ++rt) {
-            float av[C::CPT];
-            Unpack<ST, C::CPT>::run(raw[rt], av);
+          for (int k = 0; k < C::NV / 2; ++k) {
+            const float2 t = xs[k];
+            xc[2 * k + 0] = t.x; xc[2 * k + 1] = t.y;
+          }
+        }
 #pragma unroll
-            for (int cc = 0; cc < C::CPT; ++cc) {
+        for (int rt = 0; rt < C::RT; ++rt) {
+          float av[C::CPT];
+          Unp::run(raw[rt], av);
 #pragma unroll
-              for (int k = 0; k < D; ++k) {
-                racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
-                cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
-              }
+          for (int cc = 0; cc < C::CPT; ++cc) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              racc[rt][k] = fmaf(av[cc], xc[cc * D + k], racc[rt][k]);
+              cacc[cc * D + k] = fmaf(av[cc], xr[rt][k], cacc[cc * D + k]);
             }
           }
         }

@@ -111,7 +111,9 @@ static cudaError_t launch_panel_st(const StreamArgs& a, cudaStream_t st) {
   switch (a.g.storage) {
     case NSRGS_F32: return launch_panel<D, RB, NSRGS_F32>(a, st);
     case NSRGS_BF16: return launch_panel<D, RB, NSRGS_BF16>(a, st);
-    case NSRGS_FP8E4M3: return launch_panel<D, RB, NSRGS_FP8E4M3>(a, st);
+    case NSRGS_FP8E4M3:
+      if constexpr (D <= 4) return launch_panel<D, RB, NSRGS_FP8E4M3>(a, st);
+      break;
   }
   return cudaErrorInvalidValue;
 }
@@ -124,6 +126,10 @@ cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X,
     case 2: return launch_panel_st<2, 4>(a, st);
     case 3: return launch_panel_st<3, 2>(a, st);
     case 4: return launch_panel_st<4, 1>(a, st);
+    case 5: return launch_panel_st<5, 1>(a, st);
+    case 6: return launch_panel_st<6, 1>(a, st);
+    case 7: return launch_panel_st<7, 1>(a, st);
+    case 8: return launch_panel_st<8, 1>(a, st);
   }
   return cudaErrorInvalidValue;
 }

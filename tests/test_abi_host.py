@@ -39,9 +39,11 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_version_and_sizes(L):
     assert "sm_103a" in L.nsrgs_version()
-    # symmetric layouts cover d <= 4; the dense layout any d <= 64
+    # symmetric layouts cover d <= 8 (FP8 d <= 4); the dense layout any d <= 64
     assert L.nsrgs_packed_bytes(200, 3, L.F32) > 0
-    assert L.nsrgs_packed_bytes(200, 5, L.F32) == 0
+    assert L.nsrgs_packed_bytes(200, 8, L.F32) > 0 and L.nsrgs_packed_bytes(200, 5, L.BF16) > 0
+    assert L.nsrgs_packed_bytes(200, 9, L.F32) == 0
+    assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0
     assert L.nsrgs_packed_bytes(200, 25, L.DENSE_F32) == 200 * 25 * 5000 * 4
     assert L.nsrgs_packed_bytes(1, 3, L.F32) == 0
     # BF16 / FP8 shrink the panels by 2x / 4x (plus small tables)

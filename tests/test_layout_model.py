@@ -24,9 +24,10 @@ class Geom:
     def __init__(self, n, d, storage):
         self.n, self.D, self.st = n, d, storage
         self.E = E_OF[storage]
-        self.RB = RB_OF[d]
+        self.RB = RB_OF.get(d, 1)
         self.RT = self.RB * d
-        self.LOADB = 8 if storage == 2 else 16
+        # 16-byte row loads (8 for FP8) up to d = 4, two columns per thread above
+        self.LOADB = (8 if storage == 2 else 16) if d <= 4 else 2 * self.E
         self.CPT = self.LOADB // self.E
         self.SC = 4 * self.CPT
         self.NW = 8
@@ -82,7 +83,8 @@ def slot_coords(g, b, q, W):
     return b * g.SB * g.D + r, b * g.SB * g.D + q * g.SC + c
 
 
-CASES = [(2, 1, 0), (2, 3, 0), (5, 2, 1), (130, 3, 0), (131, 3, 1), (200, 3, 2), (257, 4, 0), (300, 1, 2), (513, 2, 0), (140, 4, 2)]
+CASES = [(2, 1, 0), (2, 3, 0), (5, 2, 1), (130, 3, 0), (131, 3, 1), (200, 3, 2), (257, 4, 0), (300, 1, 2), (513, 2, 0), (140, 4, 2),
+         (3, 5, 0), (70, 5, 1), (67, 6, 0), (66, 7, 1), (130, 8, 0), (65, 8, 1)]
 
 
 @pytest.mark.parametrize("n,d,storage", CASES)
@@ -130,7 +132,7 @@ def test_layout_is_a_bijection_and_rebuilds_AX(n, d, storage):
     assert np.all(Y[N:] == 0.0)
 
 
-@pytest.mark.parametrize("n,d,storage", CASES + [(10000, 3, 0), (10000, 3, 1), (10000, 3, 2), (2000, 4, 0)])
+@pytest.mark.parametrize("n,d,storage", CASES + [(10000, 3, 0), (10000, 3, 1), (10000, 3, 2), (2000, 4, 0), (3000, 8, 0), (2500, 6, 1)])
 def test_packed_bytes_match_library(n, d, storage):
     L = pytest.importorskip("paper_2604_07372_gb300._lib")
     try:
