@@ -94,6 +94,8 @@ typedef struct nsrgs_info {
   double spectral_residual;/* ||A V - V H||_F / ||H||_F at the end of the spectral initialisation */
   uint32_t flags;          /* bit 0: non-finite iterate; bit 1: NS precondition violated;
                               bit 2: spectral initialisation not converged */
+  double objective;        /* nsrgs_solve_objective: F(X) of eq. (1) at the returned X; NaN otherwise */
+  double rel_decrease;     /* nsrgs_solve_objective: the last relative decrease R^t formed; NaN otherwise */
 } nsrgs_info;
 
 /* ---------------------------------------------------------------- sizes */
@@ -175,6 +177,30 @@ nsrgs_status nsrgs_step_static(const nsrgs_A* A, float eta, int K, const float* 
 nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
                          int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
                          size_t ws_bytes, void* st);
+
+/* The least-squares objective of eq. (1) at X (device, nd x d):
+ *   F(X) = 1/2 sum_{i != j} ||X_i X_j^T - A_ij||_F^2,
+ * with A the stored (packed) matrix.  Evaluated as
+ *   1/2 (||X^T X||_F^2 - sum_i ||X_i^T X_i||_F^2) - tr(X^T A_off X) + 1/2 ||A_off||_F^2
+ * from one A pass for A_off X, one for ||A_off||_F^2, and float64 sums of the
+ * d x d terms.  *F (host) is written after a synchronisation of `st`. */
+nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* ws, size_t ws_bytes, void* st);
+
+/* Whole solve with the paper's stopping rule (§4.1): as nsrgs_solve, but the
+ * loop stops after the first iteration t whose relative decrease
+ *   R^t = (F(X^t) - F(X^{t+1})) / F(X^{t+1})
+ * is below rel_tol (the paper: 1e-8 with at most 100 iterations), returning
+ * X^{t+1}; otherwise after T iterations.  F(X^{t+1}) comes from the product
+ * A_off X^{t+1} that the next iteration computes anyway; one extra product
+ * follows the last iteration and one pass computes ||A_off||_F^2.  The decrease
+ * is evaluated in difference form, tr(X'^T A X') - tr(X^T A X) =
+ * tr((X' - X)^T (A X + A X')), so its float32 rounding scales with the update
+ * rather than with F.  info->objective = F(X) at the returned X and
+ * info->rel_decrease = the last R^t formed.  rel_tol may be any finite value
+ * (<= 0: stop only when F does not decrease).  Update-norm fields as nsrgs_solve. */
+nsrgs_status nsrgs_solve_objective(const nsrgs_A* A, float eta, int T, int K, double rel_tol, int init,
+                                   int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
+                                   size_t ws_bytes, void* st);
 
 /* ------------------------------------------------------- batched form */
 

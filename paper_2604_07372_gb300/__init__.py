@@ -25,6 +25,8 @@ from ._lib import (  # noqa: F401
     nsrgs_spectral_init,
     nsrgs_step,
     nsrgs_solve,
+    nsrgs_solve_objective,
+    nsrgs_objective,
     nsrgs_dF,
     nsrgs_version,
     nsrgs_set_kernel_timing,

@@ -51,6 +51,8 @@ class Info(ctypes.Structure):
         ("last_update_norm", ctypes.c_double),
         ("spectral_residual", ctypes.c_double),
         ("flags", ctypes.c_uint32),
+        ("objective", ctypes.c_double),
+        ("rel_decrease", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -76,6 +78,8 @@ def lib() -> ctypes.CDLL:
         "nsrgs_spectral_init": (i, [Ap, vp, i, d, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_step": (i, [Ap, f, i, vp, vp, vp, vp, sz, vp]),
         "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
+        "nsrgs_solve_objective": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
+        "nsrgs_objective": (i, [Ap, vp, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_set_kernel_timing": (i, [i]),
         "nsrgs_kernel_timing": (i, [ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(i)]),
@@ -235,6 +239,52 @@ def nsrgs_solve(
         )
     )
     return X, inf
+
+
+def nsrgs_solve_objective(
+    A: PackedA,
+    eta: float,
+    T: int,
+    K: int,
+    rel_tol: float = 1e-8,
+    init: bool = True,
+    spectral_max_iters: int = 50,
+    X: torch.Tensor | None = None,
+    ws=None,
+    info: bool = True,
+):
+    """Solve with the relative-decrease stopping rule (R^t < rel_tol or T iterations)."""
+    if X is None:
+        X = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    a = A.struct()
+    inf = Info() if info else None
+    _check(
+        lib().nsrgs_solve_objective(
+            ctypes.byref(a),
+            eta,
+            T,
+            K,
+            rel_tol,
+            1 if init else 0,
+            spectral_max_iters,
+            _ptr(X),
+            ctypes.byref(inf) if inf is not None else None,
+            _ptr(w),
+            w.numel(),
+            _stream(),
+        )
+    )
+    return X, inf
+
+
+def nsrgs_objective(A: PackedA, X: torch.Tensor, ws=None) -> float:
+    """F(X) of eq. (1) for the stored A."""
+    w = _ws(A, ws)
+    a = A.struct()
+    out = ctypes.c_double(0.0)
+    _check(lib().nsrgs_objective(ctypes.byref(a), _ptr(X), ctypes.byref(out), _ptr(w), w.numel(), _stream()))
+    return out.value
 
 
 def nsrgs_dF(X: torch.Tensor, Y: torch.Tensor, n: int, d: int, ws=None) -> float:

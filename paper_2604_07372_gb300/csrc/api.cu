@@ -54,6 +54,11 @@ cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, _
 cudaError_t tc_dense_tune(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
                           cudaStream_t st);
 int tc_dense_splits(int n, int d);
+size_t obj_partials_doubles(int n, int D);
+cudaError_t launch_objective(const float* Xc, const float* Yc, const float* Xp, float* Yp, int n, int D,
+                             double rel_tol, const ObjScratch& o, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const PanelGeom& g, const ObjScratch& o,
+                         Ctl* ctl, cudaStream_t st);
 
 constexpr int kMaxReduceGrid = 512;
 constexpr int kMaxSmallD = 8;
@@ -65,6 +70,7 @@ struct Workspace {
   float* Y;
   float* W;
   SpecScratch s;
+  ObjScratch obj;
   __nv_bfloat16* XT;  // X^T in bfloat16 for the tensor-core stream (d >= 16 only)
   size_t bytes;
 };
@@ -94,6 +100,11 @@ static Workspace map_workspace(void* base, int n, int d) {
   w.s.Q = reinterpret_cast<double*>(take(dd));
   w.s.scal = reinterpret_cast<double*>(take(8 * sizeof(double)));
   w.s.partials = reinterpret_cast<double*>(take((size_t)kMaxReduceGrid * 2 * dd));
+  w.obj.scal = reinterpret_cast<double*>(take(OBJ_NSCAL * sizeof(double)));
+  w.obj.Gprev = reinterpret_cast<double*>(take(dd));
+  w.obj.total = reinterpret_cast<double*>(take(dd + 3 * sizeof(double)));
+  w.obj.partials = reinterpret_cast<double*>(take(obj_partials_doubles(n, d) * sizeof(double)));
+  w.obj.Yprev = reinterpret_cast<float*>(take(vec));
   if (d >= 16) w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)d * dense_bf16_pitch(n, d) * 2));
   w.bytes = off;
   return w;
@@ -172,6 +183,7 @@ static cudaError_t maybe_tune(const nsrgs_A* A, const Workspace& w, cudaStream_t
 static cudaError_t reset_ws(const Workspace& w, int n, int d, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.obj.scal, 0, OBJ_NSCAL * sizeof(double), st)) != cudaSuccess) return e;
   const size_t vec = (size_t)xpad_rows(n, d) * d * sizeof(float);
   const size_t body = (size_t)n * d * d * sizeof(float);
   if ((e = cudaMemsetAsync(w.Y, 0, vec, st)) != cudaSuccess) return e;
@@ -204,7 +216,7 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
   return launch_polar_blocks(w.W, out, n, d, st);
 }
 
-enum { METHOD_NSRGS = 0, METHOD_GPM = 1 };
+enum { METHOD_NSRGS = 0, METHOD_GPM = 1, METHOD_NSRGS_OBJECTIVE = 2 };
 
 static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
                                       int K, double tol, int method, cudaStream_t st,
@@ -216,11 +228,24 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = stream_AX(A, g, Xt, w, &w.ctl->stop, st)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if (method == METHOD_GPM)
+    if (method == METHOD_GPM) {
       e = launch_gpm_epilogue(Xt, w.Y, Xn, A->n, A->d, tol, w.ctl, st);
-    else
+    } else if (method == METHOD_NSRGS_OBJECTIVE) {
+      // F(X^t) and R^{t-1} from Y = A_off X^t (Xn still holds X^{t-1}); a stop
+      // leaves X^t as the result and skips this iteration's update
+      e = launch_objective(Xt, w.Y, Xn, w.obj.Yprev, A->n, A->d, tol, w.obj, w.ctl, st);
+      if (e == cudaSuccess) e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, 0.0, w.ctl, nullptr, st);
+    } else {
       e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st);
+    }
     if (e != cudaSuccess) return e;
+  }
+  if (method == METHOD_NSRGS_OBJECTIVE) {
+    // one more product for F(X^T) and R^{T-1} (skipped after a stop)
+    if ((e = stream_AX(A, g, w.X[T & 1], w, &w.ctl->stop, st)) != cudaSuccess) return e;
+    if ((e = launch_objective(w.X[T & 1], w.Y, w.X[(T + 1) & 1], w.obj.Yprev, A->n, A->d, tol, w.obj, w.ctl, st)) !=
+        cudaSuccess)
+      return e;
   }
   return cudaSuccess;
 }
@@ -418,6 +443,42 @@ nsrgs_status nsrgs_gpm_solve(const nsrgs_A* A, int T, double tol, int init, int 
   return solve_impl(A, 1.0f, T, 0, tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv, METHOD_GPM);
 }
 
+nsrgs_status nsrgs_solve_objective(const nsrgs_A* A, float eta, int T, int K, double rel_tol, int init,
+                                   int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
+                                   void* stv) {
+  NSRGS_CHECK_ARG(isfinite(rel_tol), "rel_tol must be finite");
+  return solve_impl(A, eta, T, K, rel_tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv,
+                    METHOD_NSRGS_OBJECTIVE);
+}
+
+nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* ws, size_t ws_bytes, void* stv) {
+  PanelGeom g{};
+  nsrgs_status s = check_A(A, &g);
+  if (s != NSRGS_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(X && aligned16(X) && F, "X must be a 16-byte aligned device pointer and F non-null");
+  const size_t bytes = (size_t)A->n * A->d * A->d * sizeof(float);
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, A->n, A->d);
+  NSRGS_CUDA_TRY(maybe_tune(A, w, st));
+  NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
+  NSRGS_CUDA_TRY(launch_norm2(A->packed, A->n, A->d, A->storage, g, w.obj, w.ctl, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, st));
+  NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
+  NSRGS_CUDA_TRY(launch_objective(w.X[0], w.Y, w.X[1], w.obj.Yprev, A->n, A->d, 0.0, w.obj, w.ctl, st));
+  double oscal[OBJ_NSCAL];
+  Ctl c{};
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(oscal, w.obj.scal, sizeof(oscal), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (c.flags & FLAG_TIMEOUT) {
+    set_error("a device-side wait timed out");
+    return NSRGS_ERR_TIMEOUT;
+  }
+  *F = oscal[OBJ_F];
+  return NSRGS_OK;
+}
+
 static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
                                int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
                                void* stv, int method) {
@@ -433,7 +494,7 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
   NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
   NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");
   NSRGS_CHECK_ARG(T >= 0 && T <= 100000, "T must be in [0, 100000]");
-  NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
+  NSRGS_CHECK_ARG((method == METHOD_NSRGS_OBJECTIVE || tol >= 0.0) && isfinite(tol), "tol must be finite and >= 0");
   NSRGS_CHECK_ARG(!init || (spectral_max_iters >= 1 && spectral_max_iters <= 10000),
                   "spectral_max_iters must be in [1, 10000]");
   NSRGS_CHECK_ARG(X && aligned16(X), "X must be a 16-byte aligned device pointer");
@@ -487,6 +548,7 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     NSRGS_CUDA_TRY(cudaStreamSynchronize(cs));
     NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = reset_ws(w, n, d, cs);
+    if (e == cudaSuccess && method == METHOD_NSRGS_OBJECTIVE) e = launch_norm2(A->packed, n, d, A->storage, g, w.obj, w.ctl, cs);
     if (e == cudaSuccess) {
       if (init) e = enqueue_spectral(A, g, w, spectral_max_iters, 1e-6, w.X[0], cs);
       else e = cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, cs);
@@ -519,8 +581,13 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
   g_timing_state[dev].last_nodes = kernel_nodes;
   if (info) {
     Ctl c{};
+    double oscal[OBJ_NSCAL] = {};
     NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    if (method == METHOD_NSRGS_OBJECTIVE)
+      NSRGS_CUDA_TRY(cudaMemcpyAsync(oscal, w.obj.scal, sizeof(oscal), cudaMemcpyDeviceToHost, st));
     NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+    info->objective = (method == METHOD_NSRGS_OBJECTIVE && oscal[OBJ_EVALS] >= 1.0) ? oscal[OBJ_F] : NAN;
+    info->rel_decrease = (method == METHOD_NSRGS_OBJECTIVE && oscal[OBJ_EVALS] >= 2.0) ? oscal[OBJ_R] : NAN;
     info->spectral_iters = c.spec_iters;
     info->iters = c.iters_done;
     info->last_update_norm = c.last_upd;

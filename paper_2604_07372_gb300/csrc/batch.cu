@@ -56,9 +56,9 @@ struct BatchSrc {
   }
 };
 
-template <int D, int RB, int ST>
-__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_batch_kernel(BatchSrc src) {
-  panel_stream_body<D, RB, ST>(src, src.base(src.cnt));
+template <int D, int ST>
+__global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_stream_batch_kernel(BatchSrc src) {
+  panel_stream_body<D, ST>(src, src.base(src.cnt));
 }
 
 // ------------------------------------------------ per-instance CTA kernels
@@ -295,12 +295,11 @@ __global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
 // ------------------------------------------------------------- launchers
 template <int D, int ST>
 static cudaError_t launch_batch_stream_t(const BatchSrc& s, cudaStream_t st, bool prepare) {
-  constexpr int RB = PanelRB<D>::value;
-  using C = PCfg<D, RB, ST>;
+  using C = PCfg<D, ST>;
   if (prepare)
-    return cudaFuncSetAttribute(panel_stream_batch_kernel<D, RB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(panel_stream_batch_kernel<D, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 C::SMEM);
-  panel_stream_batch_kernel<D, RB, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(s);
+  panel_stream_batch_kernel<D, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(s);
   return cudaGetLastError();
 }
 
@@ -548,6 +547,8 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
       info[i].iters = rep[i].iters;
       info[i].last_update_norm = rep[i].last_upd;
       info[i].spectral_residual = rep[i].spec_res;
+      info[i].objective = NAN;
+      info[i].rel_decrease = NAN;
       info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND)) |
                       ((init && rep[i].spec_res > 1e-6) ? FLAG_SPEC_NOT_CONVERGED : 0u);
       timeout = timeout || (rep[i].flags & FLAG_TIMEOUT);

@@ -78,6 +78,24 @@ struct SpecScratch {
   double* partials;  // per-CTA partial sums
 };
 
+// float64 state of the objective evaluations (eq. (1), §4.1's stopping rule).
+enum : int {
+  OBJ_A2 = 0,         // ||A_off||_F^2 of the stored A
+  OBJ_F = 1,          // F at the latest evaluated iterate
+  OBJ_R = 2,          // relative decrease formed by the latest evaluation (NaN if none)
+  OBJ_S_PREV = 3,     // sum_i ||X_i^T X_i||_F^2 at the latest evaluated iterate
+  OBJ_HAVE_PREV = 4,  // nonzero once an evaluation has been stored
+  OBJ_EVALS = 5,      // evaluations run
+  OBJ_NSCAL = 8,
+};
+struct ObjScratch {
+  double* scal;      // OBJ_* values
+  double* Gprev;     // X^T X at the latest evaluated iterate (d x d)
+  double* total;     // d*d + 3 totals of the running evaluation
+  double* partials;  // per-CTA partial sums
+  float* Yprev;      // A_off X at the latest evaluated iterate (n*d x d)
+};
+
 // ----------------------------------------------------------- panel geometry
 // The symmetric read-once layout ("panel layout") of the packed strict
 // block-upper triangle.  Block rows are grouped into slabs of SB block rows
@@ -94,13 +112,12 @@ struct SpecScratch {
 struct PanelGeom {
   int n, D, storage;
   int E;       // bytes per stored element
-  int RB;      // block rows per thread
-  int RT;      // scalar rows per thread (RB*D)
+  int RT;      // scalar rows per thread
   int LOADB;   // bytes one thread loads per row and step
   int CPT;     // columns per thread (LOADB / E)
   int SC;      // columns per step (4*CPT)
   int NW;      // consumer warps per CTA
-  int SB;      // block rows per slab (NW*8*RB)
+  int SB;      // block rows per slab (NW*8*RT / D)
   int RS;      // scalar rows per slab
   int WROWS;   // rows per warp slice (8*RT)
   int WB;      // bytes per warp slice (WROWS*SC*E)
@@ -113,6 +130,21 @@ struct PanelGeom {
   long long off_byte_off;    // int64[nslabs+1]: byte offset of each slab's panels
   long long off_scale;       // float[n]: FP8 per-block-row scales (absent otherwise)
 };
+
+// Shape of the panel stream per (d, storage): scalar rows per thread (RT) and
+// bytes loaded per row and step by one thread (LOADB).  A thread's d x d work is
+// RT rows x LOADB/E columns against d X columns; RT and LOADB keep its row
+// partials, X rows and column partials in registers (at most 168 with 10 warps
+// per CTA).  NW*8*RT must be a multiple of d so that slabs hold whole block rows.
+__host__ __device__ constexpr int panel_rt(int d, int storage) {
+  return d <= 2 ? 8 : d == 3 ? 6 : d == 4 ? 4 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 4;
+}
+__host__ __device__ constexpr int panel_loadb(int d, int storage) {
+  return storage == NSRGS_FP8E4M3 ? 8
+         : d <= 4                 ? 16
+         : d == 7                 ? (storage == NSRGS_F32 ? 8 : 4)
+                                  : (storage == NSRGS_F32 ? 16 : 8);
+}
 
 // Rows of X/Y padding needed by a layout (columns of the last step run past n*D).
 __host__ __device__ inline int xpad_rows(int n, int D) { return n * D + 64; }

@@ -31,16 +31,14 @@ bool make_panel_geom(int n, int d, int storage, PanelGeom* g) {
   G.D = d;
   G.storage = storage;
   G.E = E;
-  static const int rb_for_d[5] = {0, 8, 4, 2, 1};
-  G.RB = d <= 4 ? rb_for_d[d] : 1;
-  G.RT = G.RB * d;
-  // 16-byte row loads (8 for FP8) up to d = 4; two columns per thread above
-  G.LOADB = d <= 4 ? ((storage == NSRGS_FP8E4M3) ? 8 : 16) : 2 * E;
+  G.RT = panel_rt(d, storage);
+  G.LOADB = panel_loadb(d, storage);
   G.CPT = G.LOADB / E;
   G.SC = 4 * G.CPT;
   G.NW = 8;
-  G.SB = G.NW * 8 * G.RB;
-  G.RS = G.SB * d;
+  G.RS = G.NW * 8 * G.RT;
+  if (G.RS % d != 0) return false;
+  G.SB = G.RS / d;
   G.WROWS = 8 * G.RT;
   G.WB = G.WROWS * G.SC * E;
   G.nslabs = (n + G.SB - 1) / G.SB;

@@ -11,8 +11,8 @@
 //    of the X rows of the step's columns into a ring of shared-memory stages,
 //    completion tracked by mbarriers (expect_tx);
 //  * warps 0..NW-1 (consumers): warp w owns slab rows [w*WROWS, (w+1)*WROWS);
-//    lane (rg, cg) owns RB whole block rows and CPT consecutive columns of each
-//    step.  Row partials of Y accumulate in registers across the whole walk
+//    lane (rg, cg) owns RT consecutive scalar rows and CPT consecutive columns
+//    of each step.  Row partials of Y accumulate in registers across the whole walk
 //    through a slab (reduced over the 4 cg lanes and added to Y once per slab).
 //    Column partials of a step are reduced over the 8 rg lanes with shuffles
 //    and written to a slot of a small shared-memory ring;
@@ -30,20 +30,17 @@
 
 namespace nsrgs {
 
-template <int D, int RB, int ST>
+template <int D, int ST>
 struct PCfg {
   static constexpr int E = ST == NSRGS_F32 ? 4 : (ST == NSRGS_BF16 ? 2 : 1);
-  // bytes per row and step loaded by one thread: 16 (8 for FP8) up to d = 4; for
-  // 5 <= d <= 8 two columns per thread (8 bytes FP32, 4 bytes BF16) keep the
-  // d x d register blocks within the budget
-  static constexpr int LOADB = D <= 4 ? (ST == NSRGS_FP8E4M3 ? 8 : 16) : (ST == NSRGS_F32 ? 8 : (ST == NSRGS_BF16 ? 4 : 2));
+  static constexpr int RT = panel_rt(D, ST);
+  static constexpr int LOADB = panel_loadb(D, ST);
   static constexpr int CPT = LOADB / E;
   static constexpr int SC = 4 * CPT;
   static constexpr int NW = 8;
-  static constexpr int RT = RB * D;
   static constexpr int WROWS = 8 * RT;
-  static constexpr int SB = NW * 8 * RB;
-  static constexpr int RS = SB * D;
+  static constexpr int RS = NW * WROWS;
+  static constexpr int SB = RS / D;
   static constexpr int WB = WROWS * SC * E;
   static constexpr int STAGE_A = NW * WB;
   static constexpr int STAGE_X = SC * D * 4;
@@ -59,13 +56,7 @@ struct PCfg {
   static constexpr int OFF_BARS = OFF_RING + RING * NW * COLVALS * 4;
   static constexpr int SMEM = OFF_BARS + (2 * NSTAGE + 2 * RING) * 8;
   static_assert(COLVALS % 4 == 0 && COLVALS / 4 <= 32, "reducer lanes");
-};
-
-// Block rows per thread for each d (keeps every thread on whole block rows and
-// the register footprint near 110-130 registers).
-template <int D>
-struct PanelRB {
-  static constexpr int value = D == 1 ? 8 : (D == 2 ? 4 : (D == 3 ? 2 : 1));
+  static_assert(RS % D == 0, "slabs of whole block rows");
 };
 
 // ---------------------------------------------------- column reduction
@@ -257,9 +248,9 @@ __device__ __forceinline__ void for_segments(const Src& src, long long g0, long 
   }
 }
 
-template <int D, int RB, int ST, class Src>
+template <int D, int ST, class Src>
 __device__ __forceinline__ void panel_stream_body(const Src& src, long long total_steps) {
-  using C = PCfg<D, RB, ST>;
+  using C = PCfg<D, ST>;
   extern __shared__ __align__(128) uint8_t smem[];
   const long long g0 = total_steps * blockIdx.x / gridDim.x;
   const long long g1 = total_steps * (blockIdx.x + 1) / gridDim.x;
@@ -381,23 +372,20 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     const int n = v.g.n;
     const float* scale =
         (ST == NSRGS_FP8E4M3) ? reinterpret_cast<const float*>(v.packed + v.g.off_scale) : nullptr;
-    float xr[C::RT][D];    // X rows of the thread's RB block rows (times s_i for FP8)
+    float xr[C::RT][D];    // X rows of the thread's RT scalar rows (times s_i for FP8)
     float racc[C::RT][D];  // row partials
-    float rsc[RB];         // FP8 row scales
+    const int nrows = n * D;
     auto load_rows = [&](int bb) {
 #pragma unroll
-      for (int rb = 0; rb < RB; ++rb) {
-        const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
+      for (int rt = 0; rt < C::RT; ++rt) {
+        const int row = bb * C::RS + (warp * 8 + rg) * C::RT + rt;
         float s = 1.f;
-        if (ST == NSRGS_FP8E4M3 && i < n) s = scale[i];
-        rsc[rb] = s;
+        if (ST == NSRGS_FP8E4M3 && row < nrows) s = scale[row / D];
 #pragma unroll
-        for (int r = 0; r < D; ++r)
-#pragma unroll
-          for (int k = 0; k < D; ++k) {
-            xr[rb * D + r][k] = (i < n) ? v.X[((long long)i * D + r) * D + k] * s : 0.f;
-            racc[rb * D + r][k] = 0.f;
-          }
+        for (int k = 0; k < D; ++k) {
+          xr[rt][k] = (row < nrows) ? v.X[(long long)row * D + k] * s : 0.f;
+          racc[rt][k] = 0.f;
+        }
       }
     };
     auto flush_rows = [&](int bb) {
@@ -412,14 +400,12 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
         }
       if (cg == 0) {
 #pragma unroll
-        for (int rb = 0; rb < RB; ++rb) {
-          const int i = bb * C::SB + (warp * 8 + rg) * RB + rb;
-          if (i < n) {
+        for (int rt = 0; rt < C::RT; ++rt) {
+          const int row = bb * C::RS + (warp * 8 + rg) * C::RT + rt;
+          if (row < nrows) {
+            const float s = (ST == NSRGS_FP8E4M3) ? scale[row / D] : 1.f;
 #pragma unroll
-            for (int r = 0; r < D; ++r)
-#pragma unroll
-              for (int k = 0; k < D; ++k)
-                red_add_f32(v.Y + ((long long)i * D + r) * D + k, racc[rb * D + r][k] * rsc[rb]);
+            for (int k = 0; k < D; ++k) red_add_f32(v.Y + (long long)row * D + k, racc[rt][k] * s);
           }
         }
       }

@@ -31,11 +31,11 @@ struct SingleSrc {
   }
 };
 
-template <int D, int RB, int ST>
-__global__ void __launch_bounds__(PCfg<D, RB, ST>::THREADS, 1) panel_stream_kernel(const __grid_constant__ StreamArgs a) {
+template <int D, int ST>
+__global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_stream_kernel(const __grid_constant__ StreamArgs a) {
   if (*a.skip) return;  // written only by earlier launches: uniform
   SingleSrc src{&a};
-  panel_stream_body<D, RB, ST>(src, a.g.total_steps);
+  panel_stream_body<D, ST>(src, a.g.total_steps);
 }
 
 // ------------------------------------------------------------ dense form
@@ -92,27 +92,27 @@ __global__ void __launch_bounds__(256) dense_stream_kernel(const float* __restri
 // ------------------------------------------------------------- launchers
 // Opt-in to the kernel's dynamic shared memory; called outside of any stream
 // capture (cudaFuncSetAttribute is a device-wide setting, idempotent).
-template <int D, int RB, int ST>
+template <int D, int ST>
 static cudaError_t prepare_panel() {
-  using C = PCfg<D, RB, ST>;
-  return cudaFuncSetAttribute(panel_stream_kernel<D, RB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  using C = PCfg<D, ST>;
+  return cudaFuncSetAttribute(panel_stream_kernel<D, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
 }
 
-template <int D, int RB, int ST>
+template <int D, int ST>
 static cudaError_t launch_panel(const StreamArgs& a, cudaStream_t st) {
-  using C = PCfg<D, RB, ST>;
-  if (a.g.n < 0) return prepare_panel<D, RB, ST>();  // preparation request
-  panel_stream_kernel<D, RB, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(a);
+  using C = PCfg<D, ST>;
+  if (a.g.n < 0) return prepare_panel<D, ST>();  // preparation request
+  panel_stream_kernel<D, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int D, int RB>
+template <int D>
 static cudaError_t launch_panel_st(const StreamArgs& a, cudaStream_t st) {
   switch (a.g.storage) {
-    case NSRGS_F32: return launch_panel<D, RB, NSRGS_F32>(a, st);
-    case NSRGS_BF16: return launch_panel<D, RB, NSRGS_BF16>(a, st);
+    case NSRGS_F32: return launch_panel<D, NSRGS_F32>(a, st);
+    case NSRGS_BF16: return launch_panel<D, NSRGS_BF16>(a, st);
     case NSRGS_FP8E4M3:
-      if constexpr (D <= 4) return launch_panel<D, RB, NSRGS_FP8E4M3>(a, st);
+      if constexpr (D <= 4) return launch_panel<D, NSRGS_FP8E4M3>(a, st);
       break;
   }
   return cudaErrorInvalidValue;
@@ -122,14 +122,14 @@ cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X,
                          const int* skip, cudaStream_t st) {
   StreamArgs a{reinterpret_cast<const uint8_t*>(packed), X, Y, ctl, skip, g};
   switch (g.D) {
-    case 1: return launch_panel_st<1, 8>(a, st);
-    case 2: return launch_panel_st<2, 4>(a, st);
-    case 3: return launch_panel_st<3, 2>(a, st);
-    case 4: return launch_panel_st<4, 1>(a, st);
-    case 5: return launch_panel_st<5, 1>(a, st);
-    case 6: return launch_panel_st<6, 1>(a, st);
-    case 7: return launch_panel_st<7, 1>(a, st);
-    case 8: return launch_panel_st<8, 1>(a, st);
+    case 1: return launch_panel_st<1>(a, st);
+    case 2: return launch_panel_st<2>(a, st);
+    case 3: return launch_panel_st<3>(a, st);
+    case 4: return launch_panel_st<4>(a, st);
+    case 5: return launch_panel_st<5>(a, st);
+    case 6: return launch_panel_st<6>(a, st);
+    case 7: return launch_panel_st<7>(a, st);
+    case 8: return launch_panel_st<8>(a, st);
   }
   return cudaErrorInvalidValue;
 }

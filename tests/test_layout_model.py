@@ -17,23 +17,34 @@ import pytest
 import synth
 
 E_OF = {0: 4, 1: 2, 2: 1}
-RB_OF = {1: 8, 2: 4, 3: 2, 4: 1}
+# scalar rows per thread, per d
+RT_OF = {1: 8, 2: 8, 3: 6, 4: 4, 5: 5, 6: 6, 7: 7, 8: 4}
+
+
+def loadb(d, storage):
+    """Bytes one thread loads per row and step."""
+    if storage == 2:
+        return 8
+    if d <= 4:
+        return 16
+    if d == 7:
+        return 8 if storage == 0 else 4
+    return 16 if storage == 0 else 8
 
 
 class Geom:
     def __init__(self, n, d, storage):
         self.n, self.D, self.st = n, d, storage
         self.E = E_OF[storage]
-        self.RB = RB_OF.get(d, 1)
-        self.RT = self.RB * d
-        # 16-byte row loads (8 for FP8) up to d = 4, two columns per thread above
-        self.LOADB = (8 if storage == 2 else 16) if d <= 4 else 2 * self.E
+        self.RT = RT_OF[d]
+        self.LOADB = loadb(d, storage)
         self.CPT = self.LOADB // self.E
         self.SC = 4 * self.CPT
         self.NW = 8
-        self.SB = self.NW * 8 * self.RB
-        self.RS = self.SB * d
         self.WROWS = 8 * self.RT
+        self.RS = self.NW * self.WROWS
+        assert self.RS % d == 0
+        self.SB = self.RS // d
         self.WB = self.WROWS * self.SC * self.E
         self.nslabs = -(-n // self.SB)
 
