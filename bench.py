@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
+    ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
     return ap.parse_args()
 
 
@@ -268,7 +269,7 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     out = {}
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
-        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 8 else []) + (["dense_bf16"] if d in (16, 32, 64) else [])
+        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 8 else []) + (["dense_bf16", "bf16"] if d in (16, 32, 64) else [])
         res = {}
         Zs = Z.reshape(n * d, d)
         nb = n * (n - 1) // 2 * d * d
@@ -716,7 +717,7 @@ def main():
         torch.cuda.set_device(local)
         if args.leg == "sweep":
             dims = tuple(int(x) for x in args.sweep_dims.split(","))
-            out = dsweep_leg(P, synth, seed=args.seed + 3, dims=dims, reps=args.sweep_reps)
+            out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps)
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
         else:

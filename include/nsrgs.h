@@ -55,7 +55,11 @@ typedef enum {
 
 /* Storage precision of the packed A.  Arithmetic is float32 in every case.
  *  F32     : A stored as float32.
- *  BF16    : A rounded to bfloat16 (round to nearest even).
+ *  BF16    : A rounded to bfloat16 (round to nearest even).  For d <= 8 the panel
+ *            layout on the CUDA cores; for d in {16, 32, 64} the tile-upper layout
+ *            on the tensor cores (128 x 128 tiles of the upper triangle, each feeding
+ *            Y_I += A_IJ X_J and Y_J += A_IJ^T X_I through tcgen05 with X rounded to
+ *            bfloat16, float32 accumulation in TMEM): half the bytes of DENSE_BF16.
  *  FP8E4M3 : A stored as FP8 E4M3 (round to nearest, saturating at +-448) with one
  *            float32 scale per block row i: s_i = max_{j>i} max|A_ij| / 448 and
  *            A_ij ~ s_i * q_ij.  The per-block-row scale is this library's choice;
@@ -101,7 +105,7 @@ typedef struct nsrgs_info {
 /* ---------------------------------------------------------------- sizes */
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
- * supported (F32 and BF16 symmetric layouts: d <= 8; FP8E4M3: d <= 4;
+ * supported (F32: d <= 8; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4;
  * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
 

@@ -54,6 +54,12 @@ cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, _
 cudaError_t tc_dense_tune(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
                           cudaStream_t st);
 int tc_dense_splits(int n, int d);
+bool tc_sym_supported(int d);
+long long tc_sym_bytes(int n, int d);
+long long tc_sym_xt_bytes(int n, int d);
+cudaError_t tc_sym_prepare(int d);
+cudaError_t tc_sym_product(const void* packed, int n, int d, const float* X, uint8_t* xt, float* Y, Ctl* ctl,
+                           const int* skip, cudaStream_t st);
 size_t obj_partials_doubles(int n, int D);
 cudaError_t launch_objective(const float* Xc, const float* Yc, const float* Xp, float* Yp, int n, int D,
                              double rel_tol, const ObjScratch& o, Ctl* ctl, cudaStream_t st);
@@ -105,7 +111,11 @@ static Workspace map_workspace(void* base, int n, int d) {
   w.obj.total = reinterpret_cast<double*>(take(dd + 3 * sizeof(double)));
   w.obj.partials = reinterpret_cast<double*>(take(obj_partials_doubles(n, d) * sizeof(double)));
   w.obj.Yprev = reinterpret_cast<float*>(take(vec));
-  if (d >= 16) w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)d * dense_bf16_pitch(n, d) * 2));
+  if (d >= 16) {
+    // X^T in bfloat16: row-major for the dense stream, swizzled tiles for the tile-upper stream
+    const long long a = (long long)d * dense_bf16_pitch(n, d) * 2, b = tc_sym_xt_bytes(n, d);
+    w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)(a > b ? a : b)));
+  }
   w.bytes = off;
   return w;
 }
@@ -142,8 +152,12 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     return NSRGS_OK;
   }
   NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
+  if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d)) {
+    NSRGS_CUDA_TRY(tc_sym_prepare(A->d));
+    return NSRGS_OK;
+  }
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
-    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4); use NSRGS_DENSE_F32 or NSRGS_DENSE_BF16");
+    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4) or BF16 with d in {16, 32, 64}; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   NSRGS_CUDA_TRY(stream_panel_prepare(*g));
@@ -166,6 +180,8 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
                              const int* skip, cudaStream_t st) {
   if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, w.Y, skip, st);
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
+  if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d))
+    return tc_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl, skip, st);
   return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
 }
 
@@ -334,6 +350,7 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (storage == NSRGS_DENSE_F32) return (size_t)n * d * (size_t)dense_pitch(n, d) * sizeof(float);
   if (storage == NSRGS_DENSE_BF16)
     return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
+  if (storage == NSRGS_BF16 && tc_sym_supported(d)) return (size_t)tc_sym_bytes(n, d);
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) return 0;
   return (size_t)(g.header_bytes + g.panel_bytes);

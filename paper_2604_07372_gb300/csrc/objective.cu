@@ -241,6 +241,8 @@ cudaError_t launch_objective(const float* Xc, const float* Yc, const float* Xp, 
 
 long long dense_pitch(int n, int d);
 long long dense_bf16_pitch(int n, int d);
+bool tc_sym_supported(int d);
+long long tc_sym_bytes(int n, int d);
 
 cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const PanelGeom& g, const ObjScratch& o,
                          Ctl* ctl, cudaStream_t st) {
@@ -251,6 +253,10 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
   } else if (storage == NSRGS_DENSE_BF16) {
     const long long count = (long long)n * d * dense_bf16_pitch(n, d);
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), count, 1.0, o, ctl);
+  } else if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
+    // tile-upper layout: the upper triangle once, everything else zero
+    norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), tc_sym_bytes(n, d) / 2, 2.0,
+                                            o, ctl);
   } else if (storage == NSRGS_F32) {
     const uint8_t* p = reinterpret_cast<const uint8_t*>(packed) + g.header_bytes;
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(p), g.panel_bytes / 4, 2.0, o, ctl);

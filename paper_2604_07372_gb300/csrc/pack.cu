@@ -8,7 +8,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "common.cuh"
+#include "src.cuh"
 
 namespace nsrgs {
 
@@ -72,33 +72,6 @@ static void panel_tables(const PanelGeom& G, std::vector<long long>& tab) {
     }
   }
 }
-
-// Source accessors: element (row, col) of A_off (zero on/below the block diagonal
-// and outside the matrix), read from the canonical upper-block list or a dense matrix.
-struct UpperSrc {
-  const float* p;
-  int n, d;
-  __device__ float operator()(long long row, long long col) const {
-    long long N = (long long)n * d;
-    if (row >= N || col >= N) return 0.f;
-    long long i = row / d, j = col / d;
-    if (j <= i) return 0.f;
-    long long a = row - i * d, bcol = col - j * d;
-    long long idx = i * n - i * (i + 1) / 2 + (j - i - 1);
-    return p[idx * d * d + a * d + bcol];
-  }
-};
-
-struct DenseSrc {
-  const float* p;
-  int n, d;
-  __device__ float operator()(long long row, long long col) const {
-    long long N = (long long)n * d;
-    if (row >= N || col >= N) return 0.f;
-    if (col / d <= row / d) return 0.f;
-    return p[row * N + col];
-  }
-};
 
 // FP8 scales: s_i = max_{j > i} max |A_ij| / 448 (1 when the row is all zero).
 template <class Src>
@@ -189,6 +162,9 @@ __global__ void pack_dense_kernel(Src src, int n, int d, int pitch, T* out) {
 
 long long dense_pitch(int n, int d) { return ((long long)n * d + 3) / 4 * 4; }
 long long dense_bf16_pitch(int n, int d);
+bool tc_sym_supported(int d);
+template <class Src>
+cudaError_t tc_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st);
 
 template <class Src>
 static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, cudaStream_t st) {
@@ -204,9 +180,13 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
     NSRGS_CUDA_TRY(cudaGetLastError());
     return NSRGS_OK;
   }
+  if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
+    NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, packed, st));
+    return NSRGS_OK;
+  }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
-    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4); use NSRGS_DENSE_F32 or NSRGS_DENSE_BF16");
+    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4) or BF16 with d in {16, 32, 64}; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   std::vector<long long> tab;

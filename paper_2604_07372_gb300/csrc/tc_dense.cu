@@ -25,7 +25,7 @@
 #include <mutex>
 #include <string>
 
-#include "common.cuh"
+#include "tc_common.cuh"
 
 namespace nsrgs {
 
@@ -40,9 +40,7 @@ struct TcCfg {
   static constexpr int TMEM_COLS = N < 32 ? 32 : N;   // power of two >= 32
   static constexpr int OFF_BARS = NSTAGE * STAGE;
   static constexpr int SMEM = 1024 + OFF_BARS + (2 * NSTAGE + 2) * 8 + 16;
-  // instruction descriptor, kind::f16: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC = tc_idesc(BM, N, false);  // both operands K-major
   static_assert(STAGE % 1024 == 0, "stages must keep 1024-byte swizzle alignment");
 };
 
@@ -56,18 +54,6 @@ struct TcArgs {
   int splits;      // K chunks per row tile
 };
 
-// Shared-memory matrix descriptor: K-major operand with 128-byte swizzle,
-// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
-  return d;
-}
-
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -75,37 +61,6 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* t
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int N>
 __global__ void __launch_bounds__(192, 1)
@@ -133,12 +88,7 @@ __global__ void __launch_bounds__(192, 1)
     failed = 0;
     fence_mbar_init();
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)C::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc_warp(tmem_slot, (uint32_t)C::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -191,7 +141,7 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
         for (int kk = 0; kk < C::BK / 16; ++kk)
-          tc_mma(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC, (ks > kb || kk > 0) ? 1u : 0u);
+          tc_mma(tmem, sw128_desc(sa + kk * 32, 16, 1024), sw128_desc(sb + kk * 32, 16, 1024), C::IDESC, (ks > kb || kk > 0) ? 1u : 0u);
         tc_commit(&empty[st]);
         if (++st == C::NSTAGE) {
           st = 0;
@@ -235,8 +185,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
-                 : "memory");
+    tmem_dealloc_warp(tmem, (uint32_t)C::TMEM_COLS);
   }
 }
 

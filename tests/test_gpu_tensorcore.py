@@ -1,8 +1,10 @@
-"""Tensor-core (tcgen05) A stream for d in {16, 32, 64}: NSRGS_DENSE_BF16.
+"""Tensor-core (tcgen05) A streams for d in {16, 32, 64}: the dense form
+(NSRGS_DENSE_BF16, both triangles) and the symmetric tile-upper form (NSRGS_BF16
+at these d: each stored tile feeds Y_I += A_IJ X_J and Y_J += A_IJ^T X_I).
 
 The product is checked against an exact float64 product of the same
-bfloat16-rounded A and X (the kernel rounds X to bfloat16 for the multiply and
-accumulates in float32), then whole solves against the float32 path: final
+bfloat16-rounded A and X (the kernels round X to bfloat16 for the multiply and
+accumulate in float32), then whole solves against the float32 path: final
 d_F(X, Z) within 1%.
 """
 import math
@@ -31,14 +33,18 @@ def bf16_round(a):
     return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("n,d", [(20, 16), (9, 32), (5, 64), (300, 16), (130, 32), (70, 64)])
-def test_tensor_core_product(P, n, d):
+PRODUCT_CASES = [(2, 16), (20, 16), (9, 32), (5, 64), (300, 16), (130, 32), (70, 64), (8, 16), (17, 64), (1000, 16)]
+
+
+@pytest.mark.parametrize("storage", ["dense_bf16", "bf16"])
+@pytest.mark.parametrize("n,d", PRODUCT_CASES)
+def test_tensor_core_product(P, n, d, storage):
     inst = synth.make_instance(n, d, 0.5, seed=n + d, dtype=np.float32)
     A = inst.dense()
     for i in range(n):
         A[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
     X = np.random.default_rng(d).standard_normal((n * d, d)).astype(np.float32)
-    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.DENSE_BF16)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.STORAGE[storage])
     Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
     torch.cuda.synchronize()
     Ab, Xb = bf16_round(A), bf16_round(X)
@@ -48,16 +54,37 @@ def test_tensor_core_product(P, n, d):
     assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-6), np.max(np.abs(got - ref) / (scale + 1e-6))
 
 
-@pytest.mark.parametrize("n,d", [(200, 16), (80, 32)])
-def test_tensor_core_solve_within_one_percent(P, n, d):
+@pytest.mark.parametrize("storage", ["dense_bf16", "bf16"])
+@pytest.mark.parametrize("n,d", [(200, 16), (80, 32), (40, 64)])
+def test_tensor_core_solve_within_one_percent(P, n, d, storage):
     T, K = 40, 2
     inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=7 * d, dtype=np.float32)
     up = torch.from_numpy(inst.upper).cuda()
     Xf, _ = P.nsrgs_solve(P.nsrgs_pack_upper(up, n, d, P.DENSE_F32), 1.0 / n, T, K)
-    Xb, info = P.nsrgs_solve(P.nsrgs_pack_upper(up, n, d, P.DENSE_BF16), 1.0 / n, T, K)
+    Xb, info = P.nsrgs_solve(P.nsrgs_pack_upper(up, n, d, P.STORAGE[storage]), 1.0 / n, T, K)
     torch.cuda.synchronize()
     Z = inst.Zstack()
     ef = O.dF(Xf.double().cpu().numpy(), Z, d)
     eb = O.dF(Xb.double().cpu().numpy(), Z, d)
     assert info.iters == T
     assert abs(eb - ef) / ef <= 0.01, (ef, eb)
+
+
+def test_tile_upper_bytes_are_about_half_of_dense(P):
+    for n, d in [(2000, 16), (1000, 32), (500, 64)]:
+        dense = P.nsrgs_packed_bytes(n, d, P.DENSE_BF16)
+        sym = P.nsrgs_packed_bytes(n, d, P.BF16)
+        assert 0.49 < sym / dense < 0.53, (n, d, sym / dense)
+
+
+@pytest.mark.parametrize("n,d", [(500, 16), (64, 64)])
+def test_tile_upper_objective_equals_dense_bf16(P, n, d):
+    """F(X) through the tile-upper layout (its ||A_off||^2 pass reads the stored
+    triangle once, weighted twice) equals F through the dense BF16 layout (both
+    triangles): the same bfloat16 values and the same bfloat16-rounded X."""
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=3 + d, dtype=np.float32)
+    up = torch.from_numpy(inst.upper).cuda()
+    X = torch.from_numpy(inst.Zstack().astype(np.float32)).cuda()
+    Ft = P.nsrgs_objective(P.nsrgs_pack_upper(up, n, d, P.BF16), X)
+    Fd = P.nsrgs_objective(P.nsrgs_pack_upper(up, n, d, P.DENSE_BF16), X)
+    assert abs(Ft - Fd) <= 1e-6 * abs(Fd), (Ft, Fd)
