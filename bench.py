@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
-    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving"],
+    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving", "sparse"],
                     help="run only one extra leg (prints its JSON, no metric line), for profiling")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
@@ -315,6 +315,53 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
         del up, Z
         torch.cuda.empty_cache()
     return out
+
+
+# ------------------------------------------------------------- sparse leg
+def sparse_leg(P, synth, seed: int, n: int = 8000, d: int = 3, ps=(0.05, 0.2, 0.5), reps: int = 10, T: int = 50):
+    """Incomplete observations (pairs kept with probability p, unobserved A_ij = 0),
+    n = 8000, d = 3, c = 0.3: the A-stream product and short solves (T = 50,
+    eta = 1/n) with the symmetric FP32 panels (zeros stored) against the
+    block-sparse rows (FP32, BF16) whose bytes scale with p."""
+    import torch
+
+    out = {}
+    for p in ps:
+        Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed, p=p)
+        Zs = Z.reshape(n * d, d)
+        res = {}
+        for name in ("f32", "bcsr_f32", "bcsr_bf16"):
+            try:
+                pa = P.nsrgs_pack_upper(up, n, d, P.STORAGE[name])
+                ws = P.workspace(n, d)
+                X = torch.randn(n * d, d, device="cuda")
+                Y = torch.empty_like(X)
+                P.nsrgs_product(pa, X, Y, ws=ws)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    P.nsrgs_product(pa, X, Y, ws=ws)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                ent = {"product_ms": ms, "stored_GB": pa.nbytes / 1e9, "GBps": pa.nbytes / (ms / 1e3) / 1e9}
+                Xs, _ = P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, ws=ws)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                Xs, _ = P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, X=Xs, ws=ws)
+                torch.cuda.synchronize()
+                ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
+                ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
+                res[name] = ent
+                del pa, ws, X, Y
+            except Exception as e:
+                res[name] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+            torch.cuda.empty_cache()
+        out[f"p{p}"] = res
+        del up, Z
+        torch.cuda.empty_cache()
+    return {"n": n, "d": d, "T": T, "per_p": out}
 
 
 # ------------------------------------------------------------ serving leg
@@ -720,6 +767,8 @@ def main():
             out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps)
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
+        elif args.leg == "sparse":
+            out = sparse_leg(P, synth, seed=args.seed + 4)
         else:
             out = serving_leg(P, synth, seed=args.seed + 2)
         print(json.dumps({args.leg: out}))

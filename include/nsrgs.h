@@ -69,13 +69,24 @@ typedef enum {
  *            symmetric layouts are measured against.
  *  DENSE_BF16: the full matrix in bfloat16 for d in {16, 32, 64}, multiplied on the
  *            tensor cores (tcgen05, float32 accumulation in TMEM) with X rounded to
- *            bfloat16 for the product; the d x d work stays float32. */
+ *            bfloat16 for the product; the d x d work stays float32.
+ *  BCSR_F32 / BCSR_BF16: block-sparse rows for incomplete observations (§4.1's
+ *            sampling model, unobserved A_ij = 0), d <= 8: only blocks with a
+ *            nonzero entry are stored, both A_ij and A_ji = A_ij^T, each block row
+ *            complete and sorted by j, so one warp owns a row and no atomics are
+ *            needed.  Bytes per A pass ~ 2 p (n^2 - n) d^2 E: below the symmetric
+ *            panels whenever the observed fraction p < 1/2.  The exact size depends
+ *            on the data: nsrgs_bcsr_packed_bytes; nsrgs_packed_bytes returns the
+ *            bound for p = 1.  Single-instance calls only (not the batched or served
+ *            forms). */
 typedef enum {
   NSRGS_F32 = 0,
   NSRGS_BF16 = 1,
   NSRGS_FP8E4M3 = 2,
   NSRGS_DENSE_F32 = 3,
-  NSRGS_DENSE_BF16 = 4
+  NSRGS_DENSE_BF16 = 4,
+  NSRGS_BCSR_F32 = 5,
+  NSRGS_BCSR_BF16 = 6
 } nsrgs_storage;
 
 /* A packed measurement matrix.  `packed` is the device buffer written by
@@ -97,7 +108,8 @@ typedef struct nsrgs_info {
   double last_update_norm; /* ||X^{t+1} - X^t||_F / sqrt(nd) of the last iteration run */
   double spectral_residual;/* ||A V - V H||_F / ||H||_F at the end of the spectral initialisation */
   uint32_t flags;          /* bit 0: non-finite iterate; bit 1: NS precondition violated;
-                              bit 2: spectral initialisation not converged */
+                              bit 2: spectral initialisation not converged;
+                              bit 4: the safeguarded Newton-Schulz start acted */
   double objective;        /* nsrgs_solve_objective: F(X) of eq. (1) at the returned X; NaN otherwise */
   double rel_decrease;     /* nsrgs_solve_objective: the last relative decrease R^t formed; NaN otherwise */
 } nsrgs_info;
@@ -106,11 +118,21 @@ typedef struct nsrgs_info {
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
  * supported (F32: d <= 8; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4;
- * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}). */
+ * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}; BCSR_*: d <= 8, the
+ * bound for fully observed data -- see nsrgs_bcsr_packed_bytes for the exact size). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
 
 /* Bytes of scratch workspace that every call below accepts for (n, d). */
 size_t nsrgs_workspace_bytes(int n, int d);
+
+/* Exact bytes of a block-sparse packed buffer (storage NSRGS_BCSR_F32 or
+ * NSRGS_BCSR_BF16) for the given data: `src` (device, float32) is the canonical
+ * upper-block list (src_is_dense = 0) or the dense nd x nd matrix (src_is_dense
+ * != 0), as passed to nsrgs_pack_upper / nsrgs_pack_dense.  Counts the blocks
+ * with a nonzero entry on the device (using the workspace), then synchronises
+ * `st` and writes *bytes (host). */
+nsrgs_status nsrgs_bcsr_packed_bytes(const float* src, int src_is_dense, int n, int d, int storage, size_t* bytes,
+                                     void* ws, size_t ws_bytes, void* st);
 
 /* ------------------------------------------------------------- packing */
 
@@ -206,6 +228,32 @@ nsrgs_status nsrgs_solve_objective(const nsrgs_A* A, float eta, int T, int K, do
                                    int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
                                    size_t ws_bytes, void* st);
 
+/* Options of nsrgs_solve_ex.
+ *  stop_rule    : NSRGS_STOP_UPDATE_NORM -- stop after the first iteration with
+ *                 ||X^{t+1} - X^t||_F / sqrt(nd) < tol (tol = 0: run T iterations),
+ *                 as nsrgs_solve; NSRGS_STOP_REL_DECREASE -- the paper's rule
+ *                 R^t < tol (§4.1), as nsrgs_solve_objective.
+ *  ns_safeguard : nonzero selects a safeguarded Newton-Schulz start, which is not
+ *                 part of the paper: a block whose F_i fails Lemma 2.1's
+ *                 precondition (checked as ||I - F_i^T F_i||_F >= 1) starts
+ *                 Algorithm 1 from F_i / ||F_i||_F, whose singular values lie in
+ *                 (0, 1] and whose polar factor is that of F_i.  Blocks that meet
+ *                 the precondition are untouched, so where it always holds the
+ *                 result is Algorithm 2's.  It keeps large steps on sparse data
+ *                 (e.g. the paper's mu = 1/(np) at p = 0.05) finite, where plain
+ *                 Newton-Schulz overflows; info->flags bit 4 reports that it acted. */
+enum { NSRGS_STOP_UPDATE_NORM = 0, NSRGS_STOP_REL_DECREASE = 1 };
+typedef struct nsrgs_solve_opts {
+  int stop_rule;
+  double tol;
+  int ns_safeguard;
+} nsrgs_solve_opts;
+
+/* nsrgs_solve / nsrgs_solve_objective with explicit options (opts non-null). */
+nsrgs_status nsrgs_solve_ex(const nsrgs_A* A, float eta, int T, int K, const nsrgs_solve_opts* opts, int init,
+                            int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
+                            void* st);
+
 /* ------------------------------------------------------- batched form */
 
 /* One independent instance of a batch. */
@@ -214,6 +262,7 @@ typedef struct nsrgs_batch_item {
   int n;
   float eta;          /* step size of this instance */
   float* X;           /* device, nd x d: result; also X^0 on entry when init == 0 */
+  int ns_safeguard;   /* nonzero: safeguarded Newton-Schulz start (see nsrgs_solve_opts) */
 } nsrgs_batch_item;
 
 /* Workspace bytes for a batch of `count` instances with sizes n[0..count-1] and
@@ -258,6 +307,7 @@ typedef struct nsrgs_server_config {
   int spectral_max_iters;  /* subspace-iteration passes cap per request */
   double spectral_tol;     /* subspace residual target (e.g. 1e-6) */
   int ticks_per_step;      /* ticks per nsrgs_server_step call */
+  int ns_safeguard;        /* nonzero: safeguarded Newton-Schulz start for every request */
 } nsrgs_server_config;
 
 typedef struct nsrgs_server_result {

@@ -45,6 +45,7 @@ __all__ = [
     "tangent_projection",
     "euclidean_gradient",
     "nsrgs_iteration",
+    "ns_safeguard",
     "nsrgs_rows_update",
     "spectral_init",
     "nsrgs",
@@ -123,16 +124,46 @@ def euclidean_gradient(A: np.ndarray, X: np.ndarray, n: int, d: int) -> np.ndarr
     return (n - 1) * Xb - offdiag
 
 
+# ------------------- beyond the paper: safeguarded Newton-Schulz start
+def ns_safeguard(F: np.ndarray) -> np.ndarray:
+    """Safeguarded start of Algorithm 1 (not part of the paper's method).
+
+    Lemma 2.1 needs ||I - F_i^T F_i|| < 1 for the Newton-Schulz iteration to
+    converge; the test here uses the Frobenius norm (an upper bound of the
+    spectral norm).  A block F_i that fails it is replaced by F_i / ||F_i||_F:
+    its singular values move into (0, 1], where the Newton-Schulz map converges
+    to the polar factor, and the polar factor itself is unchanged
+    (sgn(c F) = sgn(F) for c > 0).  Blocks that pass are left as they are, so
+    on data where the precondition always holds this is Algorithm 2 exactly.
+    Accepts one d x d matrix or a stack (n, d, d).
+    """
+    F = np.array(F, dtype=np.float64, copy=True)
+    one = F.ndim == 2
+    if one:
+        F = F[None]
+    d = F.shape[-1]
+    E = np.eye(d) - np.swapaxes(F, -1, -2) @ F
+    bad = np.sqrt(np.sum(E * E, axis=(-2, -1))) >= 1.0
+    norms = np.sqrt(np.sum(F * F, axis=(-2, -1)))
+    F[bad] = F[bad] / norms[bad][:, None, None]
+    return F[0] if one else F
+
+
 # ------------------------------------------ Algorithm 2: one iteration
-def nsrgs_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, Ts: int) -> np.ndarray:
+def nsrgs_iteration(
+    A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, Ts: int, safeguard: bool = False
+) -> np.ndarray:
     """One sweep of Algorithm 2's loop body for all i, every block from X^t.
 
     G_i = sum_{j != i}(X_i - A_ij X_j);  F_i = X_i - mu P_{X_i}(G_i);
-    X_i^{t+1} = S(F_i) with S = Algorithm 1 run for Ts steps.
+    X_i^{t+1} = S(F_i) with S = Algorithm 1 run for Ts steps.  With
+    ``safeguard`` the Newton-Schulz start is ``ns_safeguard(F)`` (beyond the paper).
     """
     Xb = blocks(X, d)
     G = euclidean_gradient(A, X, n, d)
     F = Xb - mu * tangent_projection(Xb, G)
+    if safeguard:
+        F = ns_safeguard(F)
     return stack(newton_schulz(F, Ts))
 
 
@@ -209,6 +240,7 @@ def nsrgs(
     X0: np.ndarray | None = None,
     rel_tol: float | None = None,
     history: bool = False,
+    safeguard: bool = False,
 ):
     """Algorithm 2: spectral start (unless X0 is given), then up to T iterations.
 
@@ -216,7 +248,7 @@ def nsrgs(
     decrease R^t = (F(X^t) - F(X^{t+1})) / F(X^{t+1}) is below it (§4.1's rule:
     R^t < 1e-8 or 100 iterations).  Returns (X, info) where info holds the
     number of iterations run and, with ``history``, every iterate's update
-    norm ||X^{t+1} - X^t||_F / sqrt(nd).
+    norm ||X^{t+1} - X^t||_F / sqrt(nd).  ``safeguard`` as in ``nsrgs_iteration``.
     """
     if X0 is None:
         X0, _ = spectral_init(A, n, d)
@@ -224,7 +256,7 @@ def nsrgs(
     info = {"iters": 0, "upd": []}
     Fcur = objective(A, X, n, d) if rel_tol is not None else None
     for t in range(T):
-        Xn = nsrgs_iteration(A, X, n, d, mu, Ts)
+        Xn = nsrgs_iteration(A, X, n, d, mu, Ts, safeguard)
         if history:
             info["upd"].append(update_norm(Xn, X))
         info["iters"] = t + 1

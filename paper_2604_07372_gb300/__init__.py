@@ -12,6 +12,8 @@ from ._lib import (  # noqa: F401
     FP8E4M3,
     DENSE_F32,
     DENSE_BF16,
+    BCSR_F32,
+    BCSR_BF16,
     STORAGE,
     NsrgsError,
     PackedA,
@@ -20,12 +22,17 @@ from ._lib import (  # noqa: F401
     lib_path,
     nsrgs_packed_bytes,
     nsrgs_workspace_bytes,
+    nsrgs_bcsr_packed_bytes,
     nsrgs_pack_upper,
     nsrgs_pack_dense,
     nsrgs_spectral_init,
     nsrgs_step,
     nsrgs_solve,
     nsrgs_solve_objective,
+    nsrgs_solve_ex,
+    SolveOpts,
+    STOP_UPDATE_NORM,
+    STOP_REL_DECREASE,
     nsrgs_objective,
     nsrgs_dF,
     nsrgs_version,

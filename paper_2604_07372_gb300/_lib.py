@@ -12,8 +12,16 @@ from dataclasses import dataclass
 
 import torch
 
-F32, BF16, FP8E4M3, DENSE_F32, DENSE_BF16 = 0, 1, 2, 3, 4
-STORAGE = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "dense_f32": DENSE_F32, "dense_bf16": DENSE_BF16}
+F32, BF16, FP8E4M3, DENSE_F32, DENSE_BF16, BCSR_F32, BCSR_BF16 = 0, 1, 2, 3, 4, 5, 6
+STORAGE = {
+    "f32": F32,
+    "bf16": BF16,
+    "fp8": FP8E4M3,
+    "dense_f32": DENSE_F32,
+    "dense_bf16": DENSE_BF16,
+    "bcsr_f32": BCSR_F32,
+    "bcsr_bf16": BCSR_BF16,
+}
 _STATUS = {
     0: "NSRGS_OK",
     1: "NSRGS_ERR_INVALID_ARG",
@@ -73,6 +81,7 @@ def lib() -> ctypes.CDLL:
     sig = {
         "nsrgs_packed_bytes": (sz, [i, i, i]),
         "nsrgs_workspace_bytes": (sz, [i, i]),
+        "nsrgs_bcsr_packed_bytes": (i, [vp, i, i, i, i, ctypes.POINTER(sz), vp, sz, vp]),
         "nsrgs_pack_upper": (i, [vp, i, i, i, vp, vp]),
         "nsrgs_pack_dense": (i, [vp, i, i, i, vp, vp]),
         "nsrgs_spectral_init": (i, [Ap, vp, i, d, ctypes.POINTER(d), vp, sz, vp]),
@@ -80,6 +89,7 @@ def lib() -> ctypes.CDLL:
         "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_solve_objective": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_objective": (i, [Ap, vp, ctypes.POINTER(d), vp, sz, vp]),
+        "nsrgs_solve_ex": (i, [Ap, f, i, i, vp, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_set_kernel_timing": (i, [i]),
         "nsrgs_kernel_timing": (i, [ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(i)]),
@@ -150,7 +160,19 @@ class PackedA:
         return self.buf.numel()
 
 
-def _alloc_packed(n: int, d: int, storage: int, device) -> torch.Tensor:
+def nsrgs_bcsr_packed_bytes(src: torch.Tensor, n: int, d: int, storage: int, dense: bool = False, ws=None) -> int:
+    """Exact bytes of a block-sparse packed buffer for this data (counts observed blocks on the device)."""
+    w = ws if ws is not None else workspace(n, d, src.device)
+    out = ctypes.c_size_t(0)
+    _check(lib().nsrgs_bcsr_packed_bytes(_ptr(src), 1 if dense else 0, n, d, storage, ctypes.byref(out), _ptr(w),
+                                         w.numel(), _stream()))
+    return int(out.value)
+
+
+def _alloc_packed(n: int, d: int, storage: int, device, src=None, dense=False) -> torch.Tensor:
+    if storage in (BCSR_F32, BCSR_BF16) and src is not None and d <= 8:
+        nb = nsrgs_bcsr_packed_bytes(src, n, d, storage, dense=dense)
+        return torch.empty(nb, dtype=torch.uint8, device=device)
     nb = nsrgs_packed_bytes(n, d, storage)
     if nb == 0:
         raise NsrgsError(8, f"storage {storage} does not support (n={n}, d={d})")
@@ -160,7 +182,7 @@ def _alloc_packed(n: int, d: int, storage: int, device) -> torch.Tensor:
 def nsrgs_pack_upper(upper: torch.Tensor, n: int, d: int, storage: int = F32) -> PackedA:
     """Pack the canonical upper-block list (n(n-1)/2, d, d) float32 on the device."""
     assert upper.dtype == torch.float32 and upper.numel() == n * (n - 1) // 2 * d * d
-    buf = _alloc_packed(n, d, storage, upper.device)
+    buf = _alloc_packed(n, d, storage, upper.device, src=upper)
     _check(lib().nsrgs_pack_upper(_ptr(upper), n, d, storage, _ptr(buf), _stream()))
     return PackedA(buf, n, d, storage)
 
@@ -168,7 +190,7 @@ def nsrgs_pack_upper(upper: torch.Tensor, n: int, d: int, storage: int = F32) ->
 def nsrgs_pack_dense(A: torch.Tensor, n: int, d: int, storage: int = F32) -> PackedA:
     """Pack a dense symmetric (nd, nd) float32 device matrix."""
     assert A.dtype == torch.float32 and A.shape == (n * d, n * d)
-    buf = _alloc_packed(n, d, storage, A.device)
+    buf = _alloc_packed(n, d, storage, A.device, src=A, dense=True)
     _check(lib().nsrgs_pack_dense(_ptr(A), n, d, storage, _ptr(buf), _stream()))
     return PackedA(buf, n, d, storage)
 
@@ -278,6 +300,53 @@ def nsrgs_solve_objective(
     return X, inf
 
 
+STOP_UPDATE_NORM, STOP_REL_DECREASE = 0, 1
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("stop_rule", ctypes.c_int), ("tol", ctypes.c_double), ("ns_safeguard", ctypes.c_int)]
+
+
+def nsrgs_solve_ex(
+    A: PackedA,
+    eta: float,
+    T: int,
+    K: int,
+    stop_rule: int = STOP_UPDATE_NORM,
+    tol: float = 0.0,
+    ns_safeguard: bool = False,
+    init: bool = True,
+    spectral_max_iters: int = 50,
+    X: torch.Tensor | None = None,
+    ws=None,
+    info: bool = True,
+):
+    """nsrgs_solve / nsrgs_solve_objective with explicit options; returns (X, Info or None)."""
+    if X is None:
+        X = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    a = A.struct()
+    opts = SolveOpts(stop_rule, tol, 1 if ns_safeguard else 0)
+    inf = Info() if info else None
+    _check(
+        lib().nsrgs_solve_ex(
+            ctypes.byref(a),
+            eta,
+            T,
+            K,
+            ctypes.byref(opts),
+            1 if init else 0,
+            spectral_max_iters,
+            _ptr(X),
+            ctypes.byref(inf) if inf is not None else None,
+            _ptr(w),
+            w.numel(),
+            _stream(),
+        )
+    )
+    return X, inf
+
+
 def nsrgs_objective(A: PackedA, X: torch.Tensor, ws=None) -> float:
     """F(X) of eq. (1) for the stored A."""
     w = _ws(A, ws)
@@ -320,7 +389,13 @@ def nsrgs_step_static(A: PackedA, eta: float, K: int, X_in: torch.Tensor, X_out:
 
 
 class _BatchItem(ctypes.Structure):
-    _fields_ = [("packed", ctypes.c_void_p), ("n", ctypes.c_int), ("eta", ctypes.c_float), ("X", ctypes.c_void_p)]
+    _fields_ = [
+        ("packed", ctypes.c_void_p),
+        ("n", ctypes.c_int),
+        ("eta", ctypes.c_float),
+        ("X", ctypes.c_void_p),
+        ("ns_safeguard", ctypes.c_int),
+    ]
 
 
 def nsrgs_batch_workspace_bytes(ns, d: int) -> int:
@@ -342,6 +417,7 @@ def nsrgs_batch_solve(
     Xs=None,
     ws=None,
     info: bool = True,
+    ns_safeguard: bool = False,
 ):
     """Solve a batch of PackedA instances (same d and storage); returns (list of X, list of Info or None)."""
     count = len(packs)
@@ -352,7 +428,7 @@ def nsrgs_batch_solve(
     items = (_BatchItem * count)()
     for k, (p, e, X) in enumerate(zip(packs, etas, Xs)):
         assert p.d == d and p.storage == storage
-        items[k] = _BatchItem(p.buf.data_ptr(), p.n, float(e), X.data_ptr())
+        items[k] = _BatchItem(p.buf.data_ptr(), p.n, float(e), X.data_ptr(), 1 if ns_safeguard else 0)
     if ws is None:
         ws = torch.empty(nsrgs_batch_workspace_bytes([p.n for p in packs], d), dtype=torch.uint8, device=packs[0].buf.device)
     infos = (Info * count)() if info else None
@@ -378,6 +454,7 @@ class _ServerConfig(ctypes.Structure):
         ("spectral_max_iters", ctypes.c_int),
         ("spectral_tol", ctypes.c_double),
         ("ticks_per_step", ctypes.c_int),
+        ("ns_safeguard", ctypes.c_int),
     ]
 
 
@@ -396,7 +473,8 @@ class Server:
     """nsrgs_server_* over a caller-owned device arena (a torch uint8 tensor)."""
 
     def __init__(self, d: int, storage: int, max_slots: int, arena_bytes: int, K: int = 2,
-                 spectral_max_iters: int = 60, spectral_tol: float = 1e-6, ticks_per_step: int = 4, device=None):
+                 spectral_max_iters: int = 60, spectral_tol: float = 1e-6, ticks_per_step: int = 4, device=None,
+                 ns_safeguard: bool = False):
         L = lib()
         for name, res, args in [
             ("nsrgs_server_table_bytes", ctypes.c_size_t, [ctypes.c_int]),
@@ -417,7 +495,8 @@ class Server:
         self.d = d
         self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=device or "cuda")
         self._keep = {}
-        cfg = _ServerConfig(d, storage, max_slots, K, spectral_max_iters, spectral_tol, ticks_per_step)
+        cfg = _ServerConfig(d, storage, max_slots, K, spectral_max_iters, spectral_tol, ticks_per_step,
+                            1 if ns_safeguard else 0)
         h = ctypes.c_void_p(0)
         _check(L.nsrgs_server_create(ctypes.byref(cfg), _ptr(self.arena), self.arena.numel(), _stream(), ctypes.byref(h)))
         self._h = h

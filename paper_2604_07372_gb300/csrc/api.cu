@@ -34,7 +34,8 @@ cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float
 cudaError_t stream_panel_prepare(const PanelGeom& g);
 
 int reduce_grid(long long rows);
-cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, double, Ctl*, double*, cudaStream_t);
+cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
+                            cudaStream_t);
 cudaError_t launch_gpm_epilogue(const float*, float*, float*, int, int, double, Ctl*, cudaStream_t);
 cudaError_t launch_spec_v0(float*, long long, int, cudaStream_t);
 cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
@@ -54,6 +55,12 @@ cudaError_t tc_dense_product(const void* packed, int n, int d, const float* X, _
 cudaError_t tc_dense_tune(const void* packed, int n, int d, __nv_bfloat16* XT, float* Y, Ctl* ctl, const int* skip,
                           cudaStream_t st);
 int tc_dense_splits(int n, int d);
+bool bcsr_storage(int storage);
+long long bcsr_bytes(int n, int d, int storage, long long nnzb);
+cudaError_t bcsr_stream(const void* packed, int n, int d, int storage, const float* X, float* Y, const int* skip,
+                        cudaStream_t st);
+cudaError_t bcsr_count_upper(const float* upper, int n, int d, unsigned long long* d_total, cudaStream_t st);
+cudaError_t bcsr_count_dense(const float* A, int n, int d, unsigned long long* d_total, cudaStream_t st);
 bool tc_sym_supported(int d);
 long long tc_sym_bytes(int n, int d);
 long long tc_sym_xt_bytes(int n, int d);
@@ -151,6 +158,13 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     NSRGS_CUDA_TRY(tc_dense_prepare(A->d));
     return NSRGS_OK;
   }
+  if (bcsr_storage(A->storage)) {
+    if (A->d > 8) {
+      set_error("block-sparse storage covers d <= 8");
+      return NSRGS_ERR_UNSUPPORTED;
+    }
+    return NSRGS_OK;
+  }
   NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
   if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d)) {
     NSRGS_CUDA_TRY(tc_sym_prepare(A->d));
@@ -182,6 +196,7 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
   if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d))
     return tc_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl, skip, st);
+  if (bcsr_storage(A->storage)) return bcsr_stream(A->packed, A->n, A->d, A->storage, X, w.Y, skip, st);
   return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
 }
 
@@ -235,7 +250,7 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
 enum { METHOD_NSRGS = 0, METHOD_GPM = 1, METHOD_NSRGS_OBJECTIVE = 2 };
 
 static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
-                                      int K, double tol, int method, cudaStream_t st,
+                                      int K, double tol, int method, int safeguard, cudaStream_t st,
                                       const cudaEvent_t* ev = nullptr) {
   cudaError_t e;
   for (int t = 0; t < T; ++t) {
@@ -250,9 +265,9 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
       // F(X^t) and R^{t-1} from Y = A_off X^t (Xn still holds X^{t-1}); a stop
       // leaves X^t as the result and skips this iteration's update
       e = launch_objective(Xt, w.Y, Xn, w.obj.Yprev, A->n, A->d, tol, w.obj, w.ctl, st);
-      if (e == cudaSuccess) e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, 0.0, w.ctl, nullptr, st);
+      if (e == cudaSuccess) e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, safeguard, 0.0, w.ctl, nullptr, st);
     } else {
-      e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, tol, w.ctl, nullptr, st);
+      e = launch_epilogue(Xt, w.Y, Xn, A->n, A->d, eta, K, safeguard, tol, w.ctl, nullptr, st);
     }
     if (e != cudaSuccess) return e;
   }
@@ -279,6 +294,7 @@ struct GraphKey {
   void* ws;
   int timing;
   int method;
+  int safeguard;
   bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -351,6 +367,7 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (storage == NSRGS_DENSE_BF16)
     return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
   if (storage == NSRGS_BF16 && tc_sym_supported(d)) return (size_t)tc_sym_bytes(n, d);
+  if (bcsr_storage(storage)) return d <= 8 ? (size_t)bcsr_bytes(n, d, storage, (long long)n * (n - 1)) : 0;
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) return 0;
   return (size_t)(g.header_bytes + g.panel_bytes);
@@ -359,6 +376,26 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
 size_t nsrgs_workspace_bytes(int n, int d) {
   if (n < 2 || d < 1 || d > 64) return 0;
   return map_workspace(nullptr, n, d).bytes;
+}
+
+nsrgs_status nsrgs_bcsr_packed_bytes(const float* src, int src_is_dense, int n, int d, int storage, size_t* bytes,
+                                     void* ws, size_t ws_bytes, void* stv) {
+  nsrgs_status s = check_nd(n, d);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(bcsr_storage(storage), "storage must be NSRGS_BCSR_F32 or NSRGS_BCSR_BF16");
+  NSRGS_CHECK_ARG(d <= 8, "block-sparse storage covers d <= 8");
+  NSRGS_CHECK_ARG(src && bytes, "src and bytes must be non-null");
+  if ((s = check_ws(ws, ws_bytes, n, d)) != NSRGS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, n, d);
+  // the count lands in the first 8 bytes of the spectral scalars (8 doubles)
+  unsigned long long* total = reinterpret_cast<unsigned long long*>(w.s.scal);
+  NSRGS_CUDA_TRY(src_is_dense ? bcsr_count_dense(src, n, d, total, st) : bcsr_count_upper(src, n, d, total, st));
+  unsigned long long nnzb = 0;
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(&nnzb, total, sizeof(nnzb), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  *bytes = (size_t)bcsr_bytes(n, d, storage, (long long)nnzb);
+  return NSRGS_OK;
 }
 
 nsrgs_status nsrgs_pack_upper(const float* upper, int n, int d, int storage, void* packed, void* st) {
@@ -442,13 +479,13 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
   NSRGS_CUDA_TRY(reset_ws(w, A->n, A->d, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X_in, bytes, cudaMemcpyDeviceToDevice, st));
   NSRGS_CUDA_TRY(stream_AX(A, g, w.X[0], w, &w.ctl->stop, st));
-  NSRGS_CUDA_TRY(launch_epilogue(w.X[0], w.Y, X_out, A->n, A->d, eta, K, 0.0, w.ctl, upd_norm, st));
+  NSRGS_CUDA_TRY(launch_epilogue(w.X[0], w.Y, X_out, A->n, A->d, eta, K, 0, 0.0, w.ctl, upd_norm, st));
   return NSRGS_OK;
 }
 
 static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
                                int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
-                               void* stv, int method);
+                               void* stv, int method, int safeguard = 0);
 
 nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, int init, int spectral_max_iters,
                          float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
@@ -466,6 +503,17 @@ nsrgs_status nsrgs_solve_objective(const nsrgs_A* A, float eta, int T, int K, do
   NSRGS_CHECK_ARG(isfinite(rel_tol), "rel_tol must be finite");
   return solve_impl(A, eta, T, K, rel_tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv,
                     METHOD_NSRGS_OBJECTIVE);
+}
+
+nsrgs_status nsrgs_solve_ex(const nsrgs_A* A, float eta, int T, int K, const nsrgs_solve_opts* opts, int init,
+                            int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  NSRGS_CHECK_ARG(opts != nullptr, "opts is null");
+  NSRGS_CHECK_ARG(opts->stop_rule == NSRGS_STOP_UPDATE_NORM || opts->stop_rule == NSRGS_STOP_REL_DECREASE,
+                  "unknown stop_rule");
+  NSRGS_CHECK_ARG(isfinite(opts->tol), "tol must be finite");
+  const int method = opts->stop_rule == NSRGS_STOP_REL_DECREASE ? METHOD_NSRGS_OBJECTIVE : METHOD_NSRGS;
+  return solve_impl(A, eta, T, K, opts->tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv, method,
+                    opts->ns_safeguard ? 1 : 0);
 }
 
 nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* ws, size_t ws_bytes, void* stv) {
@@ -498,7 +546,7 @@ nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* 
 
 static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double tol, int init,
                                int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
-                               void* stv, int method) {
+                               void* stv, int method, int safeguard) {
   PanelGeom g{};
   nsrgs_status s = check_A(A, &g);
   if (s != NSRGS_OK) return s;
@@ -539,6 +587,7 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
   key.ws = ws;
   key.timing = g_timing;
   key.method = method;
+  key.safeguard = safeguard ? 1 : 0;
 
   cudaGraphExec_t exec = nullptr;
   int kernel_nodes = 0;
@@ -570,7 +619,7 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
       if (init) e = enqueue_spectral(A, g, w, spectral_max_iters, 1e-6, w.X[0], cs);
       else e = cudaMemcpyAsync(w.X[0], X, bytes, cudaMemcpyDeviceToDevice, cs);
     }
-    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, method, cs, ev);
+    if (e == cudaSuccess) e = enqueue_iterations(A, g, w, eta, T, K, tol, method, key.safeguard, cs, ev);
     if (e == cudaSuccess) e = launch_copy_out(w.X[0], w.X[1], X, (long long)n * d * d, w.ctl, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -609,7 +658,8 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     info->iters = c.iters_done;
     info->last_update_norm = c.last_upd;
     info->spectral_residual = c.spec_res;
-    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND)) | ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
+    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
+                  ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
     if (c.flags & FLAG_TIMEOUT) {
       set_error("a device-side wait timed out");
       return NSRGS_ERR_TIMEOUT;

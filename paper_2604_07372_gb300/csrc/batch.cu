@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) batch_phase_kernel(const BatchDesc* descs
     float* Xn = d.X[(it + 1) & 1];
     double diff2 = 0.0;
     unsigned int flags = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) block_update<D>(Xc, d.Y, Xn, i, n, d.eta, d.K, diff2, flags);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) block_update<D>(Xc, d.Y, Xn, i, n, d.eta, d.K, d.safeguard != 0, diff2, flags);
     if (flags) atomicOr(&c->flags, flags);
     const double tot = block_sum(diff2, sh);
     __syncthreads();
@@ -475,6 +475,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     ds.K = K;
     ds.smax = init ? spectral_max_iters : 0;
     ds.start_given = init ? 0 : 1;
+    ds.safeguard = items[i].ns_safeguard ? 1 : 0;
     bases[i] = steps;
     steps += ds.g.total_steps;
   }
@@ -549,7 +550,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
       info[i].spectral_residual = rep[i].spec_res;
       info[i].objective = NAN;
       info[i].rel_decrease = NAN;
-      info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND)) |
+      info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
                       ((init && rep[i].spec_res > 1e-6) ? FLAG_SPEC_NOT_CONVERGED : 0u);
       timeout = timeout || (rep[i].flags & FLAG_TIMEOUT);
       nonfinite = nonfinite || (rep[i].flags & FLAG_NONFINITE);

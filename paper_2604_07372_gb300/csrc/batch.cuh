@@ -19,7 +19,7 @@ struct BatchDesc {
   int K;
   int smax;               // spectral passes cap
   int start_given;        // 1: X^0 comes from Xout, no spectral initialisation
-  int pad;
+  int safeguard;          // 1: safeguarded Newton-Schulz start (beyond the paper)
   double tol;             // stop when the update norm falls below it (0: run T iterations)
   double spec_tol;        // spectral residual target
 };

@@ -203,11 +203,14 @@ __device__ inline void chol_inv(const double* G, double* Rinv, int D, double* Rt
 //   G = (n-1) X_i - Y_i,  P = (G - X_i G^T X_i)/2,  F = X_i - eta P,
 //   S <- S (3I - S^T S)/2 applied K times (Algorithm 1), X_i^{t+1} = S.
 // Y_i (= sum_{j != i} A_ij X_j) is zeroed for the next pass.  Adds
-// ||X^{t+1}_i - X_i||^2 to diff2 and FLAG_* bits to flags.
+// ||X^{t+1}_i - X_i||^2 to diff2 and FLAG_* bits to flags.  With `safeguard`
+// (beyond the paper) an F that fails Lemma 2.1's precondition, checked as
+// ||I - F^T F||_F >= 1, starts the Newton-Schulz steps from F / ||F||_F (same
+// polar factor, singular values in (0, 1]).
 template <int D>
 __device__ __forceinline__ void block_update(const float* __restrict__ X, float* __restrict__ Y,
                                              float* __restrict__ Xout, long long i, int n, float eta, int K,
-                                             double& diff2, unsigned int& flags) {
+                                             bool safeguard, double& diff2, unsigned int& flags) {
   float x[D][D], gm[D][D];
   const float nm1 = (float)(n - 1);
 #pragma unroll
@@ -254,7 +257,23 @@ __device__ __forceinline__ void block_update(const float* __restrict__ X, float*
         for (int k = 0; k < D; ++k) acc = fmaf(-s[k][r], s[k][c], acc);
         e2 = fmaf(acc, acc, e2);
       }
-    if (!(e2 < 1.f)) flags |= FLAG_NS_PRECOND;
+    if (!(e2 < 1.f)) {
+      if (safeguard) {
+        float f2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) f2 = fmaf(s[r][c], s[r][c], f2);
+        const float inv = 1.f / sqrtf(f2);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) s[r][c] *= inv;
+        flags |= FLAG_NS_SAFEGUARDED;
+      } else {
+        flags |= FLAG_NS_PRECOND;
+      }
+    }
   }
   for (int k = 0; k < K; ++k) {
     float m[D][D];  // 3I - S^T S

@@ -65,6 +65,7 @@ enum : unsigned int {
   FLAG_NS_PRECOND = 1u << 1,
   FLAG_SPEC_NOT_CONVERGED = 1u << 2,
   FLAG_TIMEOUT = 1u << 3,
+  FLAG_NS_SAFEGUARDED = 1u << 4,  // the safeguarded Newton-Schulz start was used for some block
 };
 
 // float64 scratch of the spectral initialisation and of d_F (all d x d unless noted).

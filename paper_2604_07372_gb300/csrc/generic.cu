@@ -29,7 +29,8 @@ __device__ void cta_mm(const T* A, bool transA, const T* B, T* C, int D, T alpha
 // Dynamic shared memory: 5 D x D float matrices.
 __global__ void __launch_bounds__(256) epilogue_generic_kernel(const float* __restrict__ X, float* __restrict__ Y,
                                                                float* __restrict__ Xout, int n, int D, float eta,
-                                                               int K, double tol, Ctl* ctl, double* upd_out) {
+                                                               int K, int safeguard, double tol, Ctl* ctl,
+                                                               double* upd_out) {
   extern __shared__ __align__(16) float sm[];
   __shared__ double sh[32];
   if (ctl->stop) return;
@@ -62,7 +63,27 @@ __global__ void __launch_bounds__(256) epilogue_generic_kernel(const float* __re
     e2 += v * v;
   }
   e2 = block_sum(e2, sh);
-  if (threadIdx.x == 0 && !(e2 < 1.0)) atomicOr(&ctl->flags, FLAG_NS_PRECOND);
+  __shared__ double fnorm;
+  if (threadIdx.x == 0) fnorm = !(e2 < 1.0) ? 1.0 : 0.0;  // 1: precondition fails
+  __syncthreads();
+  if (fnorm != 0.0) {
+    if (safeguard) {
+      // safeguarded start (beyond the paper): F / ||F||_F, same polar factor
+      double f2 = 0.0;
+      for (int e = threadIdx.x; e < DD; e += blockDim.x) f2 += (double)s[e] * (double)s[e];
+      f2 = block_sum(f2, sh);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        fnorm = sqrt(f2);
+        atomicOr(&ctl->flags, FLAG_NS_SAFEGUARDED);
+      }
+      __syncthreads();
+      const float inv = (float)(1.0 / fnorm);
+      for (int e = threadIdx.x; e < DD; e += blockDim.x) s[e] *= inv;
+    } else if (threadIdx.x == 0) {
+      atomicOr(&ctl->flags, FLAG_NS_PRECOND);
+    }
+  }
   for (int k = 0; k < K; ++k) {
     __syncthreads();
     cta_mm<float>(s, true, s, m, D, 1.f, nullptr, 0.f);  // S^T S
@@ -330,9 +351,10 @@ static int gram_grid(long long rows) {
   return (int)(g < 256 ? (g < 1 ? 1 : g) : 256);
 }
 
-cudaError_t launch_epilogue_generic(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, double tol,
-                                    Ctl* ctl, double* upd_out, cudaStream_t st) {
-  epilogue_generic_kernel<<<n, 256, 5 * d * d * sizeof(float), st>>>(X, Y, Xout, n, d, eta, K, tol, ctl, upd_out);
+cudaError_t launch_epilogue_generic(const float* X, float* Y, float* Xout, int n, int d, float eta, int K,
+                                    int safeguard, double tol, Ctl* ctl, double* upd_out, cudaStream_t st) {
+  epilogue_generic_kernel<<<n, 256, 5 * d * d * sizeof(float), st>>>(X, Y, Xout, n, d, eta, K, safeguard, tol, ctl,
+                                                                      upd_out);
   return cudaGetLastError();
 }
 

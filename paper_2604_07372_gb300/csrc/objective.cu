@@ -187,6 +187,32 @@ __global__ void __launch_bounds__(256) norm2_flat_kernel(const T* __restrict__ a
   }
 }
 
+// Block-sparse rows (both triangles stored, each block once per direction):
+// the stored values once; their count is in the packed header.
+template <class T>
+__global__ void __launch_bounds__(256) norm2_bcsr_kernel(const uint8_t* __restrict__ packed, int D, ObjScratch o,
+                                                         Ctl* ctl) {
+  __shared__ double sh[32];
+  const long long* hdr = reinterpret_cast<const long long*>(packed);
+  const long long count = hdr[2] * D * D;
+  const T* a = reinterpret_cast<const T*>(packed + hdr[4]);
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)to_float(a[e]);
+    acc += v * v;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) o.partials[blockIdx.x] = acc;
+  if (!last_block(&ctl->counter)) return;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) v += o.partials[c];
+    o.scal[OBJ_A2] = v;
+    ctl->counter = 0u;
+  }
+}
+
 // FP8 panels: element (row, col) holds A/s_i with i = row / D, so each step's
 // stored values are weighted by the square of their block row's scale.
 __global__ void __launch_bounds__(256) norm2_fp8_panel_kernel(const uint8_t* __restrict__ packed, PanelGeom g,
@@ -253,6 +279,10 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
   } else if (storage == NSRGS_DENSE_BF16) {
     const long long count = (long long)n * d * dense_bf16_pitch(n, d);
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), count, 1.0, o, ctl);
+  } else if (storage == NSRGS_BCSR_F32) {
+    norm2_bcsr_kernel<float><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(packed), d, o, ctl);
+  } else if (storage == NSRGS_BCSR_BF16) {
+    norm2_bcsr_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(packed), d, o, ctl);
   } else if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
     // tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), tc_sym_bytes(n, d) / 2, 2.0,

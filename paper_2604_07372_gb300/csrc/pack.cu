@@ -204,11 +204,35 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
   return NSRGS_OK;
 }
 
+bool bcsr_storage(int storage);
+cudaError_t bcsr_pack_upper(const float* upper, int n, int d, int storage, void* packed, cudaStream_t st);
+cudaError_t bcsr_pack_dense(const float* A, int n, int d, int storage, void* packed, cudaStream_t st);
+
+static nsrgs_status check_bcsr_d(int d) {
+  if (d > 8) {
+    set_error("block-sparse storage covers d <= 8");
+    return NSRGS_ERR_UNSUPPORTED;
+  }
+  return NSRGS_OK;
+}
+
 nsrgs_status pack_upper_impl(const float* upper, int n, int d, int storage, void* packed, cudaStream_t st) {
+  if (bcsr_storage(storage)) {
+    nsrgs_status s = check_bcsr_d(d);
+    if (s != NSRGS_OK) return s;
+    NSRGS_CUDA_TRY(bcsr_pack_upper(upper, n, d, storage, packed, st));
+    return NSRGS_OK;
+  }
   return pack_any(UpperSrc{upper, n, d}, n, d, storage, packed, st);
 }
 
 nsrgs_status pack_dense_impl(const float* A, int n, int d, int storage, void* packed, cudaStream_t st) {
+  if (bcsr_storage(storage)) {
+    nsrgs_status s = check_bcsr_d(d);
+    if (s != NSRGS_OK) return s;
+    NSRGS_CUDA_TRY(bcsr_pack_dense(A, n, d, storage, packed, st));
+    return NSRGS_OK;
+  }
   return pack_any(DenseSrc{A, n, d}, n, d, storage, packed, st);
 }
 

@@ -268,6 +268,7 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
     ds.K = s->cfg.K;
     ds.smax = s->cfg.spectral_max_iters;
     ds.start_given = 0;
+    ds.safeguard = s->cfg.ns_safeguard ? 1 : 0;
     ds.tol = r.tol;
     ds.spec_tol = s->cfg.spectral_tol;
     NSRGS_CUDA_TRY(cudaMemcpyAsync(&ds.ctl->phase, &kAdmitPhase, sizeof(int), cudaMemcpyHostToDevice, s->st));

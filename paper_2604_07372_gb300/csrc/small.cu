@@ -18,13 +18,13 @@ constexpr int kDmaxSmall = 8;  // thread-per-block kernels are instantiated for 
 template <int D>
 __global__ void __launch_bounds__(128) epilogue_kernel(const float* __restrict__ X, float* __restrict__ Y,
                                                        float* __restrict__ Xout, int n, float eta, int K,
-                                                       double tol, Ctl* ctl, double* upd_out) {
+                                                       int safeguard, double tol, Ctl* ctl, double* upd_out) {
   __shared__ double sh[32];
   if (ctl->stop) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double diff2 = 0.0;
   unsigned int flags = 0;
-  if (i < n) block_update<D>(X, Y, Xout, i, n, eta, K, diff2, flags);
+  if (i < n) block_update<D>(X, Y, Xout, i, n, eta, K, safeguard != 0, diff2, flags);
   if (flags) atomicOr(&ctl->flags, flags);
   const double bs = block_sum(diff2, sh);
   if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
@@ -351,7 +351,7 @@ __global__ void select_copy_kernel(const float* __restrict__ B0, const float* __
   }
 
 // Runtime-d versions for 8 < d <= 64 (generic.cu).
-cudaError_t launch_epilogue_generic(const float*, float*, float*, int, int, float, int, double, Ctl*, double*,
+cudaError_t launch_epilogue_generic(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
                                     cudaStream_t);
 cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
                                      cudaStream_t);
@@ -360,11 +360,11 @@ cudaError_t launch_spec_update_generic(const float*, const float*, float*, long 
 cudaError_t launch_polar_generic(const float*, float*, int, int, cudaStream_t);
 cudaError_t launch_dF_generic(const float*, const float*, long long, int, const SpecScratch&, Ctl*, cudaStream_t);
 
-cudaError_t launch_epilogue(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, double tol,
-                            Ctl* ctl, double* upd_out, cudaStream_t st) {
-  if (d > kDmaxSmall) return launch_epilogue_generic(X, Y, Xout, n, d, eta, K, tol, ctl, upd_out, st);
+cudaError_t launch_epilogue(const float* X, float* Y, float* Xout, int n, int d, float eta, int K, int safeguard,
+                            double tol, Ctl* ctl, double* upd_out, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_epilogue_generic(X, Y, Xout, n, d, eta, K, safeguard, tol, ctl, upd_out, st);
   const int grid = (n + 127) / 128;
-#define L(DD) epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, eta, K, tol, ctl, upd_out)
+#define L(DD) epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, eta, K, safeguard, tol, ctl, upd_out)
   NSRGS_DISPATCH_D(d, L)
 #undef L
   return cudaGetLastError();

@@ -2,7 +2,9 @@
 // d in {16, 32, 64} with A stored in bfloat16 (NSRGS_BF16 at these d).
 //
 // Layout ("tile-upper"): the nd x nd matrix is cut into 128 x 128 tiles; tile
-// (I, J) is stored for J >= I only, row panel by row panel (I ascending, then J).
+// (I, J) is stored for J >= I only, in the order the kernel visits them (groups
+// of R row tiles, columns J inside a group, rows inside a column; see TsWalk),
+// so that every CTA streams one contiguous range of the buffer.
 // A diagonal tile keeps the blocks strictly above the block diagonal (d divides
 // 128, so blocks never straddle tiles); everything else in it is zero.  Each
 // tile is 32 KB, already in the 128-byte-swizzled order the tensor core reads:
@@ -42,20 +44,7 @@ constexpr int kTsTile = 128;
 constexpr int kTsTileBytes = kTsTile * kTsTile * 2;  // 32 KB
 
 __host__ __device__ inline int ts_tile_rows(int n, int d) { return (int)(((long long)n * d + kTsTile - 1) / kTsTile); }
-__host__ __device__ inline long long ts_panel_start(int I, int NT) {
-  return (long long)I * NT - (long long)I * (I - 1) / 2;
-}
 __host__ __device__ inline long long ts_tiles(int NT) { return (long long)NT * (NT + 1) / 2; }
-
-// Row panel of tile index t (last I with ts_panel_start(I) <= t).
-__host__ __device__ inline int ts_panel_of(long long t, int NT) {
-  int lo = 0, hi = NT - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ts_panel_start(mid, NT) <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Byte offset of element (r, c) inside a swizzled 128 x 128 tile, and of
 // element (n, k) (n < N rows, k < 128) inside a swizzled N x 128 X^T tile.
@@ -120,11 +109,20 @@ struct TsWalk {
     }
     set_group(gg);
     long long u = t - base;
-    while (u >= strip_len()) {
-      u -= strip_len();
-      ++J;
+    const long long tri = (long long)Rg * (Rg + 1) / 2;  // strips of 1, 2, .., Rg tiles, then Rg each
+    if (u < tri) {
+      int c = 0;
+      while (u >= c + 1) {
+        u -= c + 1;
+        ++c;
+      }
+      J = I0 + c;
+      r = (int)u;
+    } else {
+      u -= tri;
+      J = I0 + Rg + (int)(u / Rg);
+      r = (int)(u % Rg);
     }
-    r = (int)u;
   }
   __device__ int I() const { return I0 + r; }
   // Advances; reports whether the tile just left closed its strip / its group.
@@ -214,9 +212,8 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
         break;
       }
       uint8_t* stage = smem + st * C::STAGE;
-      const long long tile = ts_panel_start(w.I(), a.NT) + (w.J - w.I());
       mbar_arrive_expect_tx(&full[st], C::STAGE);
-      bulk_g2s(stage, a.tiles + tile * (long long)kTsTileBytes, kTsTileBytes, &full[st]);
+      bulk_g2s(stage, a.tiles + t * (long long)kTsTileBytes, kTsTileBytes, &full[st]);
       bulk_g2s(stage + kTsTileBytes, a.xt + (long long)w.J * C::XB, C::XB, &full[st]);
       if (++st == C::NSTAGE) {
         st = 0;
@@ -369,13 +366,23 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
 }
 
 // ------------------------------------------------------------ packing
-// One CTA per tile (grid-stride): 2048 16-byte chunks of 8 consecutive columns.
-template <class Src>
+// One CTA per tile (grid-stride): tile number t of the processing order, 2048
+// 16-byte chunks of 8 consecutive columns.
+template <int R, class Src>
 __global__ void __launch_bounds__(256) ts_pack_kernel(Src src, int NT, uint8_t* out) {
+  __shared__ int ij[2];
   const long long total = ts_tiles(NT);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int I = ts_panel_of(t, NT);
-    const int J = I + (int)(t - ts_panel_start(I, NT));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TsWalk<R> w;
+      w.NT = NT;
+      w.seek(t);
+      ij[0] = w.I();
+      ij[1] = w.J;
+    }
+    __syncthreads();
+    const int I = ij[0], J = ij[1];
     uint8_t* tile = out + t * (long long)kTsTileBytes;
     for (int ch = threadIdx.x; ch < kTsTile * kTsTile / 8; ch += blockDim.x) {
       const int r = ch >> 4, c = (ch & 15) * 8;
@@ -463,7 +470,13 @@ template <class Src>
 cudaError_t tc_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st) {
   const int NT = ts_tile_rows(n, d);
   const int g = (int)std::min<long long>(ts_tiles(NT), 8LL * num_sms());
-  ts_pack_kernel<<<g, 256, 0, st>>>(src, NT, reinterpret_cast<uint8_t*>(packed));
+  uint8_t* out = reinterpret_cast<uint8_t*>(packed);
+  switch (d) {
+    case 16: ts_pack_kernel<TsCfg<16>::R><<<g, 256, 0, st>>>(src, NT, out); break;
+    case 32: ts_pack_kernel<TsCfg<32>::R><<<g, 256, 0, st>>>(src, NT, out); break;
+    case 64: ts_pack_kernel<TsCfg<64>::R><<<g, 256, 0, st>>>(src, NT, out); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 template cudaError_t tc_sym_pack<UpperSrc>(UpperSrc, int, int, void*, cudaStream_t);

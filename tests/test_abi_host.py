@@ -44,6 +44,10 @@ def test_version_and_sizes(L):
     assert L.nsrgs_packed_bytes(200, 8, L.F32) > 0 and L.nsrgs_packed_bytes(200, 5, L.BF16) > 0
     assert L.nsrgs_packed_bytes(200, 9, L.F32) == 0
     assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0
+    # block-sparse rows: the bound for fully observed data, both triangles, d <= 8
+    assert L.nsrgs_packed_bytes(200, 3, L.BCSR_F32) >= 200 * 199 * 9 * 4
+    assert L.nsrgs_packed_bytes(200, 3, L.BCSR_BF16) >= 200 * 199 * 9 * 2
+    assert L.nsrgs_packed_bytes(200, 9, L.BCSR_F32) == 0
     assert L.nsrgs_packed_bytes(200, 25, L.DENSE_F32) == 200 * 25 * 5000 * 4
     assert L.nsrgs_packed_bytes(1, 3, L.F32) == 0
     # BF16 / FP8 shrink the panels by 2x / 4x (plus small tables)

@@ -1,0 +1,102 @@
+"""GPU parity of the block-sparse storage (NSRGS_BCSR_F32 / NSRGS_BCSR_BF16) for
+incomplete observations (§4.1: pairs observed with probability p, unobserved
+A_ij = 0): packed size, the product A_off X against float64, whole solves and
+the objective against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2604_07372_gb300 as P
+
+    return P
+
+
+def to64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def observed_blocks(inst):
+    return int(np.count_nonzero(np.any(inst.upper.reshape(len(inst.upper), -1) != 0, axis=1)))
+
+
+CASES = [(2, 3, 1.0), (3, 1, 0.5), (70, 3, 0.3), (257, 4, 0.05), (50, 3, 0.01), (1000, 3, 0.2), (120, 8, 0.4),
+         (200, 2, 1.0)]
+
+
+@pytest.mark.parametrize("storage", ["bcsr_f32", "bcsr_bf16"])
+@pytest.mark.parametrize("n,d,p", CASES)
+def test_bcsr_product_matches_dense_matmul(P, n, d, p, storage):
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=n + d, p=p, dtype=np.float32)
+    A = inst.dense()
+    for i in range(n):
+        A[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
+    up = torch.from_numpy(inst.upper).cuda()
+    st = P.STORAGE[storage]
+    nnzb = 2 * observed_blocks(inst)
+    E = 4 if storage == "bcsr_f32" else 2
+    nb = P.nsrgs_bcsr_packed_bytes(up, n, d, st)
+    assert nb >= nnzb * d * d * E and nb <= nnzb * (d * d * E + 4) + 8 * (n + 1) + 64 + 3 * 256
+    pa = P.nsrgs_pack_upper(up, n, d, st)
+    X = np.random.default_rng(n).standard_normal((n * d, d)).astype(np.float32)
+    Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    if storage == "bcsr_bf16":
+        A = torch.from_numpy(A).to(torch.bfloat16).to(torch.float64).numpy()
+    ref = A @ X.astype(np.float64)
+    scale = np.abs(A) @ np.abs(X.astype(np.float64))
+    assert np.all(np.abs(to64(Y) - ref) <= 1e-6 * scale + 1e-6)
+
+
+def test_bcsr_from_dense_equals_from_upper(P):
+    n, d, p = 150, 3, 0.25
+    inst = synth.make_instance(n, d, 1.0, seed=4, p=p, dtype=np.float32)
+    Ad = torch.from_numpy(inst.dense(dtype=np.float32)).cuda()
+    up = torch.from_numpy(inst.upper).cuda()
+    a = P.nsrgs_pack_upper(up, n, d, P.BCSR_F32)
+    b = P.nsrgs_pack_dense(Ad, n, d, P.BCSR_F32)
+    torch.cuda.synchronize()
+    assert a.nbytes == b.nbytes and torch.equal(a.buf, b.buf)
+
+
+@pytest.mark.parametrize("n,d,p", [(300, 3, 0.2), (200, 4, 0.5)])
+def test_bcsr_solve_matches_oracle(P, n, d, p):
+    T, K = 30, 2
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=11 + d, p=p, dtype=np.float32)
+    A = inst.dense()
+    X0, _ = O.spectral_init(A, n, d)
+    Xo, _ = O.nsrgs(A, n, d, 1.0 / n, T, K, X0=X0)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BCSR_F32)
+    X, info = P.nsrgs_solve(pa, 1.0 / n, T, K, spectral_max_iters=100)
+    torch.cuda.synchronize()
+    assert info.iters == T
+    assert O.dF(to64(X), Xo, d) / math.sqrt(n * d) <= 1e-5
+
+
+def test_bcsr_objective_matches_oracle(P):
+    n, d, p = 250, 3, 0.3
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=21, p=p, dtype=np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BCSR_F32)
+    X = inst.Zstack().astype(np.float32)
+    F = P.nsrgs_objective(pa, torch.from_numpy(X).cuda())
+    ref = O.objective(inst.dense(), X.astype(np.float64), n, d)
+    assert abs(F - ref) <= 1e-5 * abs(ref)
+
+
+def test_bcsr_is_refused_where_not_built(P):
+    inst = synth.make_instance(20, 9, 0.5, seed=1, p=0.5, dtype=np.float32)
+    with pytest.raises(P.NsrgsError):
+        P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), 20, 9, P.BCSR_F32)

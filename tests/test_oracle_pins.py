@@ -349,3 +349,61 @@ def test_rows_update_matches_full_iteration():
     assert np.allclose(rows[1], A[7 * d : 8 * d]), "block_row must read A's block row"
     part = O.nsrgs_rows_update(rows, X0, idx, n, d, 1.0 / n, 2)
     assert np.allclose(part, full[idx], atol=1e-14)
+
+
+# ------------------------------- beyond the paper: safeguarded NS start
+def test_safeguard_leaves_blocks_that_meet_the_precondition():
+    """Where ||I - F_i^T F_i||_F < 1 for every block the safeguarded iteration is
+    Algorithm 2 itself, bit for bit."""
+    n, d = 120, 3
+    inst, A = _config1(n=n)
+    X0, _ = O.spectral_init(A, n, d)
+    X = X0
+    for _ in range(5):
+        a = O.nsrgs_iteration(A, X, n, d, 1.0 / n, 2)
+        b = O.nsrgs_iteration(A, X, n, d, 1.0 / n, 2, safeguard=True)
+        assert np.array_equal(a, b)
+        X = a
+
+
+def test_safeguard_restores_convergence_to_the_polar_factor():
+    """A block far outside Lemma 2.1's region: Algorithm 1 from F diverges, from the
+    safeguarded start it converges to sgn(F) (the SVD polar factor), unchanged by the scaling."""
+    rng = np.random.default_rng(3)
+    for d in (2, 3, 5):
+        F = 3.0 * rng.standard_normal((d, d))
+        assert np.linalg.norm(np.eye(d) - F.T @ F) >= 1.0
+        with np.errstate(over="ignore", invalid="ignore"):
+            bad = O.newton_schulz(F, 30)
+        assert not np.all(np.isfinite(bad)) or np.linalg.norm(bad - O.sgn(F)) > 1e-3
+        G = O.ns_safeguard(F)
+        assert np.isclose(np.linalg.norm(G), 1.0)
+        assert np.allclose(O.sgn(G), O.sgn(F), atol=1e-12)
+        assert np.allclose(O.newton_schulz(G, 60), O.sgn(F), atol=1e-10)
+        # a block inside the region is returned as it is
+        H = O.sgn(F) * 1.05
+        assert np.array_equal(O.ns_safeguard(H), H)
+
+
+def test_safeguard_keeps_the_low_p_step_finite():
+    """Sparse data with the paper's step mu = 1/(np) at p = 0.05 (n = 400, d = 3): the
+    plain iteration leaves Lemma 2.1's region and blows up within 30 iterations; with the
+    safeguarded start the iterates stay finite and d_F(X, Z) stays bounded."""
+    n, d, p = 400, 3, 0.05
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=7, p=p)
+    A = inst.dense()
+    X0, _ = O.spectral_init(A, n, d)
+    X = X0
+    blew_up = False
+    with np.errstate(over="ignore", invalid="ignore"):
+        for _ in range(30):
+            X = O.nsrgs_iteration(A, X, n, d, 1.0 / (n * p), 2)
+            if not np.all(np.isfinite(X)):
+                blew_up = True
+                break
+    assert blew_up
+    X = X0
+    for _ in range(40):
+        X = O.nsrgs_iteration(A, X, n, d, 1.0 / (n * p), 2, safeguard=True)
+        assert np.all(np.isfinite(X))
+    assert O.dF(X, inst.Zstack(), d) / math.sqrt(n * d) < 1.0

@@ -1,16 +1,19 @@
 """Host-side checks of the tile-upper layout of the tensor-core symmetric stream
 (BF16 storage at d in {16, 32, 64}), without a GPU.
 
-A NumPy model of the layout: 128 x 128 tiles (I, J) with J >= I, row panel by
-row panel; inside a tile the 128-byte-swizzled order (8-row groups 2048 bytes
-apart, the two 64-column halves 1024 bytes apart, rows 128 bytes apart, 16-byte
-chunk k of row r at k ^ (r % 8)).  Checked: (1) the swizzle is a bijection of a
+A NumPy model of the layout: 128 x 128 tiles (I, J) with J >= I, stored in the
+kernel's processing order (groups of R row tiles, R = 8 for d in {16, 32} and 4
+for d = 64; columns J inside a group; rows inside a column); inside a tile the
+128-byte-swizzled order (8-row groups 2048 bytes apart, the two 64-column halves
+1024 bytes apart, rows 128 bytes apart, 16-byte chunk k of row r at k ^ (r % 8)).  Checked: (1) the swizzle is a bijection of a
 tile onto its 32 KB; (2) every element of the strict block-upper triangle lands
 in exactly one stored slot and every other slot holds zero; (3) the two products
 each tile feeds (Y_I += A_IJ X_J, Y_J += A_IJ^T X_I) rebuild A_off X; (4) the
 MN-major reading of a tile (MN atoms 1024 bytes apart, 8-row K groups 2048
 apart) addresses the transposed tile, and the K-major reading (8-row groups 2048
-apart) the tile itself; (5) the library's packed-byte count agrees.
+apart) the tile itself; (5) the processing order visits every tile once and the
+closed-form position -> (I, J) map (group sizes, then triangular and full
+column strips) inverts it; (6) the library's packed-byte count agrees.
 """
 import numpy as np
 import pytest
@@ -107,3 +110,47 @@ def test_packed_bytes_match_library(n, d):
         pytest.skip("libnsrgs.so not built")
     NT = -(-(n * d) // T)
     assert lib.nsrgs_packed_bytes(n, d, L.BF16) == NT * (NT + 1) // 2 * 32768
+
+
+def order(NT, R):
+    """The processing (and storage) order: (I, J) of every stored tile."""
+    out = []
+    for g in range(-(-NT // R)):
+        I0 = g * R
+        Rg = min(R, NT - I0)
+        for J in range(I0, NT):
+            for r in range(min(Rg, J - I0 + 1)):
+                out.append((I0 + r, J))
+    return out
+
+
+def seek(t, NT, R):
+    """Position t -> (I, J) as the kernel and the packer compute it."""
+    base, g = 0, 0
+    while True:
+        L = NT - g * R
+        Rg = min(R, L)
+        cnt = Rg * (Rg + 1) // 2 + (L - Rg) * Rg
+        if t < base + cnt:
+            break
+        base += cnt
+        g += 1
+    I0, Rg = g * R, min(R, NT - g * R)
+    u = t - base
+    tri = Rg * (Rg + 1) // 2
+    if u < tri:
+        c = 0
+        while u >= c + 1:
+            u -= c + 1
+            c += 1
+        return I0 + u, I0 + c
+    u -= tri
+    return I0 + u % Rg, I0 + Rg + u // Rg
+
+
+@pytest.mark.parametrize("NT,R", [(1, 8), (2, 8), (8, 8), (9, 8), (17, 8), (30, 4), (7, 4), (125, 8)])
+def test_processing_order_covers_each_tile_once_and_seek_inverts_it(NT, R):
+    seq = order(NT, R)
+    assert len(seq) == NT * (NT + 1) // 2
+    assert len(set(seq)) == len(seq) and all(I <= J for I, J in seq)
+    assert all(seek(t, NT, R) == ij for t, ij in enumerate(seq))
