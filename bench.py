@@ -369,7 +369,9 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
                 tol: float = 1e-6, T_max: int = 1000, slots: int = 48):
     """Poisson arrivals (rate req/s) of requests n ~ log-U[100, 8000], d in {3, 4}, half
     dense and half block-sparse (pair kept with p ~ U[0.05, 0.5]); continuous batching
-    with BF16 storage; a request retires when its update norm falls below 1e-6 (cap T_max)."""
+    with BF16 storage (panels for the dense half, block-sparse rows for the sparse half;
+    "all_panels" repeats the run with panels for every request); a request retires when
+    its update norm falls below 1e-6 (cap T_max)."""
     import numpy as np
     import torch
 
@@ -385,8 +387,6 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
             pool.append({"n": n, "d": d, "p": p, "upper": up})
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    servers = {d: P.Server(d, P.BF16, max_slots=slots, arena_bytes=24 << 30, K=2, spectral_max_iters=SMAX,
-                           spectral_tol=1e-6, ticks_per_step=4) for d in (3, 4)}
     # arrival schedule
     arrivals = []
     t = 0.0
@@ -395,52 +395,68 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
         if t > duration:
             break
         arrivals.append((t, int(rng.integers(0, len(pool)))))
-    outs = {}
-    lat = []
-    iters = []
-    meta = {}
-    nxt = 0
-    done = 0
-    start = time.perf_counter()
-    last_finish = 0.0
-    while done < len(arrivals):
-        now = time.perf_counter() - start
-        while nxt < len(arrivals) and arrivals[nxt][0] <= now:
-            ta, k = arrivals[nxt]
-            q = pool[k]
-            X = torch.empty(q["n"] * q["d"], q["d"], device="cuda")
-            rid = servers[q["d"]].submit(q["upper"], q["n"], 1.0 / q["n"], T_max, tol, X)
-            meta[(q["d"], rid)] = (ta, X)
-            nxt += 1
-        busy = False
-        for d, srv in servers.items():
-            a, qd = srv.step()
-            busy = busy or a > 0 or qd > 0
-            for r in srv.poll():
-                ta, X = meta.pop((d, r.id))
-                fin = time.perf_counter() - start
-                lat.append(fin - ta)
-                iters.append(r.iters)
-                last_finish = max(last_finish, fin)
-                done += 1
-        if not busy and nxt < len(arrivals):
-            wait = arrivals[nxt][0] - (time.perf_counter() - start)
-            if wait > 0:
-                time.sleep(min(wait, 0.002))
-    for srv in servers.values():
-        srv.close()
-    lat = np.array(lat)
+
+    def simulate(sparse_rows: bool):
+        """Serve the arrival sequence; the sparse half as block-sparse rows or as panels."""
+        servers = {d: P.Server(d, P.BF16, max_slots=slots, arena_bytes=24 << 30, K=2, spectral_max_iters=SMAX,
+                               spectral_tol=1e-6, ticks_per_step=4) for d in (3, 4)}
+        if sparse_rows:
+            # block-sparse rows where they store under a third of the panels' bytes
+            # (below that the row kernel's lower bandwidth still wins)
+            for q in pool:
+                if q["p"] < 1.0 and "bcsr_bytes" not in q:
+                    q["bcsr_bytes"] = P.nsrgs_bcsr_packed_bytes(q["upper"], q["n"], q["d"], P.BCSR_BF16)
+                    q["use_bcsr"] = q["bcsr_bytes"] * 3 < P.nsrgs_packed_bytes(q["n"], q["d"], P.BF16)
+        lat, iters, meta = [], [], {}
+        nxt = done = 0
+        start = time.perf_counter()
+        last_finish = 0.0
+        while done < len(arrivals):
+            now = time.perf_counter() - start
+            while nxt < len(arrivals) and arrivals[nxt][0] <= now:
+                ta, k = arrivals[nxt]
+                q = pool[k]
+                X = torch.empty(q["n"] * q["d"], q["d"], device="cuda")
+                sp = sparse_rows and q.get("use_bcsr", False)
+                rid = servers[q["d"]].submit(q["upper"], q["n"], 1.0 / q["n"], T_max, tol, X, sparse=sp,
+                                             packed_bytes=q["bcsr_bytes"] if sp else 0)
+                meta[(q["d"], rid)] = (ta, X)
+                nxt += 1
+            busy = False
+            for d, srv in servers.items():
+                a, qd = srv.step()
+                busy = busy or a > 0 or qd > 0
+                for r in srv.poll():
+                    ta, X = meta.pop((d, r.id))
+                    fin = time.perf_counter() - start
+                    lat.append(fin - ta)
+                    iters.append(r.iters)
+                    last_finish = max(last_finish, fin)
+                    done += 1
+            if not busy and nxt < len(arrivals):
+                wait = arrivals[nxt][0] - (time.perf_counter() - start)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+        for srv in servers.values():
+            srv.close()
+        lat = np.array(lat)
+        return {
+            "solves_per_s": len(arrivals) / last_finish,
+            "p50_ms": float(1e3 * np.percentile(lat, 50)),
+            "p99_ms": float(1e3 * np.percentile(lat, 99)),
+            "mean_iters": float(np.mean(iters)),
+            "max_iters": int(np.max(iters)),
+        }
+
     res = {
         "requests": len(arrivals),
         "offered_rate_per_s": rate,
-        "solves_per_s": len(arrivals) / last_finish,
-        "p50_ms": float(1e3 * np.percentile(lat, 50)),
-        "p99_ms": float(1e3 * np.percentile(lat, 99)),
-        "mean_iters": float(np.mean(iters)),
-        "max_iters": int(np.max(iters)),
+        **simulate(True),
         "pool": f"{len(pool)} distinct requests (device-generated), n log-uniform [100, 8000], d in {{3, 4}}, half block-sparse",
         "generation_s": gen_s,
-        "storage": "bf16",
+        "storage": "bf16 panels; bf16 block-sparse rows for sparse requests storing < 1/3 of their panel bytes",
+        "block_sparse_requests_in_pool": sum(1 for q in pool if q.get("use_bcsr", False)),
+        "all_panels": simulate(False),
     }
     # plain sequential FP32 form: one request at a time (single-instance solve), same arrivals
     solve_s = {}

@@ -272,8 +272,9 @@ size_t nsrgs_batch_workspace_bytes(const int* n, int count, int d);
 /* Solves `count` independent instances (Algorithm 2 for each: spectral start
  * when init != 0, then T iterations with K Newton-Schulz steps; tol > 0 stops
  * an instance after its first iteration with update norm below tol) in one
- * CUDA-graph replay.  All instances share d (1..4) and the symmetric storage
- * (F32, BF16 or FP8E4M3); n and eta differ per instance.  Each tick is one
+ * CUDA-graph replay.  All instances share d (1..4) and the storage (F32, BF16
+ * or FP8E4M3 panels, or BCSR_F32 / BCSR_BF16 block-sparse rows, streamed by a
+ * warp-per-row kernel); n and eta differ per instance.  Each tick is one
  * A-stream launch over every active instance (their steps concatenated and
  * split evenly over the SMs) plus one launch with a CTA per instance for the
  * d x d work, so instances in their spectral phase and in their iterations
@@ -334,6 +335,13 @@ nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void* arena, si
  * the request could never fit in the arena. */
 nsrgs_status nsrgs_server_submit(nsrgs_server* s, const float* upper, int n, float eta, int T_max, double tol,
                                  float* X, uint64_t* id);
+
+/* nsrgs_server_submit for a request stored as block-sparse rows when `sparse` is
+ * nonzero (NSRGS_BCSR_F32 for an F32 server, NSRGS_BCSR_BF16 otherwise):
+ * packed_bytes is its exact packed size from nsrgs_bcsr_packed_bytes (the
+ * admission budget counts it).  With sparse == 0 this is nsrgs_server_submit. */
+nsrgs_status nsrgs_server_submit_ex(nsrgs_server* s, const float* upper, int n, float eta, int T_max, double tol,
+                                    int sparse, size_t packed_bytes, float* X, uint64_t* id);
 
 /* Admits, runs ticks_per_step ticks, retires; synchronises `st`.  active and
  * queued (nullable) receive the requests in flight and waiting afterwards. */

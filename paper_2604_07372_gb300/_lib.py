@@ -483,6 +483,9 @@ class Server:
             ("nsrgs_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
                                                    ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                                    ctypes.POINTER(ctypes.c_uint64)]),
+            ("nsrgs_server_submit_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                                      ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_size_t,
+                                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
             ("nsrgs_server_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             ("nsrgs_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerResult), ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int)]),
@@ -497,13 +500,18 @@ class Server:
         self._keep = {}
         cfg = _ServerConfig(d, storage, max_slots, K, spectral_max_iters, spectral_tol, ticks_per_step,
                             1 if ns_safeguard else 0)
+        self.sparse_storage = BCSR_F32 if storage == F32 else BCSR_BF16
         h = ctypes.c_void_p(0)
         _check(L.nsrgs_server_create(ctypes.byref(cfg), _ptr(self.arena), self.arena.numel(), _stream(), ctypes.byref(h)))
         self._h = h
 
-    def submit(self, upper: torch.Tensor, n: int, eta: float, T_max: int, tol: float, X: torch.Tensor) -> int:
+    def submit(self, upper: torch.Tensor, n: int, eta: float, T_max: int, tol: float, X: torch.Tensor,
+               sparse: bool = False, packed_bytes: int = 0) -> int:
+        """Queue a request; sparse=True stores it as block-sparse rows (packed_bytes from
+        nsrgs_bcsr_packed_bytes with the server's sparse storage, see sparse_storage)."""
         rid = ctypes.c_uint64(0)
-        _check(self._L.nsrgs_server_submit(self._h, _ptr(upper), n, eta, T_max, tol, _ptr(X), ctypes.byref(rid)))
+        _check(self._L.nsrgs_server_submit_ex(self._h, _ptr(upper), n, eta, T_max, tol, 1 if sparse else 0,
+                                              packed_bytes, _ptr(X), ctypes.byref(rid)))
         self._keep[rid.value] = (upper, X)
         return rid.value
 

@@ -15,11 +15,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "batch.cuh"
+#include "bcsr.cuh"
 #include "blockops.cuh"
 #include "panel.cuh"
 
@@ -293,6 +295,53 @@ __global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
 }
 
 // ------------------------------------------------------------- launchers
+// Block-sparse instances: one warp per global row; the row's instance by binary
+// search over rbase (instances with no rows share their successor's base, and
+// the last index with rbase <= r is the instance that owns row r).  Each
+// instance reads its own current X as in the panel source.
+template <int D, class T>
+__global__ void __launch_bounds__(256, 4) bcsr_batch_kernel(const BatchDesc* descs, const long long* rbase, int cnt) {
+  __shared__ float red[8][32 * 5];
+  const int lane = threadIdx.x & 31;
+  const long long total = rbase[cnt];
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < total; r += nwarps) {
+    const int inst = find_first_leq(rbase, cnt, r);
+    const BatchDesc& d = descs[inst];
+    const Ctl* c = d.ctl;
+    const int ph = c->phase;
+    const float* X;
+    if (ph == PHASE_SPEC)
+      X = d.X[(c->spec_iters + 1) & 1];
+    else if (ph == PHASE_ITER)
+      X = d.X[c->iters_done & 1];
+    else
+      continue;
+    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane, red[threadIdx.x >> 5]);
+  }
+}
+
+cudaError_t batch_bcsr_stream(const BatchDesc* descs, const long long* rbase, int count, int d, int elem_bf16,
+                              long long total_rows, cudaStream_t st) {
+  // grid sized for the largest row total the table can hold; rows past the
+  // current total return at once
+  const long long g = std::max<long long>(1, std::min<long long>((total_rows + 7) / 8, 4LL * num_sms()));
+#define L(DD)                                                                                          \
+  if (elem_bf16)                                                                                       \
+    bcsr_batch_kernel<DD, __nv_bfloat16><<<(unsigned)g, 256, 0, st>>>(descs, rbase, count);           \
+  else                                                                                                 \
+    bcsr_batch_kernel<DD, float><<<(unsigned)g, 256, 0, st>>>(descs, rbase, count);
+  switch (d) {
+    case 1: L(1); break;
+    case 2: L(2); break;
+    case 3: L(3); break;
+    case 4: L(4); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef L
+  return cudaGetLastError();
+}
+
 template <int D, int ST>
 static cudaError_t launch_batch_stream_t(const BatchSrc& s, cudaStream_t st, bool prepare) {
   using C = PCfg<D, ST>;
@@ -364,11 +413,12 @@ size_t batch_instance_bytes(int n, int d) {
   return 256 + 4 * vec;
 }
 
+// Table region: descriptors | panel step bases | reports | block-sparse row bases.
 size_t batch_table_bytes(int count) {
   const size_t t = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
   const size_t b = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
   const size_t r = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
-  return t + b + r;
+  return t + 2 * b + r;
 }
 
 void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d) {
@@ -425,7 +475,9 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
                                           size_t ws_bytes, void* stv) {
   NSRGS_CHECK_ARG(items != nullptr && count >= 1 && count <= (1 << 20), "items must be non-null, count >= 1");
   NSRGS_CHECK_ARG(d >= 1 && d <= 4, "the batched form covers 1 <= d <= 4");
-  NSRGS_CHECK_ARG(storage >= NSRGS_F32 && storage <= NSRGS_FP8E4M3, "batched storage must be F32, BF16 or FP8E4M3");
+  const bool sparse = storage == NSRGS_BCSR_F32 || storage == NSRGS_BCSR_BF16;
+  NSRGS_CHECK_ARG((storage >= NSRGS_F32 && storage <= NSRGS_FP8E4M3) || sparse,
+                  "batched storage must be F32, BF16, FP8E4M3, BCSR_F32 or BCSR_BF16");
   NSRGS_CHECK_ARG(T >= 0 && T <= 100000 && K >= 0 && K <= 64, "T in [0, 100000], K in [0, 64]");
   NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
   NSRGS_CHECK_ARG(!init || (spectral_max_iters >= 1 && spectral_max_iters <= 10000),
@@ -453,14 +505,24 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   BatchDesc* d_descs = reinterpret_cast<BatchDesc*>(base);
   long long* d_base = reinterpret_cast<long long*>(base + tbytes);
   BatchReport* d_rep = reinterpret_cast<BatchReport*>(base + tbytes + bbytes);
+  const size_t rbytes = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
+  long long* d_rbase = reinterpret_cast<long long*>(base + tbytes + bbytes + rbytes);
   std::vector<BatchDesc> descs(count);
-  std::vector<long long> bases(count + 1);
+  std::vector<long long> bases(count + 1), rbases(count + 1);
   size_t off = batch_table_bytes(count);
-  long long steps = 0;
+  long long steps = 0, rows = 0;
   for (int i = 0; i < count; ++i) {
     BatchDesc& ds = descs[i];
     memset(&ds, 0, sizeof(ds));
-    if (!make_panel_geom(items[i].n, d, storage, &ds.g)) {
+    rbases[i] = rows;
+    if (sparse) {
+      // no panel steps: the row kernel streams this instance
+      ds.sparse = 1;
+      ds.g.n = items[i].n;
+      ds.g.D = d;
+      ds.g.storage = storage;
+      rows += items[i].n;
+    } else if (!make_panel_geom(items[i].n, d, storage, &ds.g)) {
       set_error("unsupported (n, d, storage) in batch");
       return NSRGS_ERR_UNSUPPORTED;
     }
@@ -480,9 +542,11 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     steps += ds.g.total_steps;
   }
   bases[count] = steps;
-  NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
+  rbases[count] = rows;
+  if (!sparse) NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_base, bases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(d_rbase, rbases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
 
   int dev = 0;
   NSRGS_CUDA_TRY(cudaGetDevice(&dev));
@@ -513,7 +577,8 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     if (e == cudaSuccess) e = batch_admit(d_descs, count, d, cs);
     const int ticks = (init ? spectral_max_iters : 0) + T;
     for (int t = 0; t < ticks && e == cudaSuccess; ++t) {
-      e = batch_stream(d_descs, d_base, count, d, storage, cs, false);
+      e = sparse ? batch_bcsr_stream(d_descs, d_rbase, count, d, storage == NSRGS_BCSR_BF16, rows, cs)
+                 : batch_stream(d_descs, d_base, count, d, storage, cs, false);
       if (e == cudaSuccess) e = batch_phase(d_descs, count, d, cs);
     }
     if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);

@@ -20,6 +20,7 @@ struct BatchDesc {
   int smax;               // spectral passes cap
   int start_given;        // 1: X^0 comes from Xout, no spectral initialisation
   int safeguard;          // 1: safeguarded Newton-Schulz start (beyond the paper)
+  int sparse;             // 1: block-sparse rows (streamed by the row kernel, no panel steps)
   double tol;             // stop when the update norm falls below it (0: run T iterations)
   double spec_tol;        // spectral residual target
 };
@@ -36,6 +37,10 @@ struct BatchReport {
 size_t batch_instance_bytes(int n, int d);
 size_t batch_table_bytes(int count);
 void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d);
+// The row kernel over the block-sparse instances: rbase[i] = first global row of
+// instance i (instances without block-sparse storage add no rows).
+cudaError_t batch_bcsr_stream(const BatchDesc* descs, const long long* rbase, int count, int d, int elem_bf16,
+                              long long total_rows, cudaStream_t st);
 cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int count, int d, int storage,
                          cudaStream_t st, bool prepare);
 cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st);

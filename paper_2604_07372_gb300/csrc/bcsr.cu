@@ -18,22 +18,12 @@
 // order with warp ballots, so the result does not depend on thread timing.
 #include <algorithm>
 
+#include "bcsr.cuh"
 #include "src.cuh"
 
 namespace nsrgs {
 
-constexpr int kBcsrHeader = 64;
-
-__host__ __device__ inline long long bcsr_align(long long x) { return (x + 15) / 16 * 16; }
-__host__ __device__ inline int bcsr_elem_bytes(int storage) { return storage == NSRGS_BCSR_BF16 ? 2 : 4; }
-__host__ __device__ inline long long bcsr_off_col(int n) { return bcsr_align(kBcsrHeader + 8LL * (n + 1)); }
-__host__ __device__ inline long long bcsr_off_val(int n, long long nnzb) {
-  return bcsr_align(bcsr_off_col(n) + 4LL * nnzb);
-}
-long long bcsr_bytes(int n, int d, int storage, long long nnzb) {
-  const long long b = bcsr_off_val(n, nnzb) + nnzb * d * d * bcsr_elem_bytes(storage);
-  return (b + 255) / 256 * 256;
-}
+long long bcsr_bytes(int n, int d, int storage, long long nnzb) { return bcsr_bytes_of(n, d, storage, nnzb); }
 
 // Block (min(i, j), max(i, j)) of the strict upper triangle has a nonzero entry.
 template <class Src>
@@ -66,8 +56,9 @@ __global__ void __launch_bounds__(256) bcsr_count_kernel(Src src, int n, int d, 
 }
 
 // One CTA: rowptr (at packed + 64) = exclusive scan of deg, written in place over
-// deg's copy; header fields filled from the total.
-__global__ void __launch_bounds__(1024) bcsr_scan_kernel(uint8_t* packed, int n, int d) {
+// deg's copy; header fields filled from the total; the alignment gaps and the
+// tail are zeroed so that a packed buffer is a function of the data alone.
+__global__ void __launch_bounds__(1024) bcsr_scan_kernel(uint8_t* packed, int n, int d, int storage) {
   long long* rowptr = reinterpret_cast<long long*>(packed + kBcsrHeader);  // holds deg on entry
   __shared__ long long part[1024];
   const int t = threadIdx.x;
@@ -90,7 +81,12 @@ __global__ void __launch_bounds__(1024) bcsr_scan_kernel(uint8_t* packed, int n,
     hdr[2] = run;
     hdr[3] = bcsr_off_col(n);
     hdr[4] = bcsr_off_val(n, run);
+    for (int k = 5; k < kBcsrHeader / 8; ++k) hdr[k] = 0;
     rowptr[n] = run;
+    for (long long b = kBcsrHeader + 8LL * (n + 1); b < hdr[3]; ++b) packed[b] = 0;
+    for (long long b = hdr[3] + 4 * run; b < hdr[4]; ++b) packed[b] = 0;
+    for (long long b = hdr[4] + run * d * d * bcsr_elem_bytes(storage); b < bcsr_bytes_of(n, d, storage, run); ++b)
+      packed[b] = 0;
   }
   __syncthreads();
   long long run = part[t];
@@ -137,69 +133,17 @@ __global__ void __launch_bounds__(256) bcsr_fill_kernel(Src src, int n, int d, u
 }
 
 // ------------------------------------------------------------------ stream
-__device__ __forceinline__ float bcsr_load(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float bcsr_load(const __nv_bfloat16* p) {
-  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
-}
-
-// Y_i = sum_j A_ij X_j, warp per block row: lanes take the row's blocks in turn,
-// accumulate d x d partials in registers (one X_j row at a time), then a warp
-// reduction; Y_i is written (not accumulated), so Y needs no zeroing.
+// Warp per block row (bcsr_row_product).
 template <int D, class T>
-__global__ void __launch_bounds__(256) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
+__global__ void __launch_bounds__(256, D <= 5 ? 4 : 1) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
                                                            const float* __restrict__ X, float* __restrict__ Y,
                                                            const int* skip) {
   if (*skip) return;
-  const long long* hdr = reinterpret_cast<const long long*>(packed);
-  const long long* rowptr = reinterpret_cast<const long long*>(packed + kBcsrHeader);
-  const int* col = reinterpret_cast<const int*>(packed + hdr[3]);
-  const T* val = reinterpret_cast<const T*>(packed + hdr[4]);
+  __shared__ float red[8][32 * 5];
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
-    float acc[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[r][c] = 0.f;
-    const long long k1 = rowptr[i + 1];
-    for (long long k = rowptr[i] + lane; k < k1; k += 32) {
-      const int j = __ldg(col + k);
-      const T* a = val + k * D * D;
-      const float* x = X + (long long)j * D * D;
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        float xr[D], am[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) xr[c] = __ldg(x + m * D + c);
-#pragma unroll
-        for (int r = 0; r < D; ++r) am[r] = bcsr_load(a + r * D + m);
-#pragma unroll
-        for (int r = 0; r < D; ++r)
-#pragma unroll
-          for (int c = 0; c < D; ++c) acc[r][c] = fmaf(am[r], xr[c], acc[r][c]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        float v = acc[r][c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[r][c] = v;
-      }
-    float* y = Y + i * D * D;
-    for (int e = lane; e < D * D; e += 32) {
-      float v = 0.f;
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (r * D + c == e) v = acc[r][c];
-      y[e] = v;
-    }
-  }
+  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps)
+    bcsr_row_product<D, T>(packed, i, X, Y, lane, red[threadIdx.x >> 5]);
 }
 
 // ---------------------------------------------------------------- host
@@ -207,7 +151,7 @@ bool bcsr_storage(int storage) { return storage == NSRGS_BCSR_F32 || storage == 
 
 static int bcsr_grid(int n) {
   const long long g = ((long long)n + 7) / 8;  // 8 warps per CTA, one row each per sweep
-  return (int)std::min<long long>(std::max<long long>(g, 1), 16LL * num_sms());
+  return (int)std::min<long long>(std::max<long long>(g, 1), 4LL * num_sms());
 }
 
 template <class Src>
@@ -224,7 +168,7 @@ static cudaError_t bcsr_pack(Src src, int n, int d, int storage, uint8_t* packed
   bcsr_count_kernel<<<bcsr_grid(n), 256, 0, st>>>(src, n, d, deg, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  bcsr_scan_kernel<<<1, 1024, 0, st>>>(packed, n, d);
+  bcsr_scan_kernel<<<1, 1024, 0, st>>>(packed, n, d, storage);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (storage == NSRGS_BCSR_BF16)
     bcsr_fill_kernel<Src, __nv_bfloat16><<<bcsr_grid(n), 256, 0, st>>>(src, n, d, packed);

@@ -25,6 +25,7 @@
 
 namespace nsrgs {
 nsrgs_status pack_upper_impl(const float*, int, int, int, void*, cudaStream_t);
+long long bcsr_bytes(int n, int d, int storage, long long nnzb);
 }
 
 using namespace nsrgs;
@@ -88,6 +89,8 @@ struct Request {
   int Tmax;
   double tol;
   float* X;
+  int sparse;          // 1: block-sparse rows
+  size_t packed_bytes;  // exact packed size of a block-sparse request
 };
 
 struct Slot {
@@ -107,10 +110,11 @@ struct nsrgs_server {
   cudaStream_t st = nullptr;
   BatchDesc* d_descs = nullptr;
   long long* d_base = nullptr;
+  long long* d_rbase = nullptr;  // first global row of each slot's block-sparse rows
   BatchReport* d_rep = nullptr;
   std::vector<BatchDesc> h_descs;
   std::vector<Ctl*> idle_ctl;  // per slot: zeroed control block used while the slot is free
-  std::vector<long long> h_base;
+  std::vector<long long> h_base, h_rbase;
   std::vector<BatchReport> h_rep;
   std::vector<Slot> slots;
   std::deque<Request> queue;
@@ -155,8 +159,11 @@ extern "C" nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void
   s->d_descs = reinterpret_cast<BatchDesc*>(s->arena);
   s->d_base = reinterpret_cast<long long*>(s->arena + tbytes);
   s->d_rep = reinterpret_cast<BatchReport*>(s->arena + tbytes + bbytes);
+  const size_t rbytes = ((size_t)M * sizeof(BatchReport) + 255) / 256 * 256;
+  s->d_rbase = reinterpret_cast<long long*>(s->arena + tbytes + bbytes + rbytes);
   s->h_descs.assign(M, BatchDesc{});
   s->h_base.assign(M + 1, 0);
+  s->h_rbase.assign(M + 1, 0);
   s->h_rep.assign(M, BatchReport{});
   s->slots.assign(M, Slot{});
   s->alloc.reset(tb, arena_bytes);
@@ -185,20 +192,32 @@ extern "C" nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void
   return NSRGS_OK;
 }
 
+// Block-sparse requests take the element type of the server's panel storage.
+static int sparse_storage(const nsrgs_server* s) { return s->cfg.storage == NSRGS_F32 ? NSRGS_BCSR_F32 : NSRGS_BCSR_BF16; }
+
 extern "C" nsrgs_status nsrgs_server_submit(nsrgs_server* s, const float* upper, int n, float eta, int T_max,
                                             double tol, float* X, uint64_t* id) {
+  return nsrgs_server_submit_ex(s, upper, n, eta, T_max, tol, 0, 0, X, id);
+}
+
+extern "C" nsrgs_status nsrgs_server_submit_ex(nsrgs_server* s, const float* upper, int n, float eta, int T_max,
+                                               double tol, int sparse, size_t packed_bytes, float* X, uint64_t* id) {
   NSRGS_CHECK_ARG(s && upper && X && id, "null argument");
+  NSRGS_CHECK_ARG(n >= 2, "n must be >= 2");
+  NSRGS_CHECK_ARG(!sparse || packed_bytes >= (size_t)bcsr_bytes(n, s->cfg.d, sparse_storage(s), 0),
+                  "a block-sparse request needs its packed size (nsrgs_bcsr_packed_bytes)");
   NSRGS_CHECK_ARG(n >= 2 && (long long)n * s->cfg.d <= (1LL << 24), "n out of range");
   NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
   NSRGS_CHECK_ARG(T_max >= 1 && T_max <= 1000000, "T_max in [1, 1000000]");
   NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
   NSRGS_CHECK_ARG((reinterpret_cast<uintptr_t>(X) & 15u) == 0, "X must be 16-byte aligned");
-  const size_t need = nsrgs_packed_bytes(n, s->cfg.d, s->cfg.storage) + batch_instance_bytes(n, s->cfg.d) + 512;
+  const size_t abytes = sparse ? packed_bytes : nsrgs_packed_bytes(n, s->cfg.d, s->cfg.storage);
+  const size_t need = abytes + batch_instance_bytes(n, s->cfg.d) + 512;
   if (need > s->arena_bytes - server_table_bytes(s->cfg.max_slots)) {
     set_error("request can never fit in the server's arena");
     return NSRGS_ERR_NOMEM;
   }
-  Request r{s->next_id++, upper, n, eta, T_max, tol, X};
+  Request r{s->next_id++, upper, n, eta, T_max, tol, X, sparse ? 1 : 0, abytes};
   s->queue.push_back(r);
   *id = r.id;
   return NSRGS_OK;
@@ -214,6 +233,9 @@ static cudaError_t server_capture(nsrgs_server* s) {
     e = batch_admit(s->d_descs, M, d, cs);
     for (int t = 0; t < s->cfg.ticks_per_step && e == cudaSuccess; ++t) {
       e = batch_stream(s->d_descs, s->d_base, M, d, s->cfg.storage, cs, false);
+      // block-sparse slots (none: the row kernel finds no rows and returns)
+      if (e == cudaSuccess)
+        e = batch_bcsr_stream(s->d_descs, s->d_rbase, M, d, sparse_storage(s) == NSRGS_BCSR_BF16, 1LL << 40, cs);
       if (e == cudaSuccess) e = batch_phase(s->d_descs, M, d, cs);
     }
     if (e == cudaSuccess) e = batch_report(s->d_descs, M, s->d_rep, cs);
@@ -240,7 +262,8 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
       }
     if (free_slot < 0) break;
     const Request& r = s->queue.front();
-    const size_t abytes = nsrgs_packed_bytes(r.n, d, storage);
+    const int rstorage = r.sparse ? sparse_storage(s) : storage;
+    const size_t abytes = r.packed_bytes;
     const size_t wbytes = batch_instance_bytes(r.n, d);
     size_t aoff = 0, woff = 0;
     if (!s->alloc.alloc(abytes, &aoff)) break;
@@ -248,7 +271,7 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
       s->alloc.release(aoff, abytes);
       break;
     }
-    nsrgs_status ps = pack_upper_impl(r.upper, r.n, d, storage, s->arena + aoff, s->st);
+    nsrgs_status ps = pack_upper_impl(r.upper, r.n, d, rstorage, s->arena + aoff, s->st);
     if (ps != NSRGS_OK) return ps;
     Slot& sl = s->slots[free_slot];
     sl.busy = true;
@@ -259,7 +282,14 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
     sl.w_bytes = wbytes;
     BatchDesc& ds = s->h_descs[free_slot];
     memset(&ds, 0, sizeof(ds));
-    make_panel_geom(r.n, d, storage, &ds.g);
+    if (r.sparse) {
+      ds.sparse = 1;  // no panel steps: streamed by the row kernel
+      ds.g.n = r.n;
+      ds.g.D = d;
+      ds.g.storage = rstorage;
+    } else {
+      make_panel_geom(r.n, d, storage, &ds.g);
+    }
     ds.packed = s->arena + aoff;
     fill_instance(ds, s->arena + woff, r.n, d);
     ds.Xout = r.X;
@@ -277,12 +307,19 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
   }
   // 2. instance table: only busy slots contribute steps (even split over active work)
   if (s->dirty) {
-    long long steps = 0;
+    long long steps = 0, rows = 0;
     for (int i = 0; i < M; ++i) {
       s->h_base[i] = steps;
-      if (s->slots[i].busy) steps += s->h_descs[i].g.total_steps;
+      s->h_rbase[i] = rows;
+      if (s->slots[i].busy) {
+        steps += s->h_descs[i].g.total_steps;
+        if (s->h_descs[i].sparse) rows += s->h_descs[i].g.n;
+      }
     }
     s->h_base[M] = steps;
+    s->h_rbase[M] = rows;
+    NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_rbase, s->h_rbase.data(), sizeof(long long) * (M + 1),
+                                   cudaMemcpyHostToDevice, s->st));
     NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_descs, s->h_descs.data(), sizeof(BatchDesc) * M, cudaMemcpyHostToDevice, s->st));
     NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_base, s->h_base.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice,
                                    s->st));

@@ -110,3 +110,25 @@ def test_batch_reduced_precision_within_one_percent(P, storage):
         Z = I.Zstack()
         ea, eb = O.dF(to64(a), Z, d), O.dF(to64(b), Z, d)
         assert abs(eb - ea) / ea <= 0.01, (I.n, ea, eb)
+
+
+@pytest.mark.parametrize("storage", ["bcsr_f32", "bcsr_bf16"])
+def test_block_sparse_batch_alone_and_against_oracle(P, storage):
+    """Block-sparse rows in the batched form (warp-per-row kernel over every
+    instance's rows): each instance equals its single-instance solve, and the
+    F32 batch matches the oracle."""
+    d, T, K = 3, 30, 2
+    specs = [(2, 0.3, 1.0), (150, 0.3, 0.2), (300, 0.2, 0.05), (77, 0.4, 0.5), (64, 0.3, 1.0)]
+    insts = [inst(n, d, c, seed=900 + k, p=p) for k, (n, c, p) in enumerate(specs)]
+    st = P.STORAGE[storage]
+    packs = [pack(P, I, st) for I in insts]
+    Xs, infos = P.nsrgs_batch_solve(packs, [1.0 / I.n for I in insts], T, K, spectral_max_iters=80)
+    torch.cuda.synchronize()
+    for I, pa, X, info in zip(insts, packs, Xs, infos):
+        assert info.iters == T
+        Xa, _ = P.nsrgs_solve(pa, 1.0 / I.n, T, K, spectral_max_iters=80)
+        torch.cuda.synchronize()
+        assert O.dF(to64(X), to64(Xa), d) / math.sqrt(I.n * d) <= 1e-5
+        if storage == "bcsr_f32" and I.n > 2:
+            Xo, _ = O.nsrgs(I.dense(), I.n, d, 1.0 / I.n, T, K)
+            assert O.dF(to64(X), Xo, d) / math.sqrt(I.n * d) <= 1e-5

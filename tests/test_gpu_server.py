@@ -105,3 +105,36 @@ def test_request_that_can_never_fit_is_refused(P):
         srv.submit(torch.from_numpy(I.upper).cuda(), n, 1.0 / n, 10, 0.0, torch.empty(3 * n, 3, device="cuda"))
     assert e.value.status == 3
     srv.close()
+
+
+def test_sparse_and_dense_requests_share_ticks(P):
+    """Block-sparse requests (warp-per-row kernel) and panel requests in the same
+    server: each result equals the same request solved alone."""
+    d, tol, Tmax = 3, 1e-6, 600
+    specs = [(200, 0.3, 1.0), (300, 0.3, 0.2), (150, 0.3, 1.0), (400, 0.25, 0.1), (120, 0.3, 0.5), (250, 0.3, 1.0)]
+    insts = _requests(d, specs)
+    ups = [torch.from_numpy(I.upper).cuda() for I in insts]
+    srv = P.Server(d, P.F32, max_slots=4, arena_bytes=256 << 20, ticks_per_step=3)
+    Xs = [torch.empty(I.n * d, d, device="cuda") for I in insts]
+    sparse = [p < 1.0 for _, _, p in specs]
+    ids, done = {}, {}
+    for k, I in enumerate(insts):
+        nb = P.nsrgs_bcsr_packed_bytes(ups[k], I.n, d, srv.sparse_storage) if sparse[k] else 0
+        ids[srv.submit(ups[k], I.n, 1.0 / I.n, Tmax, tol, Xs[k], sparse=sparse[k], packed_bytes=nb)] = k
+    for _ in range(3000):
+        srv.step()
+        for r in srv.poll():
+            done[ids[r.id]] = r
+        if len(done) == len(insts):
+            break
+    assert len(done) == len(insts)
+    torch.cuda.synchronize()
+    for k, I in enumerate(insts):
+        r = done[k]
+        assert r.status == 0 and r.last_update_norm < tol, (k, r.status, r.iters, r.last_update_norm)
+        pa = P.nsrgs_pack_upper(ups[k], I.n, d, P.BCSR_F32 if sparse[k] else P.F32)
+        Xa, ia = P.nsrgs_solve(pa, 1.0 / I.n, Tmax, 2, tol=tol, spectral_max_iters=60)
+        torch.cuda.synchronize()
+        assert abs(r.iters - ia.iters) <= 1
+        assert O.dF(to64(Xs[k]), to64(Xa), d) / math.sqrt(I.n * d) <= 1e-5
+    srv.close()
