@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
+    ap.add_argument("--sweep-storages", default="", help="comma-separated subset of the sweep's storages")
     return ap.parse_args()
 
 
@@ -260,7 +261,8 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
 
 
 # ------------------------------------------------------- dimension sweep
-def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps: int = 5, T: int = 20):
+def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps: int = 5, T: int = 20,
+               only=None):
     """n = 2000, d in {3, 8, 16, 32, 64}, c = 0.3: the A-stream product per storage
     (ms, algorithmic GB/s), and short solves (T = 20) for iterations/s and final d_F."""
     import numpy as np
@@ -270,6 +272,8 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
         storages = ["dense_f32"] + (["f32", "bf16"] if d <= 8 else []) + (["dense_bf16", "bf16"] if d in (16, 32, 64) else [])
+        if only:
+            storages = [x for x in storages if x in only]
         res = {}
         Zs = Z.reshape(n * d, d)
         nb = n * (n - 1) // 2 * d * d
@@ -780,7 +784,8 @@ def main():
         torch.cuda.set_device(local)
         if args.leg == "sweep":
             dims = tuple(int(x) for x in args.sweep_dims.split(","))
-            out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps)
+            only = [x for x in args.sweep_storages.split(",") if x] or None
+            out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps, only=only)
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
         elif args.leg == "sparse":
