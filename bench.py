@@ -302,6 +302,13 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                 torch.cuda.synchronize()
                 ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
                 ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
+                # the A stream alone inside a solve (CUDA events around each launch in the graph)
+                P.nsrgs_set_kernel_timing(True)
+                P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, X=Xs, ws=ws, info=False)
+                _, kms, _ = P.nsrgs_kernel_timing()
+                P.nsrgs_set_kernel_timing(False)
+                ent["stream_ms"] = kms
+                ent["stream_GBps"] = alg / (kms / 1e3) / 1e9
                 if d <= 8 and name in ("dense_f32", "f32"):
                     Xg, _ = P.nsrgs_gpm_solve(pa, T, spectral_max_iters=SMAX, ws=ws)
                     torch.cuda.synchronize()

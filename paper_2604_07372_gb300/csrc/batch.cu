@@ -300,8 +300,7 @@ __global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
 // the last index with rbase <= r is the instance that owns row r).  Each
 // instance reads its own current X as in the panel source.
 template <int D, class T>
-__global__ void __launch_bounds__(256, 4) bcsr_batch_kernel(const BatchDesc* descs, const long long* rbase, int cnt) {
-  __shared__ float red[8][32 * 5];
+__global__ void __launch_bounds__(256) bcsr_batch_kernel(const BatchDesc* descs, const long long* rbase, int cnt) {
   const int lane = threadIdx.x & 31;
   const long long total = rbase[cnt];
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -317,7 +316,7 @@ __global__ void __launch_bounds__(256, 4) bcsr_batch_kernel(const BatchDesc* des
       X = d.X[c->iters_done & 1];
     else
       continue;
-    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane, red[threadIdx.x >> 5]);
+    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane);
   }
 }
 

@@ -135,15 +135,14 @@ __global__ void __launch_bounds__(256) bcsr_fill_kernel(Src src, int n, int d, u
 // ------------------------------------------------------------------ stream
 // Warp per block row (bcsr_row_product).
 template <int D, class T>
-__global__ void __launch_bounds__(256, D <= 5 ? 4 : 1) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
+__global__ void __launch_bounds__(256) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
                                                            const float* __restrict__ X, float* __restrict__ Y,
                                                            const int* skip) {
   if (*skip) return;
-  __shared__ float red[8][32 * 5];
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps)
-    bcsr_row_product<D, T>(packed, i, X, Y, lane, red[threadIdx.x >> 5]);
+    bcsr_row_product<D, T>(packed, i, X, Y, lane);
 }
 
 // ---------------------------------------------------------------- host
