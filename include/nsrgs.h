@@ -254,6 +254,25 @@ nsrgs_status nsrgs_solve_ex(const nsrgs_A* A, float eta, int T, int K, const nsr
                             int spectral_max_iters, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
                             void* st);
 
+/* --------------------------------------------- Stiefel form (extension) */
+
+/* The relaxation of O(d) synchronisation to row-orthonormal blocks X_i in
+ * R^{d x p} (X_i X_i^T = I_d, d <= p <= 64): the Stiefel manifold of §1.2 and
+ * the extension named in §6; not part of the paper's method.  Same objective
+ * (eq. (1)) and the same three steps per iteration, for every block from X^t:
+ *   G_i = X_i (X^T X - X_i^T X_i) - sum_{j != i} A_ij X_j
+ *   F_i = X_i - eta (G_i - sym(G_i X_i^T) X_i)
+ *   X_i^{t+1} = S_K(F_i),  S <- (3I - S S^T) S / 2   (Algorithm 1 by rows).
+ * With p = d and X_i orthogonal these are Algorithm 2's steps exactly.  A must
+ * be NSRGS_DENSE_F32 (the product runs with p columns of X).  X0 (device,
+ * nd x p, row-orthonormal blocks, e.g. [X_i^0, 0] from the O(d) start) is
+ * required; X (device, nd x p) receives the last iterate.  tol > 0 stops after
+ * the first iteration with ||X^{t+1} - X^t||_F / sqrt(ndp) < tol.  info: iters,
+ * last_update_norm, flags (synchronises when non-null). */
+size_t nsrgs_stiefel_workspace_bytes(int n, int d, int p);
+nsrgs_status nsrgs_stiefel_solve(const nsrgs_A* A, int p, float eta, int T, int K, double tol, const float* X0,
+                                 float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* st);
+
 /* ------------------------------------------------------- batched form */
 
 /* One independent instance of a batch. */

@@ -56,6 +56,11 @@ __all__ = [
     "update_norm",
     "gpm_iteration",
     "gpm",
+    "stiefel_gradient",
+    "stiefel_projection",
+    "newton_schulz_rows",
+    "polar_rows",
+    "stiefel_iteration",
     "blocks",
     "stack",
 ]
@@ -330,3 +335,60 @@ def gpm(A: np.ndarray, n: int, d: int, T: int, X0: np.ndarray | None = None):
     for _ in range(T):
         X = gpm_iteration(A, X, n, d)
     return X
+
+
+# ---------------------- beyond the paper: Stiefel form (d x p blocks)
+# The relaxation of O(d) synchronisation to row-orthonormal blocks X_i in
+# R^{d x p} (X_i X_i^T = I_d, p >= d), which §1.2 cites (Stiefel manifold,
+# Burer-Monteiro) and §6 names as an extension.  The same objective F (eq. (1))
+# and the same three steps as Algorithm 2; with p = d they are Algorithm 2's.
+def stiefel_gradient(A: np.ndarray, X: np.ndarray, n: int, d: int) -> np.ndarray:
+    """Blockwise Euclidean gradient at X (nd x p) as (n, d, p) blocks, the gradient of
+    f_i = 1/2 sum_{j != i} ||X_i X_j^T - A_ij||^2 in X_i (half of dF/dX_i, as in Algorithm 2):
+    G_i = sum_{j != i} (X_i X_j^T - A_ij) X_j = X_i (X^T X - X_i^T X_i) - (A_off X)_i.
+    (For X_j in O(d), X_j^T X_j = I and this is Algorithm 2's (n-1) X_i - (A_off X)_i.)"""
+    A = np.asarray(A, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    Xb = X.reshape(n, d, -1)
+    C = X.T @ X
+    AX = (A @ X).reshape(n, d, -1)
+    Aii = np.stack([A[i * d : (i + 1) * d, i * d : (i + 1) * d] for i in range(n)])
+    Y = AX - Aii @ Xb  # (A_off X)_i = sum_{j != i} A_ij X_j
+    return Xb @ (C[None, :, :] - np.swapaxes(Xb, -1, -2) @ Xb) - Y
+
+
+def stiefel_projection(Xi: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Projection onto the tangent space of the row-orthonormal matrices at X_i:
+    P(G) = G - sym(G X_i^T) X_i  (tangent vectors H satisfy H X_i^T + X_i H^T = 0).
+    With X_i square and orthogonal this is the paper's (G - X_i G^T X_i)/2."""
+    Xi = np.asarray(Xi, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    T = G @ np.swapaxes(Xi, -1, -2)
+    return G - 0.5 * (T + np.swapaxes(T, -1, -2)) @ Xi
+
+
+def newton_schulz_rows(M: np.ndarray, Ts: int) -> np.ndarray:
+    """Algorithm 1 for a d x p block with full row rank: S <- (3I - S S^T) S / 2,
+    Ts times; converges to the polar factor U V^T of M = U Sigma V^T when the
+    singular values lie in (0, sqrt(3)).  For square M this is Algorithm 1."""
+    S = np.array(M, dtype=np.float64, copy=True)
+    d = S.shape[-2]
+    I = np.eye(d)
+    for _ in range(Ts):
+        S = 0.5 * ((3.0 * I - S @ np.swapaxes(S, -1, -2)) @ S)
+    return S
+
+
+def polar_rows(M: np.ndarray) -> np.ndarray:
+    """Polar factor U V^T of a full-row-rank d x p matrix (thin SVD)."""
+    U, _, Vt = np.linalg.svd(np.asarray(M, dtype=np.float64), full_matrices=False)
+    return U @ Vt
+
+
+def stiefel_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, Ts: int) -> np.ndarray:
+    """One sweep of the Stiefel form for all blocks from X (nd x p)."""
+    X = np.asarray(X, dtype=np.float64)
+    Xb = X.reshape(n, d, -1)
+    G = stiefel_gradient(A, X, n, d)
+    F = Xb - mu * stiefel_projection(Xb, G)
+    return newton_schulz_rows(F, Ts).reshape(n * d, -1)

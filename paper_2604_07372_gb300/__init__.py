@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     STOP_UPDATE_NORM,
     STOP_REL_DECREASE,
     nsrgs_objective,
+    nsrgs_stiefel_solve,
     nsrgs_dF,
     nsrgs_version,
     nsrgs_set_kernel_timing,

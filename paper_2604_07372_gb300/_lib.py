@@ -347,6 +347,31 @@ def nsrgs_solve_ex(
     return X, inf
 
 
+def nsrgs_stiefel_solve(A: PackedA, p: int, eta: float, T: int, K: int, X0: torch.Tensor, tol: float = 0.0,
+                        X: torch.Tensor | None = None, info: bool = True):
+    """Stiefel form (d x p row-orthonormal blocks) from X0 (nd x p); returns (X, Info or None)."""
+    L = lib()
+    fn = L.nsrgs_stiefel_solve
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(_A), ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Info), ctypes.c_void_p, ctypes.c_size_t,
+                   ctypes.c_void_p]
+    wb = L.nsrgs_stiefel_workspace_bytes
+    wb.restype = ctypes.c_size_t
+    wb.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    nbytes = int(wb(A.n, A.d, p))
+    if nbytes == 0:
+        raise ValueError("unsupported (n, d, p)")
+    w = torch.empty(nbytes, dtype=torch.uint8, device=A.buf.device)
+    if X is None:
+        X = torch.empty(A.n * A.d, p, dtype=torch.float32, device=A.buf.device)
+    a = A.struct()
+    inf = Info() if info else None
+    _check(fn(ctypes.byref(a), p, eta, T, K, tol, _ptr(X0), _ptr(X), ctypes.byref(inf) if inf is not None else None,
+              _ptr(w), w.numel(), _stream()))
+    return X, inf
+
+
 def nsrgs_objective(A: PackedA, X: torch.Tensor, ws=None) -> float:
     """F(X) of eq. (1) for the stored A."""
     w = _ws(A, ws)

@@ -143,18 +143,25 @@ cudaError_t stream_panel_prepare(const PanelGeom& g) {
 
 long long dense_pitch(int n, int d);
 
-cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float* Y, const int* skip,
-                         cudaStream_t st) {
+// Y = A_off X for an X with `width` columns (d for the method, p for the Stiefel form).
+cudaError_t stream_dense_width(const void* packed, int n, int d, int width, const float* X, float* Y,
+                               const int* skip, cudaStream_t st) {
   const int N = n * d;
   const int pitch = (int)dense_pitch(n, d);
   dim3 grid((N + 63) / 64);
   const float* A = reinterpret_cast<const float*>(packed);
-  if (d <= 4) dense_stream_kernel<4><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
-  else if (d <= 8) dense_stream_kernel<8><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
-  else if (d <= 16) dense_stream_kernel<16><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
-  else if (d <= 32) dense_stream_kernel<32><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
-  else dense_stream_kernel<64><<<grid, 256, 0, st>>>(A, N, pitch, d, X, Y, skip);
+  const int w = width;
+  if (w <= 4) dense_stream_kernel<4><<<grid, 256, 0, st>>>(A, N, pitch, w, X, Y, skip);
+  else if (w <= 8) dense_stream_kernel<8><<<grid, 256, 0, st>>>(A, N, pitch, w, X, Y, skip);
+  else if (w <= 16) dense_stream_kernel<16><<<grid, 256, 0, st>>>(A, N, pitch, w, X, Y, skip);
+  else if (w <= 32) dense_stream_kernel<32><<<grid, 256, 0, st>>>(A, N, pitch, w, X, Y, skip);
+  else dense_stream_kernel<64><<<grid, 256, 0, st>>>(A, N, pitch, w, X, Y, skip);
   return cudaGetLastError();
+}
+
+cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float* Y, const int* skip,
+                         cudaStream_t st) {
+  return stream_dense_width(packed, n, d, d, X, Y, skip, st);
 }
 
 }  // namespace nsrgs

@@ -407,3 +407,74 @@ def test_safeguard_keeps_the_low_p_step_finite():
         X = O.nsrgs_iteration(A, X, n, d, 1.0 / (n * p), 2, safeguard=True)
         assert np.all(np.isfinite(X))
     assert O.dF(X, inst.Zstack(), d) / math.sqrt(n * d) < 1.0
+
+
+# ---------------------- beyond the paper: Stiefel form (d x p blocks)
+def _row_orthonormal(rng, n, d, p):
+    g = rng.standard_normal((n, d, p))
+    return np.stack([O.polar_rows(b) for b in g])
+
+
+def test_stiefel_reduces_to_algorithm_2_when_p_equals_d():
+    n, d = 60, 3
+    inst, A = _config1(n=n)
+    X0, _ = O.spectral_init(A, n, d)
+    X = X0
+    for _ in range(3):
+        a = O.nsrgs_iteration(A, X, n, d, 1.0 / n, 2)
+        b = O.stiefel_iteration(A, X, n, d, 1.0 / n, 2)
+        assert np.allclose(a, b, atol=1e-12)
+        X = a
+
+
+def test_stiefel_gradient_is_the_derivative_of_the_objective():
+    """Central differences of F (eq. (1) with d x p blocks) along random directions:
+    each X_i enters F through the pairs (i, j) and (j, i), so dF = sum_i <2 G_i, dX_i>
+    (G_i is the gradient of f_i = 1/2 sum_{j != i} ||X_i X_j^T - A_ij||^2, as in Algorithm 2)."""
+    rng = np.random.default_rng(4)
+    n, d, p = 7, 2, 4
+    inst = synth.make_instance(n, d, 0.7, seed=3)
+    A = inst.dense()
+    X = _row_orthonormal(rng, n, d, p).reshape(n * d, p)
+    G = O.stiefel_gradient(A, X, n, d).reshape(n * d, p)
+    for _ in range(3):
+        V = rng.standard_normal(X.shape)
+        h = 1e-6
+        fd = (O.objective(A, X + h * V, n, d) - O.objective(A, X - h * V, n, d)) / (2 * h)
+        assert abs(fd - 2.0 * np.sum(G * V)) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_stiefel_projection_lands_in_the_tangent_space():
+    rng = np.random.default_rng(5)
+    for d, p in [(2, 3), (3, 5), (4, 4)]:
+        Xi = _row_orthonormal(rng, 1, d, p)[0]
+        G = rng.standard_normal((d, p))
+        P = O.stiefel_projection(Xi, G)
+        assert np.allclose(P @ Xi.T + Xi @ P.T, 0.0, atol=1e-12)     # tangent
+        assert np.allclose(O.stiefel_projection(Xi, P), P, atol=1e-12)  # idempotent
+        H = rng.standard_normal((d, d))
+        N = (H + H.T) @ Xi  # a normal direction
+        assert np.allclose(O.stiefel_projection(Xi, N), 0.0, atol=1e-12)
+
+
+def test_row_newton_schulz_converges_to_the_polar_factor():
+    rng = np.random.default_rng(6)
+    for d, p in [(2, 3), (3, 7), (5, 5)]:
+        U, _, Vt = np.linalg.svd(rng.standard_normal((d, p)), full_matrices=False)
+        s = rng.uniform(0.3, 1.6, size=d)
+        M = U @ np.diag(s) @ Vt
+        assert np.allclose(O.newton_schulz_rows(M, 40), U @ Vt, atol=1e-12)
+        assert np.allclose(O.polar_rows(M), U @ Vt, atol=1e-12)
+
+
+def test_stiefel_fixed_point_at_sigma_zero():
+    """sigma = 0: X_i = [Z_i, 0] Q for any Q in O(p) is left unchanged."""
+    rng = np.random.default_rng(7)
+    n, d, p = 40, 3, 5
+    inst = synth.make_instance(n, d, 0.0, seed=8)
+    A = inst.dense()
+    Q = np.linalg.qr(rng.standard_normal((p, p)))[0]
+    Xb = np.concatenate([inst.Z, np.zeros((n, d, p - d))], axis=2) @ Q
+    X = Xb.reshape(n * d, p)
+    X1 = O.stiefel_iteration(A, X, n, d, 1.0 / n, 2)
+    assert np.allclose(X1, X, atol=1e-12)
