@@ -136,7 +136,8 @@ struct PanelGeom {
 // bytes loaded per row and step by one thread (LOADB).  A thread's d x d work is
 // RT rows x LOADB/E columns against d X columns; RT and LOADB keep its row
 // partials, X rows and column partials in registers (at most 168 with 10 warps
-// per CTA).  NW*8*RT must be a multiple of d so that slabs hold whole block rows.
+// per CTA, 146 with 14).  NW*8*RT (NW from panel_nw) must be a multiple of d so that slabs
+// hold whole block rows.
 __host__ __device__ constexpr int panel_rt(int d, int storage) {
   return d <= 2 ? 8 : d == 3 ? 6 : d == 4 ? 4 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 4;
 }
@@ -145,6 +146,14 @@ __host__ __device__ constexpr int panel_loadb(int d, int storage) {
          : d <= 4                 ? 16
          : d == 7                 ? (storage == NSRGS_F32 ? 8 : 4)
                                   : (storage == NSRGS_F32 ? 16 : 8);
+}
+
+// Consumer warps per CTA.  FP32 storage is bandwidth-bound with 8.  BF16 and FP8
+// storage at d <= 4 ask for 2d FMAs per element on a half or a quarter of the
+// bytes and are issue-bound; more consumer warps per scheduler hide more of the
+// per-step latency (shared-memory loads, shuffles, barrier waits).
+__host__ __device__ constexpr int panel_nw(int d, int storage) {
+  return (storage != NSRGS_F32 && d <= 4) ? 12 : 8;
 }
 
 // Rows of X/Y padding needed by a layout (columns of the last step run past n*D).

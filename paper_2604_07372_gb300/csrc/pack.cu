@@ -35,7 +35,7 @@ bool make_panel_geom(int n, int d, int storage, PanelGeom* g) {
   G.LOADB = panel_loadb(d, storage);
   G.CPT = G.LOADB / E;
   G.SC = 4 * G.CPT;
-  G.NW = 8;
+  G.NW = panel_nw(d, storage);
   G.RS = G.NW * 8 * G.RT;
   if (G.RS % d != 0) return false;
   G.SB = G.RS / d;

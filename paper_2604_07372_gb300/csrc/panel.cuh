@@ -5,7 +5,7 @@
 // Y_i += A_ij X_j and Y_j += A_ij^T X_i (Algorithm 2's gradient needs
 // sum_{j != i} A_ij X_j), so A is read once per iteration.
 //
-// Kernel structure (persistent, one CTA per SM, 10 warps):
+// Kernel structure (persistent, one CTA per SM, NW + 2 warps, NW from panel_nw):
 //  * warp NW (producer): lane 0 walks the CTA's contiguous range of steps and
 //    issues 1-D TMA bulk copies (cp.async.bulk) of each step's warp slices and
 //    of the X rows of the step's columns into a ring of shared-memory stages,
@@ -37,7 +37,7 @@ struct PCfg {
   static constexpr int LOADB = panel_loadb(D, ST);
   static constexpr int CPT = LOADB / E;
   static constexpr int SC = 4 * CPT;
-  static constexpr int NW = 8;
+  static constexpr int NW = panel_nw(D, ST);
   static constexpr int WROWS = 8 * RT;
   static constexpr int RS = NW * WROWS;
   static constexpr int SB = RS / D;

@@ -32,6 +32,11 @@ def loadb(d, storage):
     return 16 if storage == 0 else 8
 
 
+def nw(d, storage):
+    """Consumer warps per CTA: 12 for BF16/FP8 storage at d <= 4, else 8."""
+    return 12 if (storage != 0 and d <= 4) else 8
+
+
 class Geom:
     def __init__(self, n, d, storage):
         self.n, self.D, self.st = n, d, storage
@@ -40,7 +45,7 @@ class Geom:
         self.LOADB = loadb(d, storage)
         self.CPT = self.LOADB // self.E
         self.SC = 4 * self.CPT
-        self.NW = 8
+        self.NW = nw(d, storage)
         self.WROWS = 8 * self.RT
         self.RS = self.NW * self.WROWS
         assert self.RS % d == 0
