@@ -62,6 +62,7 @@ def parse_args():
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
     ap.add_argument("--sweep-storages", default="", help="comma-separated subset of the sweep's storages")
+    ap.add_argument("--sparse-ps", default="0.05,0.2,0.5", help="observation probabilities of the sparse leg")
     return ap.parse_args()
 
 
@@ -806,7 +807,7 @@ def main():
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
         elif args.leg == "sparse":
-            out = sparse_leg(P, synth, seed=args.seed + 4)
+            out = sparse_leg(P, synth, seed=args.seed + 4, ps=tuple(float(x) for x in args.sparse_ps.split(",")))
         else:
             out = serving_leg(P, synth, seed=args.seed + 2)
         print(json.dumps({args.leg: out}))

@@ -77,8 +77,11 @@ typedef enum {
  *            needed.  Bytes per A pass ~ 2 p (n^2 - n) d^2 E: below the symmetric
  *            panels whenever the observed fraction p < 1/2.  The exact size depends
  *            on the data: nsrgs_bcsr_packed_bytes; nsrgs_packed_bytes returns the
- *            bound for p = 1.  Single-instance calls only (not the batched or served
- *            forms). */
+ *            bound for p = 1.  Values are stored in groups of 32 consecutive blocks,
+ *            interleaved element by element (element e = r*d + c of block k at
+ *            32*d*d*(k/32) + 32*e + k%32, the last group zero-padded), so that a
+ *            warp taking 32 blocks reads each element with coalesced loads.  Used
+ *            by the single-instance, batched and served forms. */
 typedef enum {
   NSRGS_F32 = 0,
   NSRGS_BF16 = 1,

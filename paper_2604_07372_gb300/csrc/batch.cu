@@ -300,11 +300,13 @@ __global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
 // the last index with rbase <= r is the instance that owns row r).  Each
 // instance reads its own current X as in the panel source.
 template <int D, class T>
-__global__ void __launch_bounds__(256) bcsr_batch_kernel(const BatchDesc* descs, const long long* rbase, int cnt) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBcsrWarps * 32) bcsr_batch_kernel(const BatchDesc* descs, const long long* rbase,
+                                                                     int cnt) {
+  __shared__ float xs[kBcsrWarps][BcsrX<D>::kSmemFloats];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long total = rbase[cnt];
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < total; r += nwarps) {
+  const long long nwarps = (long long)gridDim.x * kBcsrWarps;
+  for (long long r = blockIdx.x * (long long)kBcsrWarps + w; r < total; r += nwarps) {
     const int inst = find_first_leq(rbase, cnt, r);
     const BatchDesc& d = descs[inst];
     const Ctl* c = d.ctl;
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(256) bcsr_batch_kernel(const BatchDesc* descs,
       X = d.X[c->iters_done & 1];
     else
       continue;
-    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane);
+    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane, xs[w]);
   }
 }
 
@@ -324,12 +326,13 @@ cudaError_t batch_bcsr_stream(const BatchDesc* descs, const long long* rbase, in
                               long long total_rows, cudaStream_t st) {
   // grid sized for the largest row total the table can hold; rows past the
   // current total return at once
-  const long long g = std::max<long long>(1, std::min<long long>((total_rows + 7) / 8, 4LL * num_sms()));
-#define L(DD)                                                                                          \
-  if (elem_bf16)                                                                                       \
-    bcsr_batch_kernel<DD, __nv_bfloat16><<<(unsigned)g, 256, 0, st>>>(descs, rbase, count);           \
-  else                                                                                                 \
-    bcsr_batch_kernel<DD, float><<<(unsigned)g, 256, 0, st>>>(descs, rbase, count);
+  const long long g = std::max<long long>(
+      1, std::min<long long>((total_rows + kBcsrWarps - 1) / kBcsrWarps, 32LL / kBcsrWarps * num_sms()));
+#define L(DD)                                                                                             \
+  if (elem_bf16)                                                                                          \
+    bcsr_batch_kernel<DD, __nv_bfloat16><<<(unsigned)g, kBcsrWarps * 32, 0, st>>>(descs, rbase, count); \
+  else                                                                                                    \
+    bcsr_batch_kernel<DD, float><<<(unsigned)g, kBcsrWarps * 32, 0, st>>>(descs, rbase, count);
   switch (d) {
     case 1: L(1); break;
     case 2: L(2); break;

@@ -11,7 +11,10 @@
 //   [0, 64)          header: int64 n, d, nnzb (number of stored blocks), off_col, off_val
 //   [64, ...)        int64 rowptr[n + 1]
 //   off_col          int32 col[nnzb], blocks of a row in increasing j
-//   off_val          values, nnzb blocks of d x d row-major (float32 or bfloat16)
+//   off_val          values (float32 or bfloat16) of the nnzb d x d blocks, in
+//                    groups of 32 consecutive blocks; within a group element
+//                    e = r*d + c of block k sits at e*32 + (k mod 32)
+//                    (bcsr_val_pos); the last group is zero-padded to 32 blocks
 // A block counts as observed when any of its d*d entries is nonzero.
 // Packing reads the strict upper triangle (the canonical list or a dense matrix)
 // twice, once to count each row's blocks and once to write them, in column
@@ -56,8 +59,10 @@ __global__ void __launch_bounds__(256) bcsr_count_kernel(Src src, int n, int d, 
 }
 
 // One CTA: rowptr (at packed + 64) = exclusive scan of deg, written in place over
-// deg's copy; header fields filled from the total; the alignment gaps and the
-// tail are zeroed so that a packed buffer is a function of the data alone.
+// deg's copy; header fields filled from the total; the alignment gaps, the
+// padding of the last value group and the tail are zeroed (the fill kernel
+// then writes the stored blocks), so that a packed buffer is a function of the
+// data alone.
 __global__ void __launch_bounds__(1024) bcsr_scan_kernel(uint8_t* packed, int n, int d, int storage) {
   long long* rowptr = reinterpret_cast<long long*>(packed + kBcsrHeader);  // holds deg on entry
   __shared__ long long part[1024];
@@ -82,19 +87,23 @@ __global__ void __launch_bounds__(1024) bcsr_scan_kernel(uint8_t* packed, int n,
     hdr[3] = bcsr_off_col(n);
     hdr[4] = bcsr_off_val(n, run);
     for (int k = 5; k < kBcsrHeader / 8; ++k) hdr[k] = 0;
-    rowptr[n] = run;
-    for (long long b = kBcsrHeader + 8LL * (n + 1); b < hdr[3]; ++b) packed[b] = 0;
-    for (long long b = hdr[3] + 4 * run; b < hdr[4]; ++b) packed[b] = 0;
-    for (long long b = hdr[4] + run * d * d * bcsr_elem_bytes(storage); b < bcsr_bytes_of(n, d, storage, run); ++b)
-      packed[b] = 0;
   }
   __syncthreads();
+  const long long* hdr = reinterpret_cast<const long long*>(packed);
+  const long long nnzb = hdr[2];
   long long run = part[t];
   for (long long i = lo; i < hi; ++i) {
     const long long v = rowptr[i];
     rowptr[i] = run;
     run += v;
   }
+  if (t == 0) rowptr[n] = nnzb;
+  const long long gaps[3][2] = {
+      {kBcsrHeader + 8LL * (n + 1), hdr[3]},
+      {hdr[3] + 4 * nnzb, hdr[4]},
+      {hdr[4] + (nnzb / 32) * 32 * d * d * bcsr_elem_bytes(storage), bcsr_bytes_of(n, d, storage, nnzb)}};
+  for (int g = 0; g < 3; ++g)
+    for (long long b = gaps[g][0] + t; b < gaps[g][1]; b += blockDim.x) packed[b] = 0;
 }
 
 __device__ __forceinline__ void bcsr_store(float* p, float v) { *p = v; }
@@ -118,13 +127,12 @@ __global__ void __launch_bounds__(256) bcsr_fill_kernel(Src src, int n, int d, u
       if (nz) {
         const long long k = pos + __popc(m & ((1u << lane) - 1u));
         col[k] = j;
-        T* blk = val + k * d * d;
         for (int r = 0; r < d; ++r)
           for (int c = 0; c < d; ++c) {
             // A_ij for j > i from the upper triangle; A_ij = (A_ji)^T for j < i
             const float v = j > i ? src(i * (long long)d + r, (long long)j * d + c)
                                   : src((long long)j * d + c, i * (long long)d + r);
-            bcsr_store(blk + r * d + c, v);
+            bcsr_store(val + bcsr_val_pos(k, r * d + c, d * d), v);
           }
       }
       pos += __popc(m);
@@ -133,16 +141,17 @@ __global__ void __launch_bounds__(256) bcsr_fill_kernel(Src src, int n, int d, u
 }
 
 // ------------------------------------------------------------------ stream
-// Warp per block row (bcsr_row_product).
+// Warp per block row (bcsr_row_product), kBcsrWarps warps per CTA.
 template <int D, class T>
-__global__ void __launch_bounds__(256) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
-                                                           const float* __restrict__ X, float* __restrict__ Y,
-                                                           const int* skip) {
+__global__ void __launch_bounds__(kBcsrWarps * 32) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
+                                                                      const float* __restrict__ X,
+                                                                      float* __restrict__ Y, const int* skip) {
+  __shared__ float xs[kBcsrWarps][BcsrX<D>::kSmemFloats];
   if (*skip) return;
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps)
-    bcsr_row_product<D, T>(packed, i, X, Y, lane);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nwarps = (long long)gridDim.x * kBcsrWarps;
+  for (long long i = blockIdx.x * (long long)kBcsrWarps + w; i < n; i += nwarps)
+    bcsr_row_product<D, T>(packed, i, X, Y, lane, xs[w]);
 }
 
 // ---------------------------------------------------------------- host
@@ -151,6 +160,10 @@ bool bcsr_storage(int storage) { return storage == NSRGS_BCSR_F32 || storage == 
 static int bcsr_grid(int n) {
   const long long g = ((long long)n + 7) / 8;  // 8 warps per CTA, one row each per sweep
   return (int)std::min<long long>(std::max<long long>(g, 1), 4LL * num_sms());
+}
+static int bcsr_stream_grid(int n) {
+  const long long g = ((long long)n + kBcsrWarps - 1) / kBcsrWarps;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 32LL / kBcsrWarps * num_sms());
 }
 
 template <class Src>
@@ -194,9 +207,9 @@ static cudaError_t bcsr_stream_d(const void* packed, int n, int storage, const f
                                  cudaStream_t st) {
   const uint8_t* p = reinterpret_cast<const uint8_t*>(packed);
   if (storage == NSRGS_BCSR_BF16)
-    bcsr_stream_kernel<D, __nv_bfloat16><<<bcsr_grid(n), 256, 0, st>>>(p, n, X, Y, skip);
+    bcsr_stream_kernel<D, __nv_bfloat16><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip);
   else
-    bcsr_stream_kernel<D, float><<<bcsr_grid(n), 256, 0, st>>>(p, n, X, Y, skip);
+    bcsr_stream_kernel<D, float><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip);
   return cudaGetLastError();
 }
 

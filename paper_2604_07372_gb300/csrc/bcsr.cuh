@@ -8,6 +8,7 @@
 namespace nsrgs {
 
 constexpr int kBcsrHeader = 64;
+constexpr int kBcsrWarps = 4;  // warps per CTA of the row kernels
 
 __host__ __device__ inline long long bcsr_align(long long x) { return (x + 15) / 16 * 16; }
 __host__ __device__ inline int bcsr_elem_bytes(int storage) { return storage == NSRGS_BCSR_BF16 ? 2 : 4; }
@@ -15,8 +16,16 @@ __host__ __device__ inline long long bcsr_off_col(int n) { return bcsr_align(kBc
 __host__ __device__ inline long long bcsr_off_val(int n, long long nnzb) {
   return bcsr_align(bcsr_off_col(n) + 4LL * nnzb);
 }
+// Blocks are stored in groups of 32 (the last group padded with zeros).
+__host__ __device__ inline long long bcsr_val_slots(long long nnzb) { return (nnzb + 31) / 32 * 32; }
+// Element e (= r*d + c) of stored block k: the 32 blocks of a group are
+// interleaved element by element, so the 32 lanes of a warp that take blocks
+// k0 .. k0+31 read element e of all of them from one or two 128-byte lines.
+__host__ __device__ inline long long bcsr_val_pos(long long k, int e, int dd) {
+  return (k >> 5) * 32LL * dd + (long long)e * 32 + (k & 31);
+}
 __host__ __device__ inline long long bcsr_bytes_of(int n, int d, int storage, long long nnzb) {
-  const long long b = bcsr_off_val(n, nnzb) + nnzb * d * d * bcsr_elem_bytes(storage);
+  const long long b = bcsr_off_val(n, nnzb) + bcsr_val_slots(nnzb) * d * d * bcsr_elem_bytes(storage);
   return (b + 255) / 256 * 256;
 }
 long long bcsr_bytes(int n, int d, int storage, long long nnzb);
@@ -26,15 +35,31 @@ __device__ __forceinline__ float bcsr_load(const __nv_bfloat16* p) {
   return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
 }
 
-// One warp: Y_i = sum_j A_ij X_j for block row i of the packed buffer.  Lanes
-// take the row's blocks in turn (U per pass, their column and value loads
-// issued together so the dependent X_j gathers overlap), accumulate d x d
-// partials in registers one X_j row at a time, then a warp reduction; Y_i is
-// written, not accumulated.  (A mapping with d*d lanes per block, which reads
-// each X_j once per block instead of once per element, measured slower.)
+// X_j (d x d, row-major at j*d*d) is 16-byte aligned for even d and is then
+// read with 128-bit loads; for odd d >= 3 the warp gathers the 32 X_j of a pass
+// together through shared memory (element f of the pass's 32*d*d values by lane
+// f mod 32), so that one load instruction touches a few lines instead of 32.
+template <int D>
+struct BcsrX {
+  static constexpr int DD = D * D;
+  static constexpr bool kCoop = (D % 2 == 1) && D >= 3;
+  // passes of 32 blocks per loop trip (their loads are in flight together)
+  static constexpr int kU = D <= 2 ? 4 : (D <= 4 ? 2 : 1);
+  static constexpr int kSmemFloats = kCoop ? kU * 32 * DD : 1;  // per warp
+};
+
+// One warp: Y_i = sum_j A_ij X_j for block row i of the packed buffer.  Lane l
+// takes blocks rowptr[i] + l, + 32 + l, ...; per loop trip it loads the column
+// indices and d*d values of kU such blocks (coalesced by the interleaved
+// layout), gathers their X_j, and accumulates the d x d partial in registers; a
+// warp reduction ends the row, and Y_i is written, not accumulated.  xs: this
+// warp's shared-memory buffer of BcsrX<D>::kSmemFloats floats (odd d >= 3).
 template <int D, class T>
 __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ packed, long long i,
-                                                 const float* __restrict__ X, float* __restrict__ Y, int lane) {
+                                                 const float* __restrict__ X, float* __restrict__ Y, int lane,
+                                                 float* xs) {
+  constexpr int DD = D * D;
+  constexpr int U = BcsrX<D>::kU;
   const long long* hdr = reinterpret_cast<const long long*>(packed);
   const long long* rowptr = reinterpret_cast<const long long*>(packed + kBcsrHeader);
   const int* col = reinterpret_cast<const int*>(packed + hdr[3]);
@@ -44,29 +69,55 @@ __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ pac
   for (int r = 0; r < D; ++r)
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[r][c] = 0.f;
-  constexpr int U = D <= 4 ? 4 : (D <= 6 ? 2 : 1);
   const long long k1 = rowptr[i + 1];
-  for (long long k = rowptr[i] + lane; k < k1; k += 32 * U) {
+  for (long long kb = rowptr[i]; kb < k1; kb += 32 * U) {
     int j[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) j[u] = (k + 32 * u < k1) ? __ldg(col + k + 32 * u) : -1;
+    float a[U][DD];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j[u] < 0) continue;
-      const T* a = val + (k + 32 * u) * D * D;
-      const float* x = X + (long long)j[u] * D * D;
+      const long long k = kb + 32 * u + lane;
+      const bool valid = k < k1;
+      // a lane past the row's end uses X_0 with zero values
+      j[u] = valid ? __ldg(col + k) : 0;
+      const T* vk = val + bcsr_val_pos(k, 0, DD);
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
-        float xr[D], am[D];
+      for (int e = 0; e < DD; ++e) a[u][e] = valid ? bcsr_load(vk + e * 32) : 0.f;
+    }
+    if constexpr (BcsrX<D>::kCoop) {
+      __syncwarp();  // the previous trip has read xs
 #pragma unroll
-        for (int c = 0; c < D; ++c) xr[c] = __ldg(x + m * D + c);
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int r = 0; r < D; ++r) am[r] = bcsr_load(a + r * D + m);
+        for (int q = 0; q < DD; ++q) {
+          const int f = q * 32 + lane;
+          const int b = f / DD, m = f - b * DD;
+          const int jb = __shfl_sync(0xffffffffu, j[u], b);
+          xs[u * 32 * DD + f] = __ldg(X + (long long)jb * DD + m);
+        }
+      __syncwarp();
+    }
 #pragma unroll
-        for (int r = 0; r < D; ++r)
+    for (int u = 0; u < U; ++u) {
+      float x[DD];
+      if constexpr (BcsrX<D>::kCoop) {
 #pragma unroll
-          for (int c = 0; c < D; ++c) acc[r][c] = fmaf(am[r], xr[c], acc[r][c]);
+        for (int m = 0; m < DD; ++m) x[m] = xs[u * 32 * DD + lane * DD + m];
+      } else if constexpr (DD % 4 == 0) {
+        const float4* xp = reinterpret_cast<const float4*>(X + (long long)j[u] * DD);
+#pragma unroll
+        for (int q = 0; q < DD / 4; ++q) {
+          const float4 t = __ldg(xp + q);
+          x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
+      } else {
+        x[0] = __ldg(X + j[u]);  // d = 1
       }
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int m = 0; m < D; ++m)
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[r][c] = fmaf(a[u][r * D + m], x[m * D + c], acc[r][c]);
     }
   }
 #pragma unroll
@@ -78,8 +129,8 @@ __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ pac
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       acc[r][c] = v;
     }
-  float* y = Y + i * D * D;
-  for (int e = lane; e < D * D; e += 32) {
+  float* y = Y + i * DD;
+  for (int e = lane; e < DD; e += 32) {
     float v = 0.f;
 #pragma unroll
     for (int r = 0; r < D; ++r)

@@ -22,6 +22,7 @@
 // the stop decision is reproducible run to run.
 #include <math.h>
 
+#include "bcsr.cuh"
 #include "blockops.cuh"
 
 namespace nsrgs {
@@ -188,13 +189,14 @@ __global__ void __launch_bounds__(256) norm2_flat_kernel(const T* __restrict__ a
 }
 
 // Block-sparse rows (both triangles stored, each block once per direction):
-// the stored values once; their count is in the packed header.
+// the stored values once.  The value array holds whole groups of 32 blocks; the
+// padding of the last group is zero, so the sum runs over all its slots.
 template <class T>
 __global__ void __launch_bounds__(256) norm2_bcsr_kernel(const uint8_t* __restrict__ packed, int D, ObjScratch o,
                                                          Ctl* ctl) {
   __shared__ double sh[32];
   const long long* hdr = reinterpret_cast<const long long*>(packed);
-  const long long count = hdr[2] * D * D;
+  const long long count = bcsr_val_slots(hdr[2]) * D * D;
   const T* a = reinterpret_cast<const T*>(packed + hdr[4]);
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;

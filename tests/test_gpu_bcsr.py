@@ -49,7 +49,8 @@ def test_bcsr_product_matches_dense_matmul(P, n, d, p, storage):
     nnzb = 2 * observed_blocks(inst)
     E = 4 if storage == "bcsr_f32" else 2
     nb = P.nsrgs_bcsr_packed_bytes(up, n, d, st)
-    assert nb >= nnzb * d * d * E and nb <= nnzb * (d * d * E + 4) + 8 * (n + 1) + 64 + 3 * 256
+    # values in groups of 32 blocks, the last group zero-padded
+    assert nb >= nnzb * d * d * E and nb <= nnzb * (d * d * E + 4) + 31 * d * d * E + 8 * (n + 1) + 64 + 3 * 256
     pa = P.nsrgs_pack_upper(up, n, d, st)
     X = np.random.default_rng(n).standard_normal((n * d, d)).astype(np.float32)
     Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
@@ -59,6 +60,48 @@ def test_bcsr_product_matches_dense_matmul(P, n, d, p, storage):
     ref = A @ X.astype(np.float64)
     scale = np.abs(A) @ np.abs(X.astype(np.float64))
     assert np.all(np.abs(to64(Y) - ref) <= 1e-6 * scale + 1e-6)
+
+
+@pytest.mark.parametrize("n,d,p,storage", [(70, 3, 0.3, "bcsr_f32"), (45, 2, 0.6, "bcsr_bf16"), (33, 5, 0.5, "bcsr_f32")])
+def test_bcsr_buffer_follows_the_documented_layout(P, n, d, p, storage):
+    """Header, int64 row pointers, int32 columns in increasing j, values in groups of
+    32 blocks interleaved element by element (element e of block k at
+    32*d*d*(k//32) + 32*e + k%32), zero padding after the last stored block."""
+    inst = synth.make_instance(n, d, 1.0, seed=n * d, p=p, dtype=np.float32)
+    A = inst.dense()
+    st = P.STORAGE[storage]
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, st)
+    torch.cuda.synchronize()
+    buf = pa.buf.cpu().numpy()
+    hdr = buf[:64].view(np.int64)
+    nnzb, off_col, off_val = int(hdr[2]), int(hdr[3]), int(hdr[4])
+    assert (hdr[0], hdr[1]) == (n, d) and off_col % 16 == 0 and off_val % 16 == 0
+    rowptr = buf[64 : 64 + 8 * (n + 1)].view(np.int64)
+    col = buf[off_col : off_col + 4 * nnzb].view(np.int32)
+    dt = np.float32 if storage == "bcsr_f32" else np.uint16
+    E = 4 if storage == "bcsr_f32" else 2
+    slots = (nnzb + 31) // 32 * 32
+    raw = buf[off_val : off_val + slots * d * d * E].view(dt)
+    vals = raw.astype(np.float32) if E == 4 else (raw.astype(np.uint32) << 16).view(np.float32)
+    expect_cols = []
+    for i in range(n):
+        for j in range(n):
+            blk = A[i * d : (i + 1) * d, j * d : (j + 1) * d]
+            if j != i and np.any(blk != 0):
+                expect_cols.append((i, j))
+    assert nnzb == len(expect_cols) and rowptr[0] == 0 and rowptr[n] == nnzb
+    for k, (i, j) in enumerate(expect_cols):
+        assert rowptr[i] <= k < rowptr[i + 1] and col[k] == j
+        pos = 32 * d * d * (k // 32) + 32 * np.arange(d * d) + k % 32
+        ref = A[i * d : (i + 1) * d, j * d : (j + 1) * d].reshape(-1)
+        if E == 2:
+            ref = torch.from_numpy(ref.copy()).to(torch.bfloat16).float().numpy()
+        assert np.array_equal(vals[pos], ref)
+    used = np.zeros(slots * d * d, dtype=bool)
+    for k in range(nnzb):
+        used[32 * d * d * (k // 32) + 32 * np.arange(d * d) + k % 32] = True
+    assert np.all(vals[~used] == 0.0)
+    assert np.all(buf[off_val + slots * d * d * E :] == 0)
 
 
 def test_bcsr_from_dense_equals_from_upper(P):
