@@ -31,6 +31,7 @@ import statistics
 import subprocess
 import sys
 import time
+import traceback
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -228,8 +229,10 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
     for st, name in ((P.BF16, "bf16"), (P.FP8E4M3, "fp8"), (P.F32, "f32")):
         ws = torch.empty(P.nsrgs_batch_workspace_bytes(ns, d), dtype=torch.uint8, device="cuda")
         Xs = [torch.empty(n * d, d, device="cuda") for n in ns]
-        P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=False)
+        # untimed warm-up with per-instance reports (raises on a device-side error flag)
+        _, infos = P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=True)
         torch.cuda.synchronize()
+        iters_ok = sum(1 for i in infos if i.iters == T)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
@@ -239,7 +242,8 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
         sec = e0.elapsed_time(e1) / 1e3 / reps
         bytes_A = sum(p.nbytes for p in packs[st])
         dF[name] = np.array([P.nsrgs_dF(X, Z, n, d, ws=None) for X, Z, n in zip(Xs, Zs, ns)])
-        out[name] = {"solves_per_s": count / sec, "batch_ms": 1e3 * sec, "packed_GB": bytes_A / 1e9}
+        out[name] = {"solves_per_s": count / sec, "batch_ms": 1e3 * sec, "packed_GB": bytes_A / 1e9,
+                     "instances_with_T_iterations": iters_ok}
         del ws
     for name in ("bf16", "fp8"):
         rel = np.abs(dF[name] - dF["f32"]) / dF["f32"]
@@ -429,7 +433,7 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
                 if q["p"] < 1.0 and "bcsr_bytes" not in q:
                     q["bcsr_bytes"] = P.nsrgs_bcsr_packed_bytes(q["upper"], q["n"], q["d"], P.BCSR_BF16)
                     q["use_bcsr"] = q["bcsr_bytes"] * 3 < P.nsrgs_packed_bytes(q["n"], q["d"], P.BF16)
-        lat, iters, meta = [], [], {}
+        lat, iters, meta, errors = [], [], {}, {}
         nxt = done = 0
         start = time.perf_counter()
         last_finish = 0.0
@@ -449,6 +453,8 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
                 a, qd = srv.step()
                 busy = busy or a > 0 or qd > 0
                 for r in srv.poll():
+                    if r.status != 0:
+                        errors[r.status] = errors.get(r.status, 0) + 1
                     ta, X = meta.pop((d, r.id))
                     fin = time.perf_counter() - start
                     lat.append(fin - ta)
@@ -468,6 +474,7 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
             "p99_ms": float(1e3 * np.percentile(lat, 99)),
             "mean_iters": float(np.mean(iters)),
             "max_iters": int(np.max(iters)),
+            "non_ok_results": {str(k): v for k, v in errors.items()},
         }
 
     res = {
@@ -754,6 +761,8 @@ def run_ours(args, world, rank, local):
             extras["plain_dense_f32"] = {"error": str(e)[:200]}
         line["extras"] = extras
         packs.clear()
+        # the legs below time whole calls; per-launch events would only add work
+        P.nsrgs_set_kernel_timing(False)
         torch.cuda.empty_cache()
         # batched and served forms (the metric's second half)
         for key, fn in (("batched", batched_leg), ("serving", serving_leg), ("dimension_sweep", dsweep_leg)):
@@ -762,6 +771,7 @@ def run_ours(args, world, rank, local):
                 line[key] = fn(P, synth, seed=args.seed + {"batched": 1, "serving": 2, "dimension_sweep": 3}[key])
                 line[key]["leg_wall_s"] = time.perf_counter() - t
             except Exception as e:  # reported in the line, the main metric stands
+                traceback.print_exc()
                 line[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
             torch.cuda.empty_cache()
         # CPU oracle on the host cores, bounded sample

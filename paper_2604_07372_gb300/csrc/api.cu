@@ -58,7 +58,7 @@ int tc_dense_splits(int n, int d);
 bool bcsr_storage(int storage);
 long long bcsr_bytes(int n, int d, int storage, long long nnzb);
 cudaError_t bcsr_stream(const void* packed, int n, int d, int storage, const float* X, float* Y, const int* skip,
-                        cudaStream_t st);
+                        Ctl* ctl, cudaStream_t st);
 cudaError_t bcsr_count_upper(const float* upper, int n, int d, unsigned long long* d_total, cudaStream_t st);
 cudaError_t bcsr_count_dense(const float* A, int n, int d, unsigned long long* d_total, cudaStream_t st);
 bool tc_sym_supported(int d);
@@ -196,7 +196,7 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
   if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d))
     return tc_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl, skip, st);
-  if (bcsr_storage(A->storage)) return bcsr_stream(A->packed, A->n, A->d, A->storage, X, w.Y, skip, st);
+  if (bcsr_storage(A->storage)) return bcsr_stream(A->packed, A->n, A->d, A->storage, X, w.Y, skip, w.ctl, st);
   return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
 }
 
@@ -431,6 +431,10 @@ nsrgs_status nsrgs_spectral_init(const nsrgs_A* A, float* X0, int max_iters, dou
   NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
   if (residual) *residual = c.spec_res;
+  if (c.flags & FLAG_BAD_LAYOUT) {
+    set_error("the packed A is inconsistent: an index or address left its buffer (access skipped)");
+    return NSRGS_ERR_INVALID_ARG;
+  }
   if (c.flags & FLAG_TIMEOUT) {
     set_error("a device-side wait timed out");
     return NSRGS_ERR_TIMEOUT;
@@ -536,6 +540,10 @@ nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* 
   NSRGS_CUDA_TRY(cudaMemcpyAsync(oscal, w.obj.scal, sizeof(oscal), cudaMemcpyDeviceToHost, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (c.flags & FLAG_BAD_LAYOUT) {
+    set_error("the packed A is inconsistent: an index or address left its buffer (access skipped)");
+    return NSRGS_ERR_INVALID_ARG;
+  }
   if (c.flags & FLAG_TIMEOUT) {
     set_error("a device-side wait timed out");
     return NSRGS_ERR_TIMEOUT;
@@ -660,6 +668,10 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     info->spectral_residual = c.spec_res;
     info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
                   ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
+    if (c.flags & FLAG_BAD_LAYOUT) {
+      set_error("the packed A is inconsistent: an index or address left its buffer (access skipped)");
+      return NSRGS_ERR_INVALID_ARG;
+    }
     if (c.flags & FLAG_TIMEOUT) {
       set_error("a device-side wait timed out");
       return NSRGS_ERR_TIMEOUT;

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kBcsrWarps * 32) bcsr_batch_kernel(const Batch
       X = d.X[c->iters_done & 1];
     else
       continue;
-    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane, xs[w]);
+    bcsr_row_product<D, T>(d.packed, r - rbase[inst], X, d.Y, lane, xs[w], d.ctl);
   }
 }
 
@@ -609,7 +609,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     std::vector<BatchReport> rep(count);
     NSRGS_CUDA_TRY(cudaMemcpyAsync(rep.data(), d_rep, sizeof(BatchReport) * count, cudaMemcpyDeviceToHost, st));
     NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
-    bool timeout = false, nonfinite = false;
+    bool timeout = false, nonfinite = false, bad = false;
     for (int i = 0; i < count; ++i) {
       info[i].spectral_iters = rep[i].spec_iters;
       info[i].iters = rep[i].iters;
@@ -620,7 +620,12 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
       info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
                       ((init && rep[i].spec_res > 1e-6) ? FLAG_SPEC_NOT_CONVERGED : 0u);
       timeout = timeout || (rep[i].flags & FLAG_TIMEOUT);
+      bad = bad || (rep[i].flags & FLAG_BAD_LAYOUT);
       nonfinite = nonfinite || (rep[i].flags & FLAG_NONFINITE);
+    }
+    if (bad) {
+      set_error("a packed A in the batch is inconsistent: an index or address left its buffer (access skipped)");
+      return NSRGS_ERR_INVALID_ARG;
     }
     if (timeout) {
       set_error("a device-side wait timed out");

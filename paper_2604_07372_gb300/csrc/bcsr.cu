@@ -145,13 +145,14 @@ __global__ void __launch_bounds__(256) bcsr_fill_kernel(Src src, int n, int d, u
 template <int D, class T>
 __global__ void __launch_bounds__(kBcsrWarps * 32) bcsr_stream_kernel(const uint8_t* __restrict__ packed, int n,
                                                                       const float* __restrict__ X,
-                                                                      float* __restrict__ Y, const int* skip) {
+                                                                      float* __restrict__ Y, const int* skip,
+                                                                      Ctl* ctl) {
   __shared__ float xs[kBcsrWarps][BcsrX<D>::kSmemFloats];
   if (*skip) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * kBcsrWarps;
   for (long long i = blockIdx.x * (long long)kBcsrWarps + w; i < n; i += nwarps)
-    bcsr_row_product<D, T>(packed, i, X, Y, lane, xs[w]);
+    bcsr_row_product<D, T>(packed, i, X, Y, lane, xs[w], ctl);
 }
 
 // ---------------------------------------------------------------- host
@@ -204,26 +205,26 @@ cudaError_t bcsr_count_dense(const float* A, int n, int d, unsigned long long* d
 
 template <int D>
 static cudaError_t bcsr_stream_d(const void* packed, int n, int storage, const float* X, float* Y, const int* skip,
-                                 cudaStream_t st) {
+                                 Ctl* ctl, cudaStream_t st) {
   const uint8_t* p = reinterpret_cast<const uint8_t*>(packed);
   if (storage == NSRGS_BCSR_BF16)
-    bcsr_stream_kernel<D, __nv_bfloat16><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip);
+    bcsr_stream_kernel<D, __nv_bfloat16><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip, ctl);
   else
-    bcsr_stream_kernel<D, float><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip);
+    bcsr_stream_kernel<D, float><<<bcsr_stream_grid(n), kBcsrWarps * 32, 0, st>>>(p, n, X, Y, skip, ctl);
   return cudaGetLastError();
 }
 
 cudaError_t bcsr_stream(const void* packed, int n, int d, int storage, const float* X, float* Y, const int* skip,
-                        cudaStream_t st) {
+                        Ctl* ctl, cudaStream_t st) {
   switch (d) {
-    case 1: return bcsr_stream_d<1>(packed, n, storage, X, Y, skip, st);
-    case 2: return bcsr_stream_d<2>(packed, n, storage, X, Y, skip, st);
-    case 3: return bcsr_stream_d<3>(packed, n, storage, X, Y, skip, st);
-    case 4: return bcsr_stream_d<4>(packed, n, storage, X, Y, skip, st);
-    case 5: return bcsr_stream_d<5>(packed, n, storage, X, Y, skip, st);
-    case 6: return bcsr_stream_d<6>(packed, n, storage, X, Y, skip, st);
-    case 7: return bcsr_stream_d<7>(packed, n, storage, X, Y, skip, st);
-    case 8: return bcsr_stream_d<8>(packed, n, storage, X, Y, skip, st);
+    case 1: return bcsr_stream_d<1>(packed, n, storage, X, Y, skip, ctl, st);
+    case 2: return bcsr_stream_d<2>(packed, n, storage, X, Y, skip, ctl, st);
+    case 3: return bcsr_stream_d<3>(packed, n, storage, X, Y, skip, ctl, st);
+    case 4: return bcsr_stream_d<4>(packed, n, storage, X, Y, skip, ctl, st);
+    case 5: return bcsr_stream_d<5>(packed, n, storage, X, Y, skip, ctl, st);
+    case 6: return bcsr_stream_d<6>(packed, n, storage, X, Y, skip, ctl, st);
+    case 7: return bcsr_stream_d<7>(packed, n, storage, X, Y, skip, ctl, st);
+    case 8: return bcsr_stream_d<8>(packed, n, storage, X, Y, skip, ctl, st);
   }
   return cudaErrorInvalidValue;
 }

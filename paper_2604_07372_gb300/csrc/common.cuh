@@ -66,6 +66,7 @@ enum : unsigned int {
   FLAG_SPEC_NOT_CONVERGED = 1u << 2,
   FLAG_TIMEOUT = 1u << 3,
   FLAG_NS_SAFEGUARDED = 1u << 4,  // the safeguarded Newton-Schulz start was used for some block
+  FLAG_BAD_LAYOUT = 1u << 5,      // a packed buffer's index or address left its buffer (access skipped)
 };
 
 // float64 scratch of the spectral initialisation and of d_F (all d x d unless noted).

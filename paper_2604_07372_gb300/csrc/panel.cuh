@@ -298,10 +298,20 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           return false;
         }
         const uint32_t bytesA = (uint32_t)wk.W * C::WB;
+        const uint8_t* srcA = panels + off;
+        const float* srcX = v.X + (long long)wk.xcol() * D;
+        // a copy that would leave the panels or start off a 16-byte boundary is
+        // refused and flagged (the consumers then time out and return)
+        if (off + bytesA > v.g.panel_bytes ||
+            ((reinterpret_cast<uintptr_t>(srcA) | reinterpret_cast<uintptr_t>(srcX)) & 15u)) {
+          atomicOr(&v.ctl->flags, FLAG_BAD_LAYOUT);
+          ok = false;
+          return false;
+        }
         uint8_t* stage = smem + st * C::STAGE_BYTES;
         mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
-        bulk_g2s(stage, panels + off, bytesA, &full[st]);
-        bulk_g2s(stage + C::STAGE_A, v.X + (long long)wk.xcol() * D, C::STAGE_X, &full[st]);
+        bulk_g2s(stage, srcA, bytesA, &full[st]);
+        bulk_g2s(stage + C::STAGE_A, srcX, C::STAGE_X, &full[st]);
         off += bytesA;
         if (wk.advance() && wk.b < wk.nslabs) off = byte_off[wk.b];
         ++issued;
@@ -326,6 +336,9 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     uint32_t ph = 0;
     for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
       if (v.skip) return true;
+      // the column offsets of a step keep 16-byte alignment; Y's base must too
+      const bool ybad = (reinterpret_cast<uintptr_t>(v.Y) & 15u) != 0;
+      if (ybad && lane == 0) atomicOr(&v.ctl->flags, FLAG_BAD_LAYOUT);
       Walk<C, D> wk;
       wk.start(v, lo);
       for (long long s = lo; s < hi; ++s) {
@@ -343,7 +356,7 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
               sum.x += x.x; sum.y += x.y; sum.z += x.z; sum.w += x.w;
             }
           }
-          red_add_v4_f32(v.Y + (long long)wk.xcol() * D + 4 * lane, sum.x, sum.y, sum.z, sum.w);
+          if (!ybad) red_add_v4_f32(v.Y + (long long)wk.xcol() * D + 4 * lane, sum.x, sum.y, sum.z, sum.w);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&cempty[slot]);

@@ -339,7 +339,8 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
       const BatchReport& r = s->h_rep[i];
       nsrgs_server_result res;
       res.id = sl.id;
-      res.status = (r.flags & FLAG_TIMEOUT) ? NSRGS_ERR_TIMEOUT
+      res.status = (r.flags & FLAG_BAD_LAYOUT) ? NSRGS_ERR_INVALID_ARG
+                   : (r.flags & FLAG_TIMEOUT)  ? NSRGS_ERR_TIMEOUT
                    : (r.flags & FLAG_NONFINITE) ? NSRGS_ERR_NONFINITE
                                                 : NSRGS_OK;
       res.iters = r.iters;

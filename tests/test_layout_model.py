@@ -100,6 +100,7 @@ def slot_coords(g, b, q, W):
 
 
 CASES = [(2, 1, 0), (2, 3, 0), (5, 2, 1), (130, 3, 0), (131, 3, 1), (200, 3, 2), (257, 4, 0), (300, 1, 2), (513, 2, 0), (140, 4, 2),
+         (257, 4, 1), (97, 4, 1), (300, 1, 1), (1100, 3, 1), (900, 4, 2), (1300, 2, 1),
          (3, 5, 0), (70, 5, 1), (67, 6, 0), (66, 7, 1), (130, 8, 0), (65, 8, 1)]
 
 
