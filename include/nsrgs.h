@@ -42,7 +42,9 @@ extern "C" {
 
 typedef enum {
   NSRGS_OK = 0,
-  NSRGS_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of contract */
+  NSRGS_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of contract, or a packed
+                                  buffer is inconsistent (an index or address found on the
+                                  device to leave its buffer; the access is skipped) */
   NSRGS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
   NSRGS_ERR_NOMEM = 3,         /* a caller buffer is smaller than the size query returned */
   NSRGS_ERR_NONFINITE = 4,     /* an iterate became NaN or Inf */

@@ -54,9 +54,9 @@ struct BcsrX {
 // layout), gathers their X_j, and accumulates the d x d partial in registers; a
 // warp reduction ends the row, and Y_i is written, not accumulated.  xs: this
 // warp's shared-memory buffer of BcsrX<D>::kSmemFloats floats (odd d >= 3).
-// A row range outside the stored blocks, a column index outside [0, n) or a
-// misaligned X for the vector loads is flagged (FLAG_BAD_LAYOUT in ctl) and the
-// access skipped, so a corrupted buffer cannot fault the device.
+// A row range outside the stored blocks or a misaligned X for the vector loads
+// is flagged (FLAG_BAD_LAYOUT in ctl) and the row skipped; a column index is
+// clamped into [0, n).  A corrupted buffer thus cannot fault the device.
 template <int D, class T>
 __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ packed, long long i,
                                                  const float* __restrict__ X, float* __restrict__ Y, int lane,
@@ -70,7 +70,7 @@ __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ pac
   const long long n = hdr[0], nnzb = hdr[2];
   const long long k0 = rowptr[i], k1 = rowptr[i + 1];
   constexpr bool kVecX = !BcsrX<D>::kCoop && DD % 4 == 0;
-  if (k0 < 0 || k1 < k0 || k1 > nnzb || (kVecX && (reinterpret_cast<uintptr_t>(X) & 15u))) {
+  if (n < 1 || k0 < 0 || k1 < k0 || k1 > nnzb || (kVecX && (reinterpret_cast<uintptr_t>(X) & 15u))) {
     if (lane == 0) atomicOr(&ctl->flags, FLAG_BAD_LAYOUT);
     return;
   }
@@ -79,21 +79,17 @@ __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ pac
   for (int r = 0; r < D; ++r)
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[r][c] = 0.f;
-  bool bad = false;
+  const unsigned int nu = (unsigned int)n;
   for (long long kb = k0; kb < k1; kb += 32 * U) {
     int j[U];
     float a[U][DD];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long k = kb + 32 * u + lane;
-      bool valid = k < k1;
+      const bool valid = k < k1;
       // a lane past the row's end uses X_0 with zero values
-      j[u] = valid ? __ldg(col + k) : 0;
-      if ((unsigned long long)(long long)j[u] >= (unsigned long long)n) {
-        bad = true;
-        valid = false;
-        j[u] = 0;
-      }
+      // clamped into [0, n): whatever the buffer holds, X_j stays in bounds
+      j[u] = (int)min(valid ? (unsigned int)__ldg(col + k) : 0u, nu - 1u);
       const T* vk = val + bcsr_val_pos(k, 0, DD);
 #pragma unroll
       for (int e = 0; e < DD; ++e) a[u][e] = valid ? bcsr_load(vk + e * 32) : 0.f;
@@ -135,7 +131,6 @@ __device__ __forceinline__ void bcsr_row_product(const uint8_t* __restrict__ pac
           for (int c = 0; c < D; ++c) acc[r][c] = fmaf(a[u][r * D + m], x[m * D + c], acc[r][c]);
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->flags, FLAG_BAD_LAYOUT);
 #pragma unroll
   for (int r = 0; r < D; ++r)
 #pragma unroll

@@ -143,3 +143,35 @@ def test_bcsr_is_refused_where_not_built(P):
     inst = synth.make_instance(20, 9, 0.5, seed=1, p=0.5, dtype=np.float32)
     with pytest.raises(P.NsrgsError):
         P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), 20, 9, P.BCSR_F32)
+
+
+@pytest.mark.parametrize("d,storage", [(3, "bcsr_f32"), (4, "bcsr_bf16")])
+def test_corrupted_row_pointer_is_reported_not_faulted(P, d, storage):
+    """A row pointer past the stored blocks is caught by the row kernel's own
+    check (the row is skipped) and the solve returns INVALID_ARG."""
+    n = 60
+    inst = synth.make_instance(n, d, 1.0, seed=5, p=0.5, dtype=np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.STORAGE[storage])
+    torch.cuda.synchronize()
+    nnzb = int(pa.buf[:64].cpu().numpy().view(np.int64)[2])
+    bad = np.array([nnzb + 1000], dtype=np.int64).view(np.uint8)
+    pa.buf[64 + 8 * 5 : 64 + 8 * 6] = torch.from_numpy(bad.copy()).cuda()  # rowptr[5]
+    with pytest.raises(P.NsrgsError) as e:
+        P.nsrgs_solve(pa, 1.0 / n, 3, 2, spectral_max_iters=5)
+        torch.cuda.synchronize()
+    assert e.value.status == 1  # NSRGS_ERR_INVALID_ARG
+
+
+def test_corrupted_column_index_stays_in_bounds(P):
+    """A stored column index outside [0, n) is clamped into range by the row
+    kernel: the solve runs to completion (wrong data in, but no fault)."""
+    n, d = 60, 3
+    inst = synth.make_instance(n, d, 1.0, seed=5, p=0.5, dtype=np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BCSR_F32)
+    torch.cuda.synchronize()
+    off_col = int(pa.buf[:64].cpu().numpy().view(np.int64)[3])
+    bad = np.array([n + 100000], dtype=np.int32).view(np.uint8)
+    pa.buf[off_col : off_col + 4] = torch.from_numpy(bad.copy()).cuda()
+    X, info = P.nsrgs_solve(pa, 1.0 / n, 3, 2, spectral_max_iters=5)
+    torch.cuda.synchronize()
+    assert info.iters == 3 and torch.isfinite(X).all()
