@@ -324,7 +324,9 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                 P.nsrgs_set_kernel_timing(False)
                 ent["stream_ms"] = kms
                 ent["stream_GBps"] = alg / (kms / 1e3) / 1e9
-                if d <= 8 and name in ("dense_f32", "f32"):
+                # the comparison method on the same stream: FP32 panels for d <= 8, the
+                # tile-upper tensor-core stream above (its per-block SVD is a CTA's Jacobi)
+                if (d <= 8 and name in ("dense_f32", "f32")) or (d >= 16 and name == "bf16"):
                     Xg, _ = P.nsrgs_gpm_solve(pa, T, spectral_max_iters=SMAX, ws=ws)
                     torch.cuda.synchronize()
                     t = time.perf_counter()
@@ -332,6 +334,18 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                     torch.cuda.synchronize()
                     ent["gpm_solve_ms"] = 1e3 * (time.perf_counter() - t)
                     ent["gpm_final_dF_to_truth"] = P.nsrgs_dF(Xg, Zs, n, d, ws=ws)
+                    # the T iterations alone, both methods from the same spectral start
+                    X0, _ = P.nsrgs_spectral_init(pa, max_iters=SMAX, tol=1e-6, ws=ws, strict=False)
+                    for key, fn in (("iters_ms", P.nsrgs_solve), ("gpm_iters_ms", P.nsrgs_gpm_solve)):
+                        args_k = (pa, 1.0 / n, T, 2) if key == "iters_ms" else (pa, T)
+                        fn(*args_k, init=False, X=X0.clone(), ws=ws, info=False)
+                        torch.cuda.synchronize()
+                        Xi = X0.clone()
+                        e0.record()
+                        fn(*args_k, init=False, X=Xi, ws=ws, info=False)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ent[key] = e0.elapsed_time(e1)
                 res[name] = ent
                 del pa, ws, X, Y
             except Exception as e:

@@ -379,7 +379,9 @@ void nsrgs_server_destroy(nsrgs_server* s);
 
 /* The comparison method of the paper (§1.1, §4.1), the generalised power
  * method, on the same A stream: X_i <- sgn(sum_j A_ij X_j) with A_ii = I, the
- * sign computed exactly per block (float32 one-sided Jacobi SVD).  Same start,
+ * sign computed exactly per block by a float32 one-sided Jacobi SVD (a thread
+ * per block for d <= 8; a CTA per block for 8 < d <= 64, its columns paired
+ * round-robin, one warp per pair).  Same start,
  * stop rule, graph replay and info as nsrgs_solve; the paper cites GPM but
  * does not write it out, so this is the reading stated above.  A baseline:
  * NS-RGS replaces exactly this per-block SVD with K Newton-Schulz products. */

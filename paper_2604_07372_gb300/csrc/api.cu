@@ -559,10 +559,6 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
   nsrgs_status s = check_A(A, &g);
   if (s != NSRGS_OK) return s;
   if ((s = check_small_d(A->d)) != NSRGS_OK) return s;
-  if (method == METHOD_GPM && A->d > kMaxSmallD) {
-    set_error("the GPM baseline covers d <= 8");
-    return NSRGS_ERR_UNSUPPORTED;
-  }
   if ((s = check_ws(ws, ws_bytes, A->n, A->d)) != NSRGS_OK) return s;
   NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
   NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");

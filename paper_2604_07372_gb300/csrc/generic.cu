@@ -120,6 +120,128 @@ __global__ void __launch_bounds__(256) epilogue_generic_kernel(const float* __re
   }
 }
 
+// ---------------------------------------------- GPM (comparison method)
+// Generalised power method step for 8 < d <= 64, CTA per block: M = Y_i + X_i,
+// X_i <- sgn(M) by a float32 one-sided Jacobi SVD (the batched per-block SVD
+// that the comparison method pays for every iteration).  The columns of M are
+// paired round-robin: d/2 disjoint pairs per round (a dummy column when d is
+// odd), one warp per pair, d - 1 rounds per sweep, sweeps until every pair is
+// orthogonal to 1e-6 (at most 20).  Then U = M V with unit columns and
+// sgn(M) = U V^T.  Shared memory: U and V (column-major) and X_i, 3 D x D
+// floats.  Same update-norm / stop bookkeeping as the epilogue.
+__global__ void __launch_bounds__(256) gpm_generic_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                                          float* __restrict__ Xout, int n, int D, double tol,
+                                                          Ctl* ctl) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double sh[32];
+  __shared__ float woff[8];
+  if (ctl->stop) return;
+  const int DD = D * D;
+  float* U = sm;           // column c at U + c * D
+  float* Vm = sm + DD;     // column c at Vm + c * D
+  float* x = sm + 2 * DD;  // X_i, row-major
+  const long long base = (long long)blockIdx.x * DD;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+    const int r = e / D, c = e % D;
+    const float xv = X[base + e];
+    x[e] = xv;
+    U[c * D + r] = Y[base + e] + xv;
+    Y[base + e] = 0.f;
+    Vm[c * D + r] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  const int m = D + (D & 1);  // columns in the round-robin, with a dummy when D is odd
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    float off = 0.f;  // warp-uniform
+    for (int rd = 0; rd < m - 1; ++rd) {
+      for (int k = warp; k < m / 2; k += nw) {
+        int p, q;
+        if (k == 0) {
+          p = m - 1;
+          q = rd;
+        } else {
+          p = (rd + k) % (m - 1);
+          q = (rd - k + (m - 1)) % (m - 1);
+        }
+        if (p >= D || q >= D) continue;
+        float* up = U + p * D;
+        float* uq = U + q * D;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int r = lane; r < D; r += 32) {
+          al = fmaf(up[r], up[r], al);
+          be = fmaf(uq[r], uq[r], be);
+          ga = fmaf(up[r], uq[r], ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        const float nrm = sqrtf(al * be);
+        if (nrm == 0.f || fabsf(ga) <= 1e-8f * nrm) continue;
+        off = fmaxf(off, fabsf(ga) / nrm);
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = rsqrtf(1.f + t * t);
+        const float sn = c * t;
+        float* vp = Vm + p * D;
+        float* vq = Vm + q * D;
+        for (int r = lane; r < D; r += 32) {
+          const float a1 = up[r], a2 = uq[r];
+          up[r] = c * a1 - sn * a2;
+          uq[r] = sn * a1 + c * a2;
+          const float b1 = vp[r], b2 = vq[r];
+          vp[r] = c * b1 - sn * b2;
+          vq[r] = sn * b1 + c * b2;
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0) woff[warp] = off;
+    __syncthreads();
+    float mo = 0.f;
+    for (int w = 0; w < nw; ++w) mo = fmaxf(mo, woff[w]);
+    __syncthreads();
+    if (mo < 1e-6f) break;
+  }
+  for (int c = warp; c < D; c += nw) {  // unit columns: U_svd = M V Sigma^{-1}
+    float s2 = 0.f;
+    for (int r = lane; r < D; r += 32) s2 = fmaf(U[c * D + r], U[c * D + r], s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    const float inv = s2 > 0.f ? rsqrtf(s2) : 0.f;
+    for (int r = lane; r < D; r += 32) U[c * D + r] *= inv;
+  }
+  __syncthreads();
+  double diff2 = 0.0;
+  bool finite = true;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+    const int r = e / D, c = e % D;
+    float q = 0.f;
+    for (int k = 0; k < D; ++k) q = fmaf(U[k * D + r], Vm[k * D + c], q);
+    finite = finite && isfinite(q);
+    Xout[base + e] = q;
+    const double dd = (double)q - (double)x[e];
+    diff2 += dd * dd;
+  }
+  if (!finite) atomicOr(&ctl->flags, FLAG_NONFINITE);
+  const double bs = block_sum(diff2, sh);
+  if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double tot = atomicAdd(&ctl->upd_acc, 0.0);
+      const double un = sqrt(tot / ((double)n * D));
+      ctl->last_upd = un;
+      ctl->iters_done += 1;
+      if (tol > 0.0 && un < tol) ctl->stop = 1;
+      ctl->upd_acc = 0.0;
+      ctl->counter = 0u;
+    }
+  }
+}
+
 // ------------------------------------------------- exact sign (float64)
 // S <- M / ||M||_F, then S <- S (3I - S^T S)/2 until ||I - S^T S||_F < 1e-14.
 // Shared scratch: 3 D x D doubles (S, T, U).  Result in S.
@@ -339,6 +461,7 @@ static cudaError_t set_smem(const void* k, size_t bytes) {
 cudaError_t generic_prepare(int d) {
   cudaError_t e;
   if ((e = set_smem((const void*)epilogue_generic_kernel, 5 * d * d * sizeof(float))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)gpm_generic_kernel, 3 * d * d * sizeof(float))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)polar_generic_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)polar_single_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)update_generic_kernel, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
@@ -355,6 +478,12 @@ cudaError_t launch_epilogue_generic(const float* X, float* Y, float* Xout, int n
                                     int safeguard, double tol, Ctl* ctl, double* upd_out, cudaStream_t st) {
   epilogue_generic_kernel<<<n, 256, 5 * d * d * sizeof(float), st>>>(X, Y, Xout, n, d, eta, K, safeguard, tol, ctl,
                                                                       upd_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gpm_generic(const float* X, float* Y, float* Xout, int n, int d, double tol, Ctl* ctl,
+                               cudaStream_t st) {
+  gpm_generic_kernel<<<n, 256, 3 * d * d * sizeof(float), st>>>(X, Y, Xout, n, d, tol, ctl);
   return cudaGetLastError();
 }
 

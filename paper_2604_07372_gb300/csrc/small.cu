@@ -370,8 +370,11 @@ cudaError_t launch_epilogue(const float* X, float* Y, float* Xout, int n, int d,
   return cudaGetLastError();
 }
 
+cudaError_t launch_gpm_generic(const float*, float*, float*, int, int, double, Ctl*, cudaStream_t);
+
 cudaError_t launch_gpm_epilogue(const float* X, float* Y, float* Xout, int n, int d, double tol, Ctl* ctl,
                                 cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_gpm_generic(X, Y, Xout, n, d, tol, ctl, st);
   const int grid = (n + 127) / 128;
 #define L(DD) gpm_epilogue_kernel<DD><<<grid, 128, 0, st>>>(X, Y, Xout, n, tol, ctl)
   NSRGS_DISPATCH_D(d, L)

@@ -68,3 +68,39 @@ def test_dF_large_d(P, n, d):
     got = P.nsrgs_dF(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), n, d)
     ref = O.dF(X.astype(np.float64), Y.astype(np.float64), d)
     assert abs(got - ref) <= 1e-9 * ref
+
+
+@pytest.mark.parametrize("n,d", [(60, 16), (40, 25), (30, 32), (20, 64), (50, 9)])
+def test_gpm_large_d_matches_oracle(P, n, d):
+    """The GPM baseline above d = 8 (per-block one-sided Jacobi SVD in a CTA)
+    against the oracle's GPM from the same start."""
+    T = 10
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=300 + d, dtype=np.float32)
+    A = inst.dense()
+    X0, _ = O.spectral_init(A, n, d)
+    X0 = X0.astype(np.float32).astype(np.float64)
+    ref = O.gpm(A, n, d, T, X0=X0)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.DENSE_F32)
+    X = torch.from_numpy(X0.astype(np.float32)).cuda()
+    X, info = P.nsrgs_gpm_solve(pa, T, init=False, X=X)
+    torch.cuda.synchronize()
+    assert info.iters == T
+    Xb = O.blocks(to64(X), d)
+    assert np.max(np.abs(np.swapaxes(Xb, 1, 2) @ Xb - np.eye(d))) <= 1e-4  # exact signs: orthogonal blocks
+    assert O.dF(to64(X), ref, d) / math.sqrt(n * d) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["bf16", "dense_bf16"])
+def test_gpm_tensor_core_storage_within_one_percent(P, storage):
+    """GPM on the tensor-core streams (BF16 A, X rounded to BF16 for the product)
+    reaches the float32 GPM's final d_F to the truth within 1%."""
+    n, d, T = 300, 16, 20
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=316, dtype=np.float32)
+    up = torch.from_numpy(inst.upper).cuda()
+    Xf, _ = P.nsrgs_gpm_solve(P.nsrgs_pack_upper(up, n, d, P.DENSE_F32), T)
+    Xb, info = P.nsrgs_gpm_solve(P.nsrgs_pack_upper(up, n, d, P.STORAGE[storage]), T)
+    torch.cuda.synchronize()
+    Z = inst.Zstack()
+    ef, eb = O.dF(to64(Xf), Z, d), O.dF(to64(Xb), Z, d)
+    assert info.iters == T
+    assert abs(eb - ef) / ef <= 0.01, (ef, eb)
