@@ -149,12 +149,14 @@ __host__ __device__ constexpr int panel_loadb(int d, int storage) {
                                   : (storage == NSRGS_F32 ? 16 : 8);
 }
 
-// Consumer warps per CTA.  FP32 storage is bandwidth-bound with 8.  BF16 and FP8
-// storage at d <= 4 ask for 2d FMAs per element on a half or a quarter of the
-// bytes and are issue-bound; more consumer warps per scheduler hide more of the
-// per-step latency (shared-memory loads, shuffles, barrier waits).
+// Consumer warps per CTA.  At d <= 4, 12 consumer warps (3 per scheduler) hide
+// more of each step's latency (shared-memory loads, shuffles, barrier waits) and
+// make each stage's bulk copy 1.5x larger: FP32 reaches the copy bandwidth with
+// them, and BF16 / FP8 (2d FMAs per element on a half or a quarter of the bytes,
+// issue-bound) gain ~10%.  Above d = 4 the per-thread tiles need the registers
+// of 8 warps.
 __host__ __device__ constexpr int panel_nw(int d, int storage) {
-  return (storage != NSRGS_F32 && d <= 4) ? 12 : 8;
+  return d <= 4 ? 12 : 8;
 }
 
 // Rows of X/Y padding needed by a layout (columns of the last step run past n*D).

@@ -33,8 +33,8 @@ def loadb(d, storage):
 
 
 def nw(d, storage):
-    """Consumer warps per CTA: 12 for BF16/FP8 storage at d <= 4, else 8."""
-    return 12 if (storage != 0 and d <= 4) else 8
+    """Consumer warps per CTA: 12 at d <= 4, else 8."""
+    return 12 if d <= 4 else 8
 
 
 class Geom:
