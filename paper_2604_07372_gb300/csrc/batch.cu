@@ -138,22 +138,6 @@ __device__ void cta_subspace_step(const float* __restrict__ V, float* __restrict
   __syncthreads();
 }
 
-// X0_i = sgn(V_i) for every block of one instance (in place allowed).
-template <int D>
-__device__ void cta_polar(const float* V, float* X0, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double M[D][D], Q[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) M[r][c] = V[((long long)i * D + r) * D + c];
-    polar_fp64<D>(M, Q);
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) X0[((long long)i * D + r) * D + c] = (float)Q[r][c];
-  }
-}
 
 __device__ __forceinline__ float v0_entry(long long e) {
   unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
@@ -208,64 +192,115 @@ __global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs
   }
 }
 
-// One phase step per instance (CTA per instance), after the tick's A-stream.
+// Spectral phase step per instance (CTA per instance), after the tick's A-stream:
+// one subspace-iteration step; at convergence (or the pass cap) the instance
+// moves to PHASE_POLAR, whose blocks batch_block_kernel turns into X^0.
 template <int D>
 __global__ void __launch_bounds__(256) batch_phase_kernel(const BatchDesc* descs) {
-  __shared__ double sh[32];
-  __shared__ int fin;
   __shared__ double s_res, s_h2;
   const BatchDesc& d = descs[blockIdx.x];
   Ctl* c = d.ctl;
-  const int ph = c->phase;  // uniform: written only by earlier launches
-  const int n = d.g.n;
-  const int rows = n * D;
-  if (ph == PHASE_SPEC) {
-    const int si = c->spec_iters;
-    const float* V = d.X[(si + 1) & 1];
-    float* Vn = d.X[si & 1];
-    cta_subspace_step<D>(V, d.Y, d.W, Vn, rows, &s_res, &s_h2);
-    if (threadIdx.x == 0) {
-      const double rel = sqrt(s_res / fmax(s_h2, 1e-300));
-      c->spec_res = rel;
-      c->spec_iters = si + 1;
-      if (rel <= d.spec_tol) c->spec_stop = 1;
-      fin = (rel <= d.spec_tol) || (si + 1 >= d.smax);
+  if (c->phase != PHASE_SPEC) return;  // uniform: written only by earlier launches
+  const int rows = d.g.n * D;
+  const int si = c->spec_iters;
+  const float* V = d.X[(si + 1) & 1];
+  float* Vn = d.X[si & 1];
+  cta_subspace_step<D>(V, d.Y, d.W, Vn, rows, &s_res, &s_h2);
+  if (threadIdx.x == 0) {
+    const double rel = sqrt(s_res / fmax(s_h2, 1e-300));
+    c->spec_res = rel;
+    c->spec_iters = si + 1;
+    if (rel <= d.spec_tol) c->spec_stop = 1;
+    if (rel <= d.spec_tol || si + 1 >= d.smax) c->phase = PHASE_POLAR;
+  }
+}
+
+// The per-block part of a tick, thread per block over every instance's blocks
+// (bbase: first global block of each instance, count + 1 entries), so that the
+// largest instance's blocks are spread over the whole GPU:
+//  PHASE_ITER:  Algorithm 2's update of block i (block_update), X^{t+1}_i also
+//               written to the caller's X;
+//  PHASE_POLAR: X^0_i = sgn(V_i), float64 polar (Algorithm 2's start).
+// Lanes of a warp are grouped by instance (blocks are consecutive, so a group is
+// a contiguous run of lanes); the group sums its update norms with a segmented
+// scan and its last lane adds them and the group's block count to the
+// instance's control block.  The lane whose count completes the instance
+// finishes the iteration (update norm, stop test) or starts the iterations.
+template <int D>
+__global__ void __launch_bounds__(256) batch_block_kernel(const BatchDesc* descs, const long long* bbase, int cnt) {
+  constexpr int DD = D * D;
+  const int lane = threadIdx.x & 31;
+  const long long total = bbase[cnt];
+  for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    int inst = -1, ph = PHASE_IDLE;
+    if (g < total) {
+      inst = find_first_leq(bbase, cnt, g);
+      ph = descs[inst].ctl->phase;
     }
-    __syncthreads();
-    if (fin) {
-      cta_polar<D>(Vn, d.X[0], n);  // Algorithm 2's start X^0 = sgn_n(Y)
-      __syncthreads();
-      if (d.T == 0)
-        for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.Xout[e] = d.X[0][e];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        c->iters_done = 0;
-        c->phase = d.T > 0 ? PHASE_ITER : PHASE_DONE;
+    const bool act = ph == PHASE_ITER || ph == PHASE_POLAR;
+    double part = 0.0;
+    if (act) {
+      const BatchDesc& d = descs[inst];
+      const long long i = g - bbase[inst];
+      const long long base = i * DD;
+      const int n = d.g.n;
+      if (ph == PHASE_ITER) {
+        const int it = d.ctl->iters_done;
+        float* Xn = d.X[(it + 1) & 1];
+        unsigned int flags = 0;
+        block_update<D>(d.X[it & 1], d.Y, Xn, i, n, d.eta, d.K, d.safeguard != 0, part, flags);
+        if (flags) atomicOr(&d.ctl->flags, flags);
+#pragma unroll
+        for (int e = 0; e < DD; ++e) d.Xout[base + e] = Xn[base + e];
+      } else {
+        const float* Vn = d.X[(d.ctl->spec_iters - 1) & 1];
+        double M[D][D], Q[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) M[r][c] = Vn[base + r * D + c];
+        polar_fp64<D>(M, Q);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            d.X[0][base + r * D + c] = (float)Q[r][c];
+            if (d.T == 0) d.Xout[base + r * D + c] = (float)Q[r][c];
+          }
       }
     }
-  } else if (ph == PHASE_ITER) {
-    const int it = c->iters_done;
-    const float* Xc = d.X[it & 1];
-    float* Xn = d.X[(it + 1) & 1];
-    double diff2 = 0.0;
-    unsigned int flags = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) block_update<D>(Xc, d.Y, Xn, i, n, d.eta, d.K, d.safeguard != 0, diff2, flags);
-    if (flags) atomicOr(&c->flags, flags);
-    const double tot = block_sum(diff2, sh);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double un = sqrt(tot / ((double)n * D));
-      c->last_upd = un;
-      c->iters_done = it + 1;
-      const bool conv = d.tol > 0.0 && un < d.tol;
-      if (conv) c->stop = 1;
-      fin = (it + 1 >= d.T) || conv || ((c->flags & FLAG_NONFINITE) != 0);
+    // segmented inclusive scan over the lanes of this warp's instance groups
+    const unsigned int m = __match_any_sync(0xffffffffu, act ? inst : -1);
+    const int head = __ffs(m) - 1, tail = 31 - __clz(m);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, part, o);
+      if (lane - o >= head) part += t;
     }
-    __syncthreads();
-    if (fin) {
-      for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.Xout[e] = Xn[e];
-      __syncthreads();
-      if (threadIdx.x == 0) c->phase = PHASE_DONE;
+    if (act && lane == tail) {
+      Ctl* c = descs[inst].ctl;
+      const BatchDesc& d = descs[inst];
+      if (ph == PHASE_ITER) atomicAdd(&c->upd_acc, part);
+      __threadfence();
+      const unsigned int k = (unsigned int)__popc(m);
+      if (atomicAdd(&c->counter, k) + k == (unsigned int)d.g.n) {
+        __threadfence();
+        if (ph == PHASE_ITER) {
+          const int it = c->iters_done;
+          const double un = sqrt(atomicAdd(&c->upd_acc, 0.0) / ((double)d.g.n * D));
+          c->last_upd = un;
+          c->iters_done = it + 1;
+          const bool conv = d.tol > 0.0 && un < d.tol;
+          if (conv) c->stop = 1;
+          if (it + 1 >= d.T || conv || (atomicOr(&c->flags, 0u) & FLAG_NONFINITE)) c->phase = PHASE_DONE;
+        } else {
+          c->iters_done = 0;
+          c->phase = d.T > 0 ? PHASE_ITER : PHASE_DONE;
+        }
+        c->upd_acc = 0.0;
+        c->counter = 0u;
+      }
     }
   }
 }
@@ -399,6 +434,15 @@ cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t s
   return cudaGetLastError();
 }
 
+cudaError_t batch_block(const BatchDesc* descs, const long long* bbase, int count, int d, long long total_blocks,
+                        cudaStream_t st) {
+  const long long g = std::max<long long>(1, std::min<long long>((total_blocks + 255) / 256, 4LL * num_sms()));
+#define L(DD) batch_block_kernel<DD><<<(unsigned)g, 256, 0, st>>>(descs, bbase, count)
+  NSRGS_BATCH_D(d, L)
+#undef L
+  return cudaGetLastError();
+}
+
 cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st) {
   batch_report_kernel<<<(count + 127) / 128, 128, 0, st>>>(descs, count, out);
   return cudaGetLastError();
@@ -415,12 +459,13 @@ size_t batch_instance_bytes(int n, int d) {
   return 256 + 4 * vec;
 }
 
-// Table region: descriptors | panel step bases | reports | block-sparse row bases.
+// Table region: descriptors | panel step bases | reports | block-sparse row bases |
+// block bases.
 size_t batch_table_bytes(int count) {
   const size_t t = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
   const size_t b = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
   const size_t r = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
-  return t + 2 * b + r;
+  return t + 3 * b + r;
 }
 
 void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d) {
@@ -509,14 +554,17 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   BatchReport* d_rep = reinterpret_cast<BatchReport*>(base + tbytes + bbytes);
   const size_t rbytes = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
   long long* d_rbase = reinterpret_cast<long long*>(base + tbytes + bbytes + rbytes);
+  long long* d_bbase = reinterpret_cast<long long*>(base + tbytes + 2 * bbytes + rbytes);
   std::vector<BatchDesc> descs(count);
-  std::vector<long long> bases(count + 1), rbases(count + 1);
+  std::vector<long long> bases(count + 1), rbases(count + 1), bbases(count + 1);
   size_t off = batch_table_bytes(count);
-  long long steps = 0, rows = 0;
+  long long steps = 0, rows = 0, blocks = 0;
   for (int i = 0; i < count; ++i) {
     BatchDesc& ds = descs[i];
     memset(&ds, 0, sizeof(ds));
     rbases[i] = rows;
+    bbases[i] = blocks;
+    blocks += items[i].n;
     if (sparse) {
       // no panel steps: the row kernel streams this instance
       ds.sparse = 1;
@@ -545,10 +593,12 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   }
   bases[count] = steps;
   rbases[count] = rows;
+  bbases[count] = blocks;
   if (!sparse) NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_base, bases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_rbase, rbases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(d_bbase, bbases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
 
   int dev = 0;
   NSRGS_CUDA_TRY(cudaGetDevice(&dev));
@@ -582,6 +632,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
       e = sparse ? batch_bcsr_stream(d_descs, d_rbase, count, d, storage == NSRGS_BCSR_BF16, rows, cs)
                  : batch_stream(d_descs, d_base, count, d, storage, cs, false);
       if (e == cudaSuccess) e = batch_phase(d_descs, count, d, cs);
+      if (e == cudaSuccess) e = batch_block(d_descs, d_bbase, count, d, blocks, cs);
     }
     if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);
     cudaGraph_t graph = nullptr;

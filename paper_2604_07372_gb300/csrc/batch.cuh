@@ -6,6 +6,10 @@
 namespace nsrgs {
 
 // One instance as the batched kernels see it (device memory, written by the host).
+// Phase of a batched / served instance after its spectral passes: the blocks of
+// its basis are turned into X^0 (extends the PHASE_* values of the control block).
+constexpr int PHASE_POLAR = 5;
+
 struct BatchDesc {
   const uint8_t* packed;  // packed A (panel layout)
   float* X[2];            // ping-pong iterates / spectral bases, padded to n*d + 64 rows
@@ -45,6 +49,8 @@ cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int coun
                          cudaStream_t st, bool prepare);
 cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st);
 cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t st);
+cudaError_t batch_block(const BatchDesc* descs, const long long* bbase, int count, int d, long long total_blocks,
+                        cudaStream_t st);
 cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st);
 cudaError_t batch_reset(const BatchDesc* descs, int count, cudaStream_t st);
 

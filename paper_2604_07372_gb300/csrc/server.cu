@@ -111,10 +111,11 @@ struct nsrgs_server {
   BatchDesc* d_descs = nullptr;
   long long* d_base = nullptr;
   long long* d_rbase = nullptr;  // first global row of each slot's block-sparse rows
+  long long* d_bbase = nullptr;  // first global block of each slot
   BatchReport* d_rep = nullptr;
   std::vector<BatchDesc> h_descs;
   std::vector<Ctl*> idle_ctl;  // per slot: zeroed control block used while the slot is free
-  std::vector<long long> h_base, h_rbase;
+  std::vector<long long> h_base, h_rbase, h_bbase;
   std::vector<BatchReport> h_rep;
   std::vector<Slot> slots;
   std::deque<Request> queue;
@@ -161,9 +162,11 @@ extern "C" nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void
   s->d_rep = reinterpret_cast<BatchReport*>(s->arena + tbytes + bbytes);
   const size_t rbytes = ((size_t)M * sizeof(BatchReport) + 255) / 256 * 256;
   s->d_rbase = reinterpret_cast<long long*>(s->arena + tbytes + bbytes + rbytes);
+  s->d_bbase = reinterpret_cast<long long*>(s->arena + tbytes + 2 * bbytes + rbytes);
   s->h_descs.assign(M, BatchDesc{});
   s->h_base.assign(M + 1, 0);
   s->h_rbase.assign(M + 1, 0);
+  s->h_bbase.assign(M + 1, 0);
   s->h_rep.assign(M, BatchReport{});
   s->slots.assign(M, Slot{});
   s->alloc.reset(tb, arena_bytes);
@@ -237,6 +240,8 @@ static cudaError_t server_capture(nsrgs_server* s) {
       if (e == cudaSuccess)
         e = batch_bcsr_stream(s->d_descs, s->d_rbase, M, d, sparse_storage(s) == NSRGS_BCSR_BF16, 1LL << 40, cs);
       if (e == cudaSuccess) e = batch_phase(s->d_descs, M, d, cs);
+      // grid sized for a full table; blocks past the current total return at once
+      if (e == cudaSuccess) e = batch_block(s->d_descs, s->d_bbase, M, d, 1LL << 40, cs);
     }
     if (e == cudaSuccess) e = batch_report(s->d_descs, M, s->d_rep, cs);
     cudaGraph_t graph = nullptr;
@@ -307,18 +312,23 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
   }
   // 2. instance table: only busy slots contribute steps (even split over active work)
   if (s->dirty) {
-    long long steps = 0, rows = 0;
+    long long steps = 0, rows = 0, blocks = 0;
     for (int i = 0; i < M; ++i) {
       s->h_base[i] = steps;
       s->h_rbase[i] = rows;
+      s->h_bbase[i] = blocks;
       if (s->slots[i].busy) {
         steps += s->h_descs[i].g.total_steps;
         if (s->h_descs[i].sparse) rows += s->h_descs[i].g.n;
+        blocks += s->h_descs[i].g.n;
       }
     }
     s->h_base[M] = steps;
     s->h_rbase[M] = rows;
+    s->h_bbase[M] = blocks;
     NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_rbase, s->h_rbase.data(), sizeof(long long) * (M + 1),
+                                   cudaMemcpyHostToDevice, s->st));
+    NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_bbase, s->h_bbase.data(), sizeof(long long) * (M + 1),
                                    cudaMemcpyHostToDevice, s->st));
     NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_descs, s->h_descs.data(), sizeof(BatchDesc) * M, cudaMemcpyHostToDevice, s->st));
     NSRGS_CUDA_TRY(cudaMemcpyAsync(s->d_base, s->h_base.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice,
