@@ -301,12 +301,15 @@ __global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restri
                                                            long long rows, int D, float shift, int mode,
                                                            SpecScratch s, Ctl* ctl) {
   // mode 0: spectral Gram (W = Y + shift V; outputs W^T W and V^T W); mode 1: M = Yv^T Xq.
-  extern __shared__ __align__(16) float smg[];
+  // The chunk is staged as float64 (exact conversions, once per element), so the
+  // inner products are float64 FMAs alone: GB300 runs float64 conversions on the
+  // same slow pipe as float64 arithmetic.
+  extern __shared__ __align__(16) double smg[];
   if (mode == 0 && ctl->spec_stop) return;
   const int DD = D * D;
   const int nout = mode == 0 ? 2 * DD : DD;
-  float* P = smg;                     // kRowsPerCta x D
-  float* Q = smg + kRowsPerCta * D;   // kRowsPerCta x D
+  double* P = smg;                     // kRowsPerCta x D
+  double* Q = smg + kRowsPerCta * D;   // kRowsPerCta x D
   double acc[32];  // outputs o = threadIdx.x + k * 256, k < nout / 256 <= 2 * 64 * 64 / 256
   for (int k = 0; k < 32; ++k) acc[k] = 0.0;
   for (long long r0 = (long long)blockIdx.x * kRowsPerCta; r0 < rows; r0 += (long long)gridDim.x * kRowsPerCta) {
@@ -333,9 +336,9 @@ __global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restri
       const int a = oo / D, b = oo % D;
       double sum = 0.0;
       if (mode == 0 && o < DD) {
-        for (int r = 0; r < nr; ++r) sum += (double)Q[r * D + a] * (double)Q[r * D + b];
+        for (int r = 0; r < nr; ++r) sum += Q[r * D + a] * Q[r * D + b];
       } else {
-        for (int r = 0; r < nr; ++r) sum += (double)P[r * D + a] * (double)Q[r * D + b];
+        for (int r = 0; r < nr; ++r) sum += P[r * D + a] * Q[r * D + b];
       }
       acc[k] += sum;
     }
@@ -387,19 +390,35 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
     hh[o] = s.H[o];
   }
   __syncthreads();
+  // Columns in tiles of 16 with k outer, so each row element is converted to
+  // float64 once per tile (float64 conversions share GB300's slow float64 pipe);
+  // every sum keeps its order over k.
+  constexpr int kTile = 16;
   double res = 0.0;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
     const float* w = W + r * D;
     const float* v = V + r * D;
-    for (int c = 0; c < D; ++c) {
-      double nv = 0.0, vh = 0.0;
+    for (int c0 = 0; c0 < D; c0 += kTile) {
+      double nv[kTile], vh[kTile];
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) nv[j] = vh[j] = 0.0;
       for (int k = 0; k < D; ++k) {
-        nv += (double)w[k] * rinv[k * D + c];
-        vh += (double)v[k] * hh[k * D + c];
+        const double wk = w[k], vk = v[k];
+#pragma unroll
+        for (int j = 0; j < kTile; ++j)
+          if (c0 + j < D) {
+            nv[j] += wk * rinv[k * D + c0 + j];
+            vh[j] += vk * hh[k * D + c0 + j];
+          }
       }
-      Vnew[r * D + c] = (float)nv;
-      const double e = (double)w[c] - vh;
-      res += e * e;
+#pragma unroll
+      for (int j = 0; j < kTile; ++j)
+        if (c0 + j < D) {
+          const int c = c0 + j;
+          Vnew[r * D + c] = (float)nv[j];
+          const double e = (double)w[c] - vh[j];
+          res += e * e;
+        }
     }
   }
   const double bs = block_sum(res, sh);
@@ -466,7 +485,7 @@ cudaError_t generic_prepare(int d) {
   if ((e = set_smem((const void*)polar_single_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)update_generic_kernel, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)dist_generic_kernel, d * d * sizeof(double))) != cudaSuccess) return e;
-  return set_smem((const void*)gram_generic_kernel, 2 * kRowsPerCta * d * sizeof(float));
+  return set_smem((const void*)gram_generic_kernel, 2 * kRowsPerCta * d * sizeof(double));
 }
 
 static int gram_grid(long long rows) {
@@ -489,7 +508,7 @@ cudaError_t launch_gpm_generic(const float* X, float* Y, float* Xout, int n, int
 
 cudaError_t launch_spec_gram_generic(const float* V, float* Y, float* W, long long rows, int d, float shift,
                                      const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
-  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(float), st>>>(V, Y, W, nullptr, rows, d,
+  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(V, Y, W, nullptr, rows, d,
                                                                                         shift, 0, s, ctl);
   return cudaGetLastError();
 }
@@ -508,7 +527,7 @@ cudaError_t launch_polar_generic(const float* V, float* X0, int n, int d, cudaSt
 
 cudaError_t launch_dF_generic(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
                               cudaStream_t st) {
-  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(float), st>>>(nullptr, const_cast<float*>(Yv),
+  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(nullptr, const_cast<float*>(Yv),
                                                                                         nullptr, X, rows, d, 0.f, 1, s,
                                                                                         ctl);
   cudaError_t e = cudaGetLastError();
