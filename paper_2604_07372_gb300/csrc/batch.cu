@@ -63,82 +63,9 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_stream_batch_ke
   panel_stream_body<D, ST>(src, src.base(src.cnt));
 }
 
-// ------------------------------------------------ per-instance CTA kernels
-// W = Y + V (or W = V when Y is null), W^T W and V^T W in float64, Cholesky of
-// W^T W; Vn = W chol^{-1}; returns ||W - V H||^2 and ||H||^2 in thread 0.
-template <int D>
-__device__ void cta_subspace_step(const float* __restrict__ V, float* __restrict__ Y, float* __restrict__ W,
-                                  float* __restrict__ Vn, int rows, double* res_out, double* h2_out) {
-  __shared__ double sh[32];
-  __shared__ double WW[D * D], H[D * D], Rinv[D * D], Rtmp[D * D];
-  double ww[D][D], vw[D][D];
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int b = 0; b < D; ++b) ww[a][b] = vw[a][b] = 0.0;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-    float v[D], w[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      v[k] = V[(long long)r * D + k];
-      w[k] = Y ? Y[(long long)r * D + k] + v[k] : v[k];
-      W[(long long)r * D + k] = w[k];
-      if (Y) Y[(long long)r * D + k] = 0.f;
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = 0; b < D; ++b) {
-        ww[a][b] += (double)w[a] * (double)w[b];
-        vw[a][b] += (double)v[a] * (double)w[b];
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const double x1 = block_sum(ww[a][b], sh);
-      const double x2 = block_sum(vw[a][b], sh);
-      if (threadIdx.x == 0) {
-        WW[a * D + b] = x1;
-        H[a * D + b] = x2;
-      }
-    }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    chol_inv(WW, Rinv, D, Rtmp);
-    double h2 = 0.0;
-    for (int o = 0; o < D * D; ++o) h2 += H[o] * H[o];
-    *h2_out = h2;
-  }
-  __syncthreads();
-  double res = 0.0;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-    double v[D], w[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      v[k] = V[(long long)r * D + k];
-      w[k] = W[(long long)r * D + k];
-    }
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      double nv = 0.0, vh = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        nv += w[k] * Rinv[k * D + c];
-        vh += v[k] * H[k * D + c];
-      }
-      Vn[(long long)r * D + c] = (float)nv;
-      const double e = w[c] - vh;
-      res += e * e;
-    }
-  }
-  const double tot = block_sum(res, sh);
-  if (threadIdx.x == 0) *res_out = tot;
-  __syncthreads();
-}
-
-
+// ------------------------------------------------ per-instance kernels
+// Deterministic start V^0 of the spectral subspace iteration (any full-rank
+// start works; entries uniform in (-1, 1)).
 __device__ __forceinline__ float v0_entry(long long e) {
   unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -148,10 +75,10 @@ __device__ __forceinline__ float v0_entry(long long e) {
 }
 
 // Prepares every instance in PHASE_ADMIT: clears its scratch, then either takes
-// X^0 from the caller (start_given) or builds the orthonormal start basis of
-// the spectral subspace iteration.
+// X^0 from the caller (start_given) or writes the start V^0 of the spectral
+// subspace iteration, which the first (orthonormalising) pass turns into a basis.
 template <int D>
-__global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs) {
+__global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs, int* nspec) {
   const BatchDesc& d = descs[blockIdx.x];
   Ctl* c = d.ctl;
   if (c->phase != PHASE_ADMIT) return;
@@ -170,10 +97,8 @@ __global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs
     for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = d.Xout[e];
   } else {
     for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = v0_entry(e);
-    __syncthreads();
-    double res, h2;
-    cta_subspace_step<D>(d.X[0], nullptr, d.W, d.X[1], rows, &res, &h2);
   }
+  for (int e = threadIdx.x; e < kScrBytes / 8; e += blockDim.x) d.scr[e] = 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
     c->upd_acc = 0.0;
@@ -185,33 +110,226 @@ __global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs
     c->flags = 0u;
     c->spec_iters = 0;
     c->spec_stop = 0;
-    c->phase = d.start_given ? (d.T > 0 ? PHASE_ITER : PHASE_DONE) : PHASE_SPEC;
+    c->phase = d.start_given ? (d.T > 0 ? PHASE_ITER : PHASE_DONE) : PHASE_SPEC0;
+    if (!d.start_given) atomicAdd(nspec, 1);
   }
   if (d.start_given && d.T == 0) {
     // nothing to iterate: X^0 is the answer (already in the caller's buffer)
   }
 }
 
-// Spectral phase step per instance (CTA per instance), after the tick's A-stream:
-// one subspace-iteration step; at convergence (or the pass cap) the instance
-// moves to PHASE_POLAR, whose blocks batch_block_kernel turns into X^0.
-template <int D>
-__global__ void __launch_bounds__(256) batch_phase_kernel(const BatchDesc* descs) {
-  __shared__ double s_res, s_h2;
-  const BatchDesc& d = descs[blockIdx.x];
-  Ctl* c = d.ctl;
-  if (c->phase != PHASE_SPEC) return;  // uniform: written only by earlier launches
-  const int rows = d.g.n * D;
-  const int si = c->spec_iters;
-  const float* V = d.X[(si + 1) & 1];
-  float* Vn = d.X[si & 1];
-  cta_subspace_step<D>(V, d.Y, d.W, Vn, rows, &s_res, &s_h2);
+// Instance of global block g for the CTA's chunk [g0, g0 + blockDim.x): thread 0
+// bounds the chunk's instances once, each thread searches only that range.
+// Call from every thread of the CTA.
+__device__ __forceinline__ int chunk_instance(const long long* bbase, int cnt, long long g0, long long total,
+                                              long long g, int* s_range) {
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double rel = sqrt(s_res / fmax(s_h2, 1e-300));
-    c->spec_res = rel;
-    c->spec_iters = si + 1;
-    if (rel <= d.spec_tol) c->spec_stop = 1;
-    if (rel <= d.spec_tol || si + 1 >= d.smax) c->phase = PHASE_POLAR;
+    const long long last = g0 + blockDim.x - 1 < total ? g0 + blockDim.x - 1 : total - 1;
+    s_range[0] = find_first_leq(bbase, cnt, g0);
+    s_range[1] = find_first_leq(bbase, cnt, last);
+  }
+  __syncthreads();
+  if (g >= total) return -1;
+  const int lo = s_range[0];
+  return lo + find_first_leq(bbase + lo, s_range[1] - lo + 1, g);
+}
+
+// Segmented inclusive sum over runs of lanes that share a key (runs of an
+// instance's consecutive blocks): on return the run's last lane holds the sum.
+__device__ __forceinline__ double seg_sum(double v, int lane, int head) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= head) v += t;
+  }
+  return v;
+}
+
+// The spectral subspace pass over every instance in it, in two launches with a
+// thread per block (bbase: first global block of each instance):
+//  part 1: W = A V over the block's d rows (= Y + V; Y is zero in the first,
+//          orthonormalising pass), Y cleared, and the float64 Gram partials
+//          W^T W and V^T W summed per instance (segmented warp sums, atomics);
+//          the lane that completes an instance forms R^{-1} from the Cholesky
+//          of W^T W and keeps H = V^T W;
+//  part 2: V_new = W R^{-1} and the residual ||W - V H||^2, summed per
+//          instance; the completing lane takes the relative residual and the
+//          stop decision (convergence or the pass cap moves the instance to
+//          PHASE_POLAR, the orthonormalising pass to PHASE_SPEC).
+// Basis buffers: pass s (spec_iters = s) reads V = X[(s + 1) & 1] and writes
+// X[s & 1]; the orthonormalising pass reads X[0] and writes X[1].
+template <int D>
+__device__ __forceinline__ void spec_buffers(const BatchDesc& d, int ph, const float*& V, float*& Vn) {
+  const int si = d.ctl->spec_iters;
+  if (ph == PHASE_SPEC0) {
+    V = d.X[0];
+    Vn = d.X[1];
+  } else {
+    V = d.X[(si + 1) & 1];
+    Vn = d.X[si & 1];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) batch_spec_gram_kernel(const BatchDesc* descs, const long long* bbase, int cnt,
+                                                              const int* nspec) {
+  constexpr int DD = D * D;
+  __shared__ int s_range[2];
+  if (*nspec == 0) return;  // no instance in a spectral pass (uniform)
+  const int lane = threadIdx.x & 31;
+  const long long total = bbase[cnt];
+  for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    const int inst = chunk_instance(bbase, cnt, g0, total, g, s_range);
+    const int ph = inst >= 0 ? descs[inst].ctl->phase : (int)PHASE_IDLE;
+    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0;
+    double ww[DD], vw[DD];
+#pragma unroll
+    for (int o = 0; o < DD; ++o) ww[o] = vw[o] = 0.0;
+    if (act) {
+      const BatchDesc& d = descs[inst];
+      const float* V;
+      float* Vn;
+      spec_buffers<D>(d, ph, V, Vn);
+      const long long r0 = (g - bbase[inst]) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float v[D], w[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const long long e = (r0 + k) * D + c;
+          v[c] = V[e];
+          w[c] = d.Y[e] + v[c];
+          d.W[e] = w[c];
+          d.Y[e] = 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            ww[a * D + b] += (double)w[a] * (double)w[b];
+            vw[a * D + b] += (double)v[a] * (double)w[b];
+          }
+      }
+    }
+    const unsigned int m = __match_any_sync(0xffffffffu, act ? inst : -1);
+    const int head = __ffs(m) - 1, tail = 31 - __clz(m);
+#pragma unroll
+    for (int o = 0; o < DD; ++o) {
+      ww[o] = seg_sum(ww[o], lane, head);
+      vw[o] = seg_sum(vw[o], lane, head);
+    }
+    if (act && lane == tail) {
+      const BatchDesc& d = descs[inst];
+      Ctl* c = d.ctl;
+      double* scr = d.scr;
+#pragma unroll
+      for (int o = 0; o < DD; ++o) {
+        atomicAdd(&scr[kScrWW + o], ww[o]);
+        atomicAdd(&scr[kScrVW + o], vw[o]);
+      }
+      __threadfence();
+      const unsigned int k = (unsigned int)__popc(m);
+      if (atomicAdd(&c->counter, k) + k == (unsigned int)d.g.n) {
+        __threadfence();
+        double G[DD], R[DD], Rt[DD], h2 = 0.0;
+#pragma unroll
+        for (int o = 0; o < DD; ++o) {
+          G[o] = atomicAdd(&scr[kScrWW + o], 0.0);
+          const double h = atomicAdd(&scr[kScrVW + o], 0.0);
+          scr[kScrH + o] = h;
+          h2 += h * h;
+          scr[kScrWW + o] = 0.0;
+          scr[kScrVW + o] = 0.0;
+        }
+        chol_inv(G, R, D, Rt);
+#pragma unroll
+        for (int o = 0; o < DD; ++o) scr[kScrRinv + o] = R[o];
+        scr[kScrH2] = h2;
+        c->counter = 0u;
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) batch_spec_update_kernel(const BatchDesc* descs, const long long* bbase,
+                                                                int cnt, int* nspec) {
+  constexpr int DD = D * D;
+  __shared__ int s_range[2];
+  if (*nspec == 0) return;  // no instance in a spectral pass (uniform)
+  const int lane = threadIdx.x & 31;
+  const long long total = bbase[cnt];
+  for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    const int inst = chunk_instance(bbase, cnt, g0, total, g, s_range);
+    const int ph = inst >= 0 ? descs[inst].ctl->phase : (int)PHASE_IDLE;
+    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0;
+    double res = 0.0;
+    if (act) {
+      const BatchDesc& d = descs[inst];
+      const float* V;
+      float* Vn;
+      spec_buffers<D>(d, ph, V, Vn);
+      double rinv[DD], hh[DD];
+#pragma unroll
+      for (int o = 0; o < DD; ++o) {
+        rinv[o] = d.scr[kScrRinv + o];
+        hh[o] = d.scr[kScrH + o];
+      }
+      const long long r0 = (g - bbase[inst]) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        double v[D], w[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          v[c] = V[(r0 + k) * D + c];
+          w[c] = d.W[(r0 + k) * D + c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          double nv = 0.0, vh = 0.0;
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            nv += w[q] * rinv[q * D + c];
+            vh += v[q] * hh[q * D + c];
+          }
+          Vn[(r0 + k) * D + c] = (float)nv;
+          const double e = w[c] - vh;
+          res += e * e;
+        }
+      }
+    }
+    const unsigned int m = __match_any_sync(0xffffffffu, act ? inst : -1);
+    const int head = __ffs(m) - 1, tail = 31 - __clz(m);
+    res = seg_sum(res, lane, head);
+    if (act && lane == tail) {
+      const BatchDesc& d = descs[inst];
+      Ctl* c = d.ctl;
+      atomicAdd(&d.scr[kScrRes], res);
+      __threadfence();
+      const unsigned int k = (unsigned int)__popc(m);
+      if (atomicAdd(&c->counter, k) + k == (unsigned int)d.g.n) {
+        __threadfence();
+        const double tot = atomicAdd(&d.scr[kScrRes], 0.0);
+        d.scr[kScrRes] = 0.0;
+        if (ph == PHASE_SPEC0) {
+          c->phase = PHASE_SPEC;
+        } else {
+          const int si = c->spec_iters;
+          const double rel = sqrt(tot / fmax(d.scr[kScrH2], 1e-300));
+          c->spec_res = rel;
+          c->spec_iters = si + 1;
+          if (rel <= d.spec_tol) c->spec_stop = 1;
+          if (rel <= d.spec_tol || si + 1 >= d.smax) {
+            c->phase = PHASE_POLAR;
+            atomicSub(nspec, 1);
+          }
+        }
+        c->counter = 0u;
+      }
+    }
   }
 }
 
@@ -229,15 +347,13 @@ __global__ void __launch_bounds__(256) batch_phase_kernel(const BatchDesc* descs
 template <int D>
 __global__ void __launch_bounds__(256) batch_block_kernel(const BatchDesc* descs, const long long* bbase, int cnt) {
   constexpr int DD = D * D;
+  __shared__ int s_range[2];
   const int lane = threadIdx.x & 31;
   const long long total = bbase[cnt];
   for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
     const long long g = g0 + threadIdx.x;
-    int inst = -1, ph = PHASE_IDLE;
-    if (g < total) {
-      inst = find_first_leq(bbase, cnt, g);
-      ph = descs[inst].ctl->phase;
-    }
+    const int inst = chunk_instance(bbase, cnt, g0, total, g, s_range);
+    const int ph = inst >= 0 ? descs[inst].ctl->phase : (int)PHASE_IDLE;
     const bool act = ph == PHASE_ITER || ph == PHASE_POLAR;
     double part = 0.0;
     if (act) {
@@ -270,14 +386,9 @@ __global__ void __launch_bounds__(256) batch_block_kernel(const BatchDesc* descs
           }
       }
     }
-    // segmented inclusive scan over the lanes of this warp's instance groups
     const unsigned int m = __match_any_sync(0xffffffffu, act ? inst : -1);
     const int head = __ffs(m) - 1, tail = 31 - __clz(m);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double t = __shfl_up_sync(0xffffffffu, part, o);
-      if (lane - o >= head) part += t;
-    }
+    part = seg_sum(part, lane, head);
     if (act && lane == tail) {
       Ctl* c = descs[inst].ctl;
       const BatchDesc& d = descs[inst];
@@ -321,8 +432,9 @@ __global__ void batch_report_kernel(const BatchDesc* descs, int count, BatchRepo
 }
 
 // Marks every instance of the table as admitted (start of a batch solve).
-__global__ void batch_reset_kernel(const BatchDesc* descs, int count) {
+__global__ void batch_reset_kernel(const BatchDesc* descs, int count, int* nspec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *nspec = 0;
   if (i >= count) return;
   Ctl* c = descs[i].ctl;
   c->phase = PHASE_ADMIT;
@@ -420,15 +532,20 @@ cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int coun
     default: return cudaErrorInvalidValue; \
   }
 
-cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st) {
-#define L(DD) batch_admit_kernel<DD><<<count, 256, 0, st>>>(descs)
+cudaError_t batch_admit(const BatchDesc* descs, int count, int d, int* nspec, cudaStream_t st) {
+#define L(DD) batch_admit_kernel<DD><<<count, 256, 0, st>>>(descs, nspec)
   NSRGS_BATCH_D(d, L)
 #undef L
   return cudaGetLastError();
 }
 
-cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t st) {
-#define L(DD) batch_phase_kernel<DD><<<count, 256, 0, st>>>(descs)
+cudaError_t batch_spec(const BatchDesc* descs, const long long* bbase, int count, int d, long long total_blocks,
+                       int* nspec, cudaStream_t st) {
+  const long long g = std::max<long long>(1, std::min<long long>((total_blocks + 255) / 256, 4LL * num_sms()));
+#define L(DD)                                                                              \
+  batch_spec_gram_kernel<DD><<<(unsigned)g, 256, 0, st>>>(descs, bbase, count, nspec);    \
+  if (cudaPeekAtLastError() == cudaSuccess)                                                \
+    batch_spec_update_kernel<DD><<<(unsigned)g, 256, 0, st>>>(descs, bbase, count, nspec);
   NSRGS_BATCH_D(d, L)
 #undef L
   return cudaGetLastError();
@@ -448,33 +565,35 @@ cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cu
   return cudaGetLastError();
 }
 
-cudaError_t batch_reset(const BatchDesc* descs, int count, cudaStream_t st) {
-  batch_reset_kernel<<<(count + 127) / 128, 128, 0, st>>>(descs, count);
+cudaError_t batch_reset(const BatchDesc* descs, int count, int* nspec, cudaStream_t st) {
+  batch_reset_kernel<<<(count + 127) / 128, 128, 0, st>>>(descs, count, nspec);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ host layout
 size_t batch_instance_bytes(int n, int d) {
   const size_t vec = ((size_t)xpad_rows(n, d) * d * sizeof(float) + 255) / 256 * 256;
-  return 256 + 4 * vec;
+  return 256 + kScrBytes + 4 * vec;
 }
 
 // Table region: descriptors | panel step bases | reports | block-sparse row bases |
-// block bases.
+// block bases | counters (256 bytes: instances in a spectral phase).
 size_t batch_table_bytes(int count) {
   const size_t t = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
   const size_t b = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
   const size_t r = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
-  return t + 3 * b + r;
+  return t + 3 * b + r + 256;
 }
 
 void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d) {
   const size_t vec = ((size_t)xpad_rows(n, d) * d * sizeof(float) + 255) / 256 * 256;
   ds.ctl = reinterpret_cast<Ctl*>(region);
-  ds.X[0] = reinterpret_cast<float*>(region + 256);
-  ds.X[1] = reinterpret_cast<float*>(region + 256 + vec);
-  ds.Y = reinterpret_cast<float*>(region + 256 + 2 * vec);
-  ds.W = reinterpret_cast<float*>(region + 256 + 3 * vec);
+  ds.scr = reinterpret_cast<double*>(region + 256);
+  uint8_t* v = region + 256 + kScrBytes;
+  ds.X[0] = reinterpret_cast<float*>(v);
+  ds.X[1] = reinterpret_cast<float*>(v + vec);
+  ds.Y = reinterpret_cast<float*>(v + 2 * vec);
+  ds.W = reinterpret_cast<float*>(v + 3 * vec);
 }
 
 }  // namespace nsrgs
@@ -555,6 +674,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   const size_t rbytes = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
   long long* d_rbase = reinterpret_cast<long long*>(base + tbytes + bbytes + rbytes);
   long long* d_bbase = reinterpret_cast<long long*>(base + tbytes + 2 * bbytes + rbytes);
+  int* d_nspec = reinterpret_cast<int*>(base + tbytes + 3 * bbytes + rbytes);
   std::vector<BatchDesc> descs(count);
   std::vector<long long> bases(count + 1), rbases(count + 1), bbases(count + 1);
   size_t off = batch_table_bytes(count);
@@ -625,13 +745,13 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     if (!g_bcap[dev]) NSRGS_CUDA_TRY(cudaStreamCreateWithFlags(&g_bcap[dev], cudaStreamNonBlocking));
     cudaStream_t cs = g_bcap[dev];
     NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = batch_reset(d_descs, count, cs);
-    if (e == cudaSuccess) e = batch_admit(d_descs, count, d, cs);
-    const int ticks = (init ? spectral_max_iters : 0) + T;
+    cudaError_t e = batch_reset(d_descs, count, d_nspec, cs);
+    if (e == cudaSuccess) e = batch_admit(d_descs, count, d, d_nspec, cs);
+    const int ticks = (init ? spectral_max_iters + 1 : 0) + T;  // + the orthonormalising pass
     for (int t = 0; t < ticks && e == cudaSuccess; ++t) {
       e = sparse ? batch_bcsr_stream(d_descs, d_rbase, count, d, storage == NSRGS_BCSR_BF16, rows, cs)
                  : batch_stream(d_descs, d_base, count, d, storage, cs, false);
-      if (e == cudaSuccess) e = batch_phase(d_descs, count, d, cs);
+      if (e == cudaSuccess) e = batch_spec(d_descs, d_bbase, count, d, blocks, d_nspec, cs);
       if (e == cudaSuccess) e = batch_block(d_descs, d_bbase, count, d, blocks, cs);
     }
     if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);

@@ -9,6 +9,17 @@ namespace nsrgs {
 // Phase of a batched / served instance after its spectral passes: the blocks of
 // its basis are turned into X^0 (extends the PHASE_* values of the control block).
 constexpr int PHASE_POLAR = 5;
+// First, orthonormalising spectral pass (W = V^0, no A-stream), after admission.
+constexpr int PHASE_SPEC0 = 6;
+
+// Per-instance float64 scratch of the spectral passes (doubles, D <= 4).
+constexpr int kScrWW = 0;     // W^T W accumulator, D x D
+constexpr int kScrVW = 16;    // V^T W accumulator, D x D
+constexpr int kScrRinv = 32;  // R^{-1} of the Cholesky of W^T W
+constexpr int kScrH = 48;     // H = V^T W
+constexpr int kScrH2 = 64;    // ||H||_F^2
+constexpr int kScrRes = 65;   // residual accumulator
+constexpr int kScrBytes = 1024;
 
 struct BatchDesc {
   const uint8_t* packed;  // packed A (panel layout)
@@ -16,6 +27,7 @@ struct BatchDesc {
   float* Y;               // A-stream accumulator, padded
   float* W;               // spectral scratch, padded
   Ctl* ctl;               // control block: phase, counters, flags
+  double* scr;            // spectral-pass scratch (kScr* offsets)
   float* Xout;            // caller's X: X^0 when start_given, the result when done
   PanelGeom g;
   float eta;
@@ -47,11 +59,12 @@ cudaError_t batch_bcsr_stream(const BatchDesc* descs, const long long* rbase, in
                               long long total_rows, cudaStream_t st);
 cudaError_t batch_stream(const BatchDesc* descs, const long long* base, int count, int d, int storage,
                          cudaStream_t st, bool prepare);
-cudaError_t batch_admit(const BatchDesc* descs, int count, int d, cudaStream_t st);
-cudaError_t batch_phase(const BatchDesc* descs, int count, int d, cudaStream_t st);
+cudaError_t batch_admit(const BatchDesc* descs, int count, int d, int* nspec, cudaStream_t st);
+cudaError_t batch_spec(const BatchDesc* descs, const long long* bbase, int count, int d, long long total_blocks,
+                       int* nspec, cudaStream_t st);
 cudaError_t batch_block(const BatchDesc* descs, const long long* bbase, int count, int d, long long total_blocks,
                         cudaStream_t st);
 cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st);
-cudaError_t batch_reset(const BatchDesc* descs, int count, cudaStream_t st);
+cudaError_t batch_reset(const BatchDesc* descs, int count, int* nspec, cudaStream_t st);
 
 }  // namespace nsrgs

@@ -112,6 +112,7 @@ struct nsrgs_server {
   long long* d_base = nullptr;
   long long* d_rbase = nullptr;  // first global row of each slot's block-sparse rows
   long long* d_bbase = nullptr;  // first global block of each slot
+  int* d_nspec = nullptr;        // slots in a spectral phase
   BatchReport* d_rep = nullptr;
   std::vector<BatchDesc> h_descs;
   std::vector<Ctl*> idle_ctl;  // per slot: zeroed control block used while the slot is free
@@ -163,6 +164,7 @@ extern "C" nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void
   const size_t rbytes = ((size_t)M * sizeof(BatchReport) + 255) / 256 * 256;
   s->d_rbase = reinterpret_cast<long long*>(s->arena + tbytes + bbytes + rbytes);
   s->d_bbase = reinterpret_cast<long long*>(s->arena + tbytes + 2 * bbytes + rbytes);
+  s->d_nspec = reinterpret_cast<int*>(s->arena + tbytes + 3 * bbytes + rbytes);
   s->h_descs.assign(M, BatchDesc{});
   s->h_base.assign(M + 1, 0);
   s->h_rbase.assign(M + 1, 0);
@@ -185,6 +187,7 @@ extern "C" nsrgs_status nsrgs_server_create(const nsrgs_server_config* cfg, void
     s->h_descs[i].ctl = s->idle_ctl[i];
   }
   cudaError_t e = cudaMemsetAsync(s->arena + ctl_off, 0, 256 * (size_t)M, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_nspec, 0, sizeof(int), s->st);
   if (e == cudaSuccess) e = batch_stream(nullptr, nullptr, 0, cfg->d, cfg->storage, s->st, true);
   if (e != cudaSuccess) {
     delete s;
@@ -233,13 +236,13 @@ static cudaError_t server_capture(nsrgs_server* s) {
   if (e != cudaSuccess) return e;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    e = batch_admit(s->d_descs, M, d, cs);
+    e = batch_admit(s->d_descs, M, d, s->d_nspec, cs);
     for (int t = 0; t < s->cfg.ticks_per_step && e == cudaSuccess; ++t) {
       e = batch_stream(s->d_descs, s->d_base, M, d, s->cfg.storage, cs, false);
       // block-sparse slots (none: the row kernel finds no rows and returns)
       if (e == cudaSuccess)
         e = batch_bcsr_stream(s->d_descs, s->d_rbase, M, d, sparse_storage(s) == NSRGS_BCSR_BF16, 1LL << 40, cs);
-      if (e == cudaSuccess) e = batch_phase(s->d_descs, M, d, cs);
+      if (e == cudaSuccess) e = batch_spec(s->d_descs, s->d_bbase, M, d, 1LL << 40, s->d_nspec, cs);
       // grid sized for a full table; blocks past the current total return at once
       if (e == cudaSuccess) e = batch_block(s->d_descs, s->d_bbase, M, d, 1LL << 40, cs);
     }
