@@ -501,6 +501,22 @@ def serving_leg(P, synth, seed: int, rate: float = 200.0, duration: float = 10.0
         "block_sparse_requests_in_pool": sum(1 for q in pool if q.get("use_bcsr", False)),
         "all_panels": simulate(False),
     }
+    # the update norm's float32 noise floor against the 1e-6 retire tolerance: a
+    # dense n = 8000, d = 3 instance, last update norm after T iterations (tol = 0)
+    _, up8 = synth.device_upper(8000, 3, synth.sigma_rule(0.3, 8000, 3), seed=seed + 7)
+    floor = {}
+    for name, st in (("f32", P.F32), ("bf16", P.BF16)):
+        pk = P.nsrgs_pack_upper(up8, 8000, 3, st)
+        ws8 = P.workspace(8000, 3)
+        floor[name] = {}
+        for Tf in (100, 200, 400, 800):
+            _, inf = P.nsrgs_solve(pk, 1.0 / 8000, Tf, 2, spectral_max_iters=SMAX, ws=ws8)
+            floor[name][str(Tf)] = inf.last_update_norm
+        del pk, ws8
+    del up8
+    torch.cuda.empty_cache()
+    res["update_norm_after_T"] = {"instance": "dense n=8000 d=3 c=0.3, eta=1/n, K=2, from the spectral start",
+                                  **floor}
     # plain sequential FP32 form: one request at a time (single-instance solve), same arrivals
     solve_s = {}
     for k, q in enumerate(pool):
