@@ -61,6 +61,13 @@ __all__ = [
     "newton_schulz_rows",
     "polar_rows",
     "stiefel_iteration",
+    "se_residuals",
+    "se_objective",
+    "se_gradient",
+    "se_iteration",
+    "se_update_norm",
+    "se_nsrgs",
+    "se_errors",
     "blocks",
     "stack",
 ]
@@ -392,3 +399,99 @@ def stiefel_iteration(A: np.ndarray, X: np.ndarray, n: int, d: int, mu: float, T
     G = stiefel_gradient(A, X, n, d)
     F = Xb - mu * stiefel_projection(Xb, G)
     return newton_schulz_rows(F, Ts).reshape(n * d, -1)
+
+
+# ------------------------- beyond the paper: SE(d) form (poses = rotation + translation)
+# §6 names the special Euclidean group as a target for the Newton-Schulz retraction
+# without writing a method for it; this is the reading the repository builds.
+# Unknowns: X_i in O(d) (as in the paper) and t_i in R^d.  Measurements for an
+# observed pair i < j (mask w_ij in {0, 1}): A_ij ~ X_i X_j^T (the paper's model) and
+# c_ij ~ X_i (t_j - t_i), the translation from i to j in the frame of i.  Objective
+#     f(X, t) = F(X) + kappa sum_{i<j} w_ij ||t_j - t_i - X_i^T c_ij||^2
+# with F of eq. (1).  One iteration from (X^t, t^t), all blocks at once:
+#     G^X_i = sum_{j != i}(X_i - A_ij X_j) - kappa sum_{j>i} w_ij c_ij (t_j - t_i)^T
+#     G^t_k = kappa [sum_{i<k} w_ik r_ik - sum_{j>k} w_kj r_kj],  r_ij = t_j - t_i - X_i^T c_ij
+#     X_i <- S_K(X_i - mu P_{X_i}(G^X_i))  (Algorithm 1),   t_k <- t_k - mu_t G^t_k.
+# G^X and G^t are half the Euclidean gradient of f, like Algorithm 2's G, with the same
+# simplification on the manifold: Algorithm 2 uses X_j^T X_j = I, and here the term
+# kappa sum_j w_ij c_ij c_ij^T X_i is dropped, whose projection P_{X_i} vanishes when
+# X_i is orthogonal (P(M X) = 0 for symmetric M).  G^t is the exact half-gradient.
+def se_residuals(Cu: np.ndarray, X: np.ndarray, t: np.ndarray, n: int, d: int) -> np.ndarray:
+    """r_ij = t_j - t_i - X_i^T c_ij for every ordered i < j, as an (n, n, d) array (zero elsewhere)."""
+    Xb = blocks(X, d)
+    t = np.asarray(t, dtype=np.float64).reshape(n, d)
+    R = np.zeros((n, n, d))
+    for i in range(n - 1):
+        c = np.asarray(Cu[i, i + 1 :], dtype=np.float64)  # (m, d)
+        R[i, i + 1 :] = t[i + 1 :] - t[i][None, :] - c @ Xb[i]  # (X_i^T c)^T = c^T X_i
+    return R
+
+
+def se_objective(A, Cu, Wm, X, t, n: int, d: int, kappa: float) -> float:
+    """f(X, t) = F(X) + kappa sum_{i<j} w_ij ||t_j - t_i - X_i^T c_ij||^2."""
+    R = se_residuals(Cu, X, t, n, d)
+    W = np.triu(np.asarray(Wm, dtype=np.float64), 1)
+    return objective(A, X, n, d) + kappa * float(np.sum(W[:, :, None] * R * R))
+
+
+def se_gradient(A, Cu, Wm, X, t, n: int, d: int, kappa: float):
+    """(G^X as (n, d, d), G^t as (n, d)) of the SE(d) reading, from the pair sums written out."""
+    Xb = blocks(X, d)
+    t = np.asarray(t, dtype=np.float64).reshape(n, d)
+    W = np.triu(np.asarray(Wm, dtype=np.float64), 1)
+    GX = euclidean_gradient(A, X, n, d)
+    Gt = np.zeros((n, d))
+    R = se_residuals(Cu, X, t, n, d)
+    for i in range(n - 1):
+        for j in range(i + 1, n):
+            if W[i, j] == 0.0:
+                continue
+            c = np.asarray(Cu[i, j], dtype=np.float64)
+            GX[i] -= kappa * np.outer(c, t[j] - t[i])
+            Gt[j] += kappa * R[i, j]
+            Gt[i] -= kappa * R[i, j]
+    return GX, Gt
+
+
+def se_iteration(A, Cu, Wm, X, t, n: int, d: int, mu: float, mu_t: float, kappa: float, Ts: int):
+    """One iteration of the SE(d) form for all blocks from (X^t, t^t): (X^{t+1} nd x d, t^{t+1} (n, d))."""
+    Xb = blocks(X, d)
+    GX, Gt = se_gradient(A, Cu, Wm, X, t, n, d, kappa)
+    F = Xb - mu * tangent_projection(Xb, GX)
+    tn = np.asarray(t, dtype=np.float64).reshape(n, d) - mu_t * Gt
+    return stack(newton_schulz(F, Ts)), tn
+
+
+def se_update_norm(Xn, X, tn, t, n: int, d: int) -> float:
+    """sqrt((||X' - X||_F^2 + ||t' - t||^2) / (n d)), the update norm of the SE(d) form."""
+    dx = np.asarray(Xn, dtype=np.float64) - np.asarray(X, dtype=np.float64)
+    dt = np.asarray(tn, dtype=np.float64) - np.asarray(t, dtype=np.float64)
+    return math.sqrt((float(np.sum(dx * dx)) + float(np.sum(dt * dt))) / (n * d))
+
+
+def se_nsrgs(A, Cu, Wm, n: int, d: int, mu: float, mu_t: float, kappa: float, T: int, Ts: int, X0, t0,
+             tol: float = 0.0):
+    """T iterations of the SE(d) form from (X0, t0); with tol > 0, stops after the first
+    iteration whose update norm is below tol.  Returns (X, t, iterations run)."""
+    X = np.asarray(X0, dtype=np.float64)
+    t = np.asarray(t0, dtype=np.float64).reshape(n, d)
+    it = 0
+    for _ in range(T):
+        Xn, tn = se_iteration(A, Cu, Wm, X, t, n, d, mu, mu_t, kappa, Ts)
+        un = se_update_norm(Xn, X, tn, t, n, d)
+        X, t, it = Xn, tn, it + 1
+        if tol > 0.0 and un < tol:
+            break
+    return X, t, it
+
+
+def se_errors(X, t, Z, tau, n: int, d: int) -> tuple[float, float]:
+    """(d_F(X, Z), translation RMS error) after the global gauge X -> X Q, t -> Q^T t + v:
+    Q minimises ||X - Z Q||_F (as in d_F), v is the mean offset."""
+    X = np.asarray(X, dtype=np.float64)
+    Zs = np.asarray(Z, dtype=np.float64).reshape(n * d, d)
+    U, _, Vt = np.linalg.svd(Zs.T @ X)
+    Q = U @ Vt
+    e = np.asarray(t, dtype=np.float64).reshape(n, d) - np.asarray(tau, dtype=np.float64).reshape(n, d) @ Q
+    e -= e.mean(axis=0, keepdims=True)
+    return dF(X, Zs, d), math.sqrt(float(np.sum(e * e)) / n)

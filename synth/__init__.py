@@ -47,6 +47,9 @@ __all__ = [
     "block_row",
     "Instance",
     "make_instance",
+    "SEInstance",
+    "make_se_instance",
+    "device_se",
 ]
 
 
@@ -188,3 +191,75 @@ def make_instance(n: int, d: int, sigma: float, seed: int, p: float = 1.0, dtype
     Z = haar_orthogonal(rng, n, d)
     up = upper_blocks(Z, sigma, rng, p=p, dtype=dtype)
     return Instance(n=n, d=d, sigma=float(sigma), p=float(p), seed=int(seed), Z=Z, upper=up)
+
+
+@dataclass
+class SEInstance:
+    """Poses (Z_i, tau_i) and measurements of the SE(d) form.
+
+    ``rot`` is the rotation instance (exactly ``make_instance`` with the same
+    arguments); ``tau`` (n, d) are the true translations; ``c_upper``
+    (n(n-1)/2, d) holds c_ij = Z_i (tau_j - tau_i) + sigma_t w_ij for i < j in
+    the canonical upper order (zero for an unobserved pair); ``mask_upper``
+    (n(n-1)/2,) is 1 for an observed pair.
+    """
+
+    rot: Instance
+    sigma_t: float
+    tau: np.ndarray
+    c_upper: np.ndarray
+    mask_upper: np.ndarray
+
+    def c_square(self) -> np.ndarray:
+        """c as an (n, n, d) float64 array with c[i, j] = c_ij for i < j, zero elsewhere."""
+        n, d = self.rot.n, self.rot.d
+        out = np.zeros((n, n, d))
+        iu, ju = np.triu_indices(n, 1)
+        out[iu, ju] = self.c_upper
+        return out
+
+    def mask_square(self) -> np.ndarray:
+        """Symmetric (n, n) 0/1 observation mask (diagonal 0)."""
+        n = self.rot.n
+        m = np.zeros((n, n))
+        iu, ju = np.triu_indices(n, 1)
+        m[iu, ju] = self.mask_upper
+        return m + m.T
+
+
+def make_se_instance(n: int, d: int, sigma: float, sigma_t: float, seed: int, p: float = 1.0,
+                     dtype=np.float64) -> SEInstance:
+    """Rotation part from ``make_instance(n, d, sigma, seed, p)``; translations from a
+    second generator PCG64([seed, 1]): first tau (n*d normals), then the translation
+    noise w_ij (n(n-1)/2 * d normals, canonical upper order).  An unobserved pair
+    (zero rotation block) has c_ij = 0 and mask 0."""
+    rot = make_instance(n, d, sigma, seed, p=p, dtype=dtype)
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    tau = rng.standard_normal((n, d))
+    w = rng.standard_normal((num_upper_blocks(n), d))
+    iu, ju = np.triu_indices(n, 1)
+    c = np.einsum("kab,kb->ka", rot.Z[iu], tau[ju] - tau[iu]) + sigma_t * w
+    mask = np.any(np.asarray(rot.upper) != 0, axis=(1, 2)).astype(np.float64)
+    c *= mask[:, None]
+    return SEInstance(rot=rot, sigma_t=float(sigma_t), tau=tau, c_upper=c.astype(dtype), mask_upper=mask)
+
+
+def device_se(n: int, d: int, sigma: float, sigma_t: float, seed: int, device="cuda"):
+    """The SE(d) measurement model generated on a GPU (complete graph), for workloads
+    too large to build on the host: returns (Z, tau, A upper-block list, c upper list)
+    as float32 torch tensors.  Rotation part as ``device_upper``; no oracle comparison."""
+    import torch
+
+    Z, up = device_upper(n, d, sigma, seed, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + 1)
+    tau = torch.randn((n, d), generator=g, device=device, dtype=torch.float32)
+    iu, ju = torch.triu_indices(n, n, offset=1, device=device)
+    nb = iu.numel()
+    c = torch.empty((nb, d), dtype=torch.float32, device=device)
+    chunk = 1 << 22
+    for s in range(0, nb, chunk):
+        e = min(nb, s + chunk)
+        c[s:e] = torch.einsum("kab,kb->ka", Z[iu[s:e]], tau[ju[s:e]] - tau[iu[s:e]])
+        c[s:e] += sigma_t * torch.randn((e - s, d), generator=g, device=device, dtype=torch.float32)
+    return Z, tau, up, c
