@@ -209,6 +209,24 @@ nsrgs_status nsrgs_solve(const nsrgs_A* A, float eta, int T, int K, double tol, 
                          int spectral_max_iters, float* X, nsrgs_info* info, void* ws,
                          size_t ws_bytes, void* st);
 
+/* nsrgs_solve for a packed A and an iterate held in host memory: one call that
+ * copies the packed bytes (`packed_host`, `packed_bytes`, laid out as the
+ * packers write them: e.g. a host copy of a packed device buffer) into the
+ * caller's device buffer A->packed, copies X^0 from X_host into the device
+ * buffer X when `init` == 0, runs the solve (Algorithm 2, arguments as
+ * nsrgs_solve), copies the final iterate from X to X_host (nd x d float32) and
+ * synchronises `st`.  packed_bytes must equal nsrgs_packed_bytes(n, d, storage)
+ * for the panel, tile and dense layouts and, for block-sparse rows, the size
+ * that the header in packed_host implies (its n and d must match A).  Host
+ * buffers in page-locked memory copy asynchronously at the link's rate;
+ * pageable ones are staged by the CUDA runtime.  The library keeps no pointer
+ * to either host buffer after the call returns.  Errors: NSRGS_ERR_INVALID_ARG
+ * for a size or header mismatch or null pointers (nothing is copied), otherwise
+ * those of nsrgs_solve; X_host is written only on success. */
+nsrgs_status nsrgs_solve_host(const nsrgs_A* A, const void* packed_host, size_t packed_bytes, float eta,
+                              int T, int K, double tol, int init, int spectral_max_iters, float* X,
+                              float* X_host, nsrgs_info* info, void* ws, size_t ws_bytes, void* st);
+
 /* The least-squares objective of eq. (1) at X (device, nd x d):
  *   F(X) = 1/2 sum_{i != j} ||X_i X_j^T - A_ij||_F^2,
  * with A the stored (packed) matrix.  Evaluated as

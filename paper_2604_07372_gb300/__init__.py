@@ -28,6 +28,7 @@ from ._lib import (  # noqa: F401
     nsrgs_spectral_init,
     nsrgs_step,
     nsrgs_solve,
+    nsrgs_solve_host,
     nsrgs_solve_objective,
     nsrgs_solve_ex,
     SolveOpts,

@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         "nsrgs_step": (i, [Ap, f, i, vp, vp, vp, vp, sz, vp]),
         "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_solve_objective": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
+        "nsrgs_solve_host": (i, [Ap, vp, sz, f, i, i, d, i, i, vp, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_objective": (i, [Ap, vp, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_solve_ex": (i, [Ap, f, i, i, vp, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
@@ -261,6 +262,55 @@ def nsrgs_solve(
         )
     )
     return X, inf
+
+
+def nsrgs_solve_host(
+    A: PackedA,
+    packed_host: torch.Tensor,
+    X_host: torch.Tensor,
+    eta: float,
+    T: int,
+    K: int,
+    tol: float = 0.0,
+    init: bool = True,
+    spectral_max_iters: int = 50,
+    X: torch.Tensor | None = None,
+    ws=None,
+    info: bool = True,
+):
+    """nsrgs_solve with the packed A and the iterate in host memory: the library
+    copies packed_host (uint8, CPU) into A.buf, solves, and writes the final
+    iterate into X_host (float32 CPU, nd x d); returns (X_host, Info or None)."""
+    for t, name in ((packed_host, "packed_host"), (X_host, "X_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor")
+    if X_host.dtype != torch.float32 or X_host.numel() != A.n * A.d * A.d:
+        raise ValueError("X_host must be float32 with n*d*d elements")
+    if X is None:
+        X = torch.empty(A.n * A.d, A.d, dtype=torch.float32, device=A.buf.device)
+    w = _ws(A, ws)
+    a = A.struct()
+    inf = Info() if info else None
+    _check(
+        lib().nsrgs_solve_host(
+            ctypes.byref(a),
+            ctypes.c_void_p(packed_host.data_ptr()),
+            packed_host.numel() * packed_host.element_size(),
+            eta,
+            T,
+            K,
+            tol,
+            1 if init else 0,
+            spectral_max_iters,
+            _ptr(X),
+            ctypes.c_void_p(X_host.data_ptr()),
+            ctypes.byref(inf) if inf is not None else None,
+            _ptr(w),
+            w.numel(),
+            _stream(),
+        )
+    )
+    return X_host, inf
 
 
 def nsrgs_solve_objective(

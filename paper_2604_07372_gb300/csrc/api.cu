@@ -520,6 +520,42 @@ nsrgs_status nsrgs_solve_ex(const nsrgs_A* A, float eta, int T, int K, const nsr
                     opts->ns_safeguard ? 1 : 0);
 }
 
+nsrgs_status nsrgs_solve_host(const nsrgs_A* A, const void* packed_host, size_t packed_bytes, float eta, int T,
+                              int K, double tol, int init, int spectral_max_iters, float* X, float* X_host,
+                              nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  NSRGS_CHECK_ARG(A != nullptr && A->packed != nullptr, "A and A->packed must be non-null");
+  NSRGS_CHECK_ARG(packed_host && X_host, "packed_host and X_host must be non-null host pointers");
+  nsrgs_status s = check_nd(A->n, A->d);
+  if (s != NSRGS_OK) return s;
+  const int n = A->n, d = A->d;
+  // The packed size is fixed by (n, d, storage), except for block-sparse rows,
+  // whose header (n, d, stored blocks) is read from the host copy.
+  size_t want = 0;
+  if (bcsr_storage(A->storage)) {
+    NSRGS_CHECK_ARG(packed_bytes >= 64, "packed_bytes is smaller than the block-sparse header");
+    const long long* hdr = static_cast<const long long*>(packed_host);
+    NSRGS_CHECK_ARG(hdr[0] == n && hdr[1] == d && hdr[2] >= 0 && hdr[2] <= (long long)n * (n - 1),
+                    "the block-sparse header does not match (n, d)");
+    want = d <= 8 ? (size_t)bcsr_bytes(n, d, A->storage, hdr[2]) : 0;
+  } else {
+    want = nsrgs_packed_bytes(n, d, A->storage);
+  }
+  NSRGS_CHECK_ARG(want != 0, "unsupported (n, d, storage)");
+  NSRGS_CHECK_ARG(packed_bytes == want, "packed_bytes differs from the packed size of (n, d, storage)");
+  cudaStream_t st = (cudaStream_t)stv;
+  const size_t xbytes = (size_t)n * d * d * sizeof(float);
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(A->packed), packed_host, packed_bytes, cudaMemcpyHostToDevice, st));
+  if (!init) {
+    NSRGS_CHECK_ARG(X && aligned16(X), "X must be a 16-byte aligned device pointer");
+    NSRGS_CUDA_TRY(cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st));
+  }
+  s = solve_impl(A, eta, T, K, tol, init, spectral_max_iters, X, info, ws, ws_bytes, stv, METHOD_NSRGS);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(X_host, X, xbytes, cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return NSRGS_OK;
+}
+
 nsrgs_status nsrgs_objective(const nsrgs_A* A, const float* X, double* F, void* ws, size_t ws_bytes, void* stv) {
   PanelGeom g{};
   nsrgs_status s = check_A(A, &g);

@@ -69,3 +69,16 @@ def test_bad_arguments_are_rejected_without_a_device(L):
     assert lib.nsrgs_dF(None, None, 10, 3, None, None, 0, None) == 1
     assert lib.nsrgs_pack_upper(None, 10, 3, 0, None, None) == 1
     assert lib.nsrgs_pack_dense(None, 1, 3, 0, None, None) == 1
+    # host-buffer solve: size and header checks come before any copy
+    buf = (ctypes.c_char * 256)()
+    A = L._lib._A(16, 100, 3, 0)
+    assert lib.nsrgs_solve_host(ctypes.byref(A), buf, 256, 0.01, 10, 2, 0.0, 1, 50, None, buf, None, None, 0,
+                                None) == 1
+    assert b"packed_bytes" in lib.nsrgs_last_error()
+    assert lib.nsrgs_solve_host(ctypes.byref(A), None, 256, 0.01, 10, 2, 0.0, 1, 50, None, buf, None, None, 0,
+                                None) == 1
+    hdr = (ctypes.c_longlong * 32)(100, 4, 10)  # block-sparse header for another d
+    A = L._lib._A(16, 100, 3, 5)
+    assert lib.nsrgs_solve_host(ctypes.byref(A), hdr, 256, 0.01, 10, 2, 0.0, 1, 50, None, buf, None, None, 0,
+                                None) == 1
+    assert b"header" in lib.nsrgs_last_error()

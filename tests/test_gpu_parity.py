@@ -142,6 +142,33 @@ def test_solve_from_given_start(P):
     assert O.dF(to64(X), Xo, d) / math.sqrt(n * d) <= 1e-5
 
 
+@pytest.mark.parametrize("storage", ["f32", "bcsr_f32"])
+def test_solve_from_host_buffers(P, storage):
+    """nsrgs_solve_host: packed A and X in (pinned) host memory, one call, same
+    answer as the oracle; from the spectral start and from a given X^0."""
+    n, d, T, K = 200, 3, 40, 2
+    inst = make(n, d, seed=7, p=0.5 if storage == "bcsr_f32" else 1.0)
+    A = inst.dense()
+    Xo, _ = O.nsrgs(A, n, d, 1.0 / n, T, K)
+    pa = packed(P, inst, P.STORAGE[storage])
+    host = torch.empty(pa.nbytes, dtype=torch.uint8, pin_memory=True)
+    host.copy_(pa.buf[: pa.nbytes])
+    torch.cuda.synchronize()
+    pa.buf.zero_()
+    Xh = torch.full((n * d, d), float("nan"), dtype=torch.float32, pin_memory=True)
+    Xh, info = P.nsrgs_solve_host(pa, host, Xh, 1.0 / n, T, K, init=True, spectral_max_iters=80)
+    assert info.iters == T and info.flags == 0, info.as_dict()
+    assert O.dF(Xh.double().numpy(), Xo, d) / math.sqrt(n * d) <= 1e-5
+    X0, _ = O.spectral_init(A, n, d)
+    Xo0, _ = O.nsrgs(A, n, d, 1.0 / n, T, K, X0=X0)
+    Xh = torch.from_numpy(X0.astype(np.float32)).contiguous()
+    Xh, info = P.nsrgs_solve_host(pa, host, Xh, 1.0 / n, T, K, init=False)
+    assert O.dF(Xh.double().numpy(), Xo0, d) / math.sqrt(n * d) <= 1e-5
+    # a host buffer of the wrong size is rejected before anything is copied
+    with pytest.raises(P.NsrgsError):
+        P.nsrgs_solve_host(pa, host[:-16], Xh, 1.0 / n, T, K)
+
+
 def test_sigma_zero_exact_recovery_gpu(P):
     n, d = 200, 3
     inst = synth.make_instance(n, d, 0.0, seed=5, dtype=np.float32)
