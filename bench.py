@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
-    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving", "sparse"],
+    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving", "sparse", "se"],
                     help="run only one extra leg (prints its JSON, no metric line), for profiling")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
@@ -402,6 +402,68 @@ def sparse_leg(P, synth, seed: int, n: int = 8000, d: int = 3, ps=(0.05, 0.2, 0.
         del up, Z
         torch.cuda.empty_cache()
     return {"n": n, "d": d, "T": T, "per_p": out}
+
+
+# ------------------------------------------------------------ SE(d) leg
+def se_leg(P, synth, seed: int, n: int = 10000, d: int = 3, T: int = 100, K: int = 2, c: float = 0.3,
+           sigma_t: float = 0.1):
+    """SE(d) form (poses: rotation + translation), n = 10^4, d = 3, c = 0.3, translation
+    noise 0.1, kappa = 1/(4d), eta = 1/n, eta_t = 1/(kappa n), from the spectral start of
+    the rotation part and t = 0: T iterations streaming the augmented (d+1)-block matrix
+    (FP32 and BF16 panels); per-launch A-stream time with CUDA events around each launch."""
+    import torch
+
+    sigma = synth.sigma_rule(c, n, d)
+    Z, tau, up, cu = synth.device_se(n, d, sigma, sigma_t, seed)
+    Zs = Z.reshape(n * d, d)
+    kappa = 1.0 / (4 * d)
+    eta, eta_t = 1.0 / n, 1.0 / (kappa * n)
+    pa = P.nsrgs_pack_upper(up, n, d, P.F32)
+    X0, _ = P.nsrgs_spectral_init(pa, max_iters=SMAX, strict=False)
+    del pa
+    torch.cuda.empty_cache()
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    out = {"n": n, "d": d, "T": T, "K": K, "kappa": kappa, "sigma_t": sigma_t}
+    for name in ("f32", "bf16"):
+        try:
+            B = P.nsrgs_se_pack(up, cu, n, d, kappa, P.STORAGE[name])
+            ws = torch.empty(int(P.lib().nsrgs_se_workspace_bytes(n, d)), dtype=torch.uint8, device="cuda")
+            X, t = X0.clone(), torch.zeros(n, d, device="cuda")
+            P.nsrgs_se_solve(B, kappa, eta, eta_t, 3, K, X, t, ws=ws)  # warm-up
+            X, t = X0.clone(), torch.zeros(n, d, device="cuda")
+            P.nsrgs_set_kernel_timing(True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, info = P.nsrgs_se_solve(B, kappa, eta, eta_t, T, K, X, t, ws=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            launches, kms, _ = P.nsrgs_kernel_timing()
+            P.nsrgs_set_kernel_timing(False)
+            sec = e0.elapsed_time(e1) / 1e3
+            ab = n * (n - 1) // 2 * (d + 1) ** 2 * {"f32": 4, "bf16": 2}[name]
+            # translation error after the gauge (X -> X Q, t -> Q^T t + v), Q from the rotations
+            U, _, Vh = torch.linalg.svd(Zs.double().T @ X.double())
+            Q = U @ Vh
+            e = t.double() - tau.double() @ Q
+            e -= e.mean(dim=0, keepdim=True)
+            out[name] = {
+                "iters_per_s": T / sec,
+                "packed_GB": B.nbytes / 1e9,
+                "stream_ms": kms,
+                "stream_launches_timed": launches,
+                "stream_GBps": ab / (kms / 1e3) / 1e9,
+                "stream_frac_of_measured_hbm": ab / (kms / 1e3) / 1e9 / hbm,
+                "rot_dF_to_truth": P.nsrgs_dF(X, Zs, n, d),
+                "trans_rms_to_truth": float(torch.sqrt((e * e).sum() / n)),
+                "flags": info.flags,
+            }
+            del B, ws
+        except Exception as e:  # reported, not fatal
+            traceback.print_exc()
+            out[name] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------ serving leg
@@ -801,10 +863,12 @@ def run_ours(args, world, rank, local):
         P.nsrgs_set_kernel_timing(False)
         torch.cuda.empty_cache()
         # batched and served forms (the metric's second half)
-        for key, fn in (("batched", batched_leg), ("serving", serving_leg), ("dimension_sweep", dsweep_leg)):
+        for key, fn in (("batched", batched_leg), ("serving", serving_leg), ("dimension_sweep", dsweep_leg),
+                        ("se_poses", se_leg)):
             try:
                 t = time.perf_counter()
-                line[key] = fn(P, synth, seed=args.seed + {"batched": 1, "serving": 2, "dimension_sweep": 3}[key])
+                line[key] = fn(P, synth, seed=args.seed + {"batched": 1, "serving": 2, "dimension_sweep": 3,
+                                                           "se_poses": 5}[key])
                 line[key]["leg_wall_s"] = time.perf_counter() - t
             except Exception as e:  # reported in the line, the main metric stands
                 traceback.print_exc()
@@ -852,6 +916,8 @@ def main():
             out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps, only=only)
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
+        elif args.leg == "se":
+            out = se_leg(P, synth, seed=args.seed + 5)
         elif args.leg == "sparse":
             out = sparse_leg(P, synth, seed=args.seed + 4, ps=tuple(float(x) for x in args.sparse_ps.split(",")))
         else:

@@ -296,6 +296,54 @@ size_t nsrgs_stiefel_workspace_bytes(int n, int d, int p);
 nsrgs_status nsrgs_stiefel_solve(const nsrgs_A* A, int p, float eta, int T, int K, double tol, const float* X0,
                                  float* X, nsrgs_info* info, void* ws, size_t ws_bytes, void* st);
 
+/* ------------------------------------------------------- SE(d) form
+ * Poses (X_i, t_i), X_i in O(d), t_i in R^d: the special Euclidean group that §6
+ * names as a target of the Newton-Schulz retraction (the paper writes no method
+ * for it; this is the library's reading).  Measurements for pairs i < j: the
+ * rotation blocks A_ij ~ X_i X_j^T of the paper's model and translations
+ * c_ij ~ X_i (t_j - t_i) (from i to j, in the frame of i); a pair is observed
+ * when A_ij has a nonzero entry (unobserved: A_ij = 0, c_ij = 0).  Objective
+ *     f(X, t) = F(X) + kappa sum_{i<j observed} ||t_j - t_i - X_i^T c_ij||^2,
+ * F of eq. (1).  Each iteration, all nodes at once from (X^t, t^t):
+ *     G^X_i = sum_{j != i} (X_i - A_ij X_j) - kappa sum_{j > i} c_ij (t_j - t_i)^T
+ *     G^t_i = kappa [deg_i t_i - sum_{j ~ i} t_j - sum_{j < i} X_j^T c_ji + X_i^T sum_{j > i} c_ij]
+ *     X_i <- S_K(X_i - eta (G^X_i - X_i G^X_i^T X_i) / 2)   (§2.2, Algorithm 1)
+ *     t_i <- t_i - eta_t G^t_i
+ * (half the gradient of f, as Algorithm 2's G; the term kappa sum_j c_ij c_ij^T X_i,
+ * whose tangent projection vanishes on O(d), is dropped as Algorithm 2 drops
+ * X_j^T X_j).  The whole gradient comes from one read of a packed matrix of
+ * augmented (d+1) x (d+1) blocks B_ij = [[A_ij, sqrt(kappa) c_ij], [0, w_ij]] in the
+ * symmetric panel layout, multiplied with [[X_j, 0], [sqrt(kappa) t_j^T, 1]].
+ * d <= 7; storage NSRGS_F32 or NSRGS_BF16 (FP8's per-row scale would store the unit
+ * weights w_ij inexactly and skew the translations). */
+
+/* Bytes of the packed augmented matrix: nsrgs_packed_bytes(n, d + 1, storage);
+ * 0 when (n, d, storage) is outside the form. */
+size_t nsrgs_se_packed_bytes(int n, int d, int storage);
+/* Workspace bytes of nsrgs_se_solve: nsrgs_workspace_bytes(n, d + 1). */
+size_t nsrgs_se_workspace_bytes(int n, int d);
+/* Packs the augmented matrix from the canonical upper-block list of A (device,
+ * n(n-1)/2 x d x d float32, blocks (i, j) for i < j ordered by i then j) and the
+ * matching list of translations c (device, n(n-1)/2 x d float32) into `packed`
+ * (device, nsrgs_se_packed_bytes, 16-byte aligned).  kappa >= 0 is folded into
+ * the stored blocks (sqrt(kappa) c_ij), so a packed matrix serves one kappa.
+ * The result is an nsrgs_A with d + 1 for nsrgs_se_solve. */
+nsrgs_status nsrgs_se_pack(const float* upper_a, const float* upper_c, int n, int d, float kappa, int storage,
+                           void* packed, void* st);
+/* T iterations of the SE(d) form from (X, t) (device: X nd x d, t n x d, both
+ * float32, 16-byte aligned), written back in place.  B: an nsrgs_A with
+ * B->d = d + 1 describing an nsrgs_se_pack result made with the same kappa.
+ * eta > 0 steps the rotations (the paper's 1/n), eta_t >= 0 the translations
+ * (1/(kappa n) solves the translation problem of complete noise-free data in
+ * one step).  tol > 0 stops after the first iteration with
+ * sqrt((||X' - X||_F^2 + ||t' - t||^2) / (nd)) < tol.  X is typically the
+ * spectral start of the rotation part (nsrgs_spectral_init on A packed alone)
+ * and t zero.  Synchronises `st`; `info` (nullable) receives iters,
+ * last_update_norm and flags.  The A stream of each iteration is timed when
+ * nsrgs_set_kernel_timing is on.  Errors as nsrgs_solve. */
+nsrgs_status nsrgs_se_solve(const nsrgs_A* B, float kappa, float eta, float eta_t, int T, int K, double tol,
+                            float* X, float* t, nsrgs_info* info, void* ws, size_t ws_bytes, void* st);
+
 /* ------------------------------------------------------- batched form */
 
 /* One independent instance of a batch. */

@@ -36,6 +36,8 @@ from ._lib import (  # noqa: F401
     STOP_REL_DECREASE,
     nsrgs_objective,
     nsrgs_stiefel_solve,
+    nsrgs_se_pack,
+    nsrgs_se_solve,
     nsrgs_dF,
     nsrgs_version,
     nsrgs_set_kernel_timing,

@@ -89,6 +89,10 @@ def lib() -> ctypes.CDLL:
         "nsrgs_solve": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_solve_objective": (i, [Ap, f, i, i, d, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_solve_host": (i, [Ap, vp, sz, f, i, i, d, i, i, vp, vp, ctypes.POINTER(Info), vp, sz, vp]),
+        "nsrgs_se_packed_bytes": (sz, [i, i, i]),
+        "nsrgs_se_workspace_bytes": (sz, [i, i]),
+        "nsrgs_se_pack": (i, [vp, vp, i, i, f, i, vp, vp]),
+        "nsrgs_se_solve": (i, [Ap, f, f, f, i, i, d, vp, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_objective": (i, [Ap, vp, ctypes.POINTER(d), vp, sz, vp]),
         "nsrgs_solve_ex": (i, [Ap, f, i, i, vp, i, i, vp, ctypes.POINTER(Info), vp, sz, vp]),
         "nsrgs_dF": (i, [vp, vp, i, i, ctypes.POINTER(d), vp, sz, vp]),
@@ -420,6 +424,36 @@ def nsrgs_stiefel_solve(A: PackedA, p: int, eta: float, T: int, K: int, X0: torc
     _check(fn(ctypes.byref(a), p, eta, T, K, tol, _ptr(X0), _ptr(X), ctypes.byref(inf) if inf is not None else None,
               _ptr(w), w.numel(), _stream()))
     return X, inf
+
+
+def nsrgs_se_pack(upper_a: torch.Tensor, upper_c: torch.Tensor, n: int, d: int, kappa: float,
+                  storage: int = F32) -> PackedA:
+    """Pack the SE(d) form's augmented matrix from the upper-block lists of A
+    ((n(n-1)/2, d, d) float32) and c ((n(n-1)/2, d) float32) on the device; the
+    result describes (d + 1)-blocks for nsrgs_se_solve."""
+    assert upper_a.dtype == torch.float32 and upper_a.numel() == n * (n - 1) // 2 * d * d
+    assert upper_c.dtype == torch.float32 and upper_c.numel() == n * (n - 1) // 2 * d
+    nb = int(lib().nsrgs_se_packed_bytes(n, d, storage))
+    if nb == 0:
+        raise NsrgsError(8, f"the SE(d) form does not support (n={n}, d={d}, storage={storage})")
+    buf = torch.empty(nb, dtype=torch.uint8, device=upper_a.device)
+    _check(lib().nsrgs_se_pack(_ptr(upper_a.contiguous()), _ptr(upper_c.contiguous()), n, d, kappa, storage,
+                               _ptr(buf), _stream()))
+    return PackedA(buf, n, d + 1, storage)
+
+
+def nsrgs_se_solve(B: PackedA, kappa: float, eta: float, eta_t: float, T: int, K: int, X: torch.Tensor,
+                   t: torch.Tensor, tol: float = 0.0, ws=None, info: bool = True):
+    """T iterations of the SE(d) form from (X (nd x d), t (n x d)), updated in place;
+    B from nsrgs_se_pack with the same kappa.  Returns (X, t, Info or None)."""
+    n, d = B.n, B.d - 1
+    if ws is None:
+        ws = torch.empty(int(lib().nsrgs_se_workspace_bytes(n, d)), dtype=torch.uint8, device=B.buf.device)
+    a = B.struct()
+    inf = Info() if info else None
+    _check(lib().nsrgs_se_solve(ctypes.byref(a), kappa, eta, eta_t, T, K, tol, _ptr(X), _ptr(t),
+                                ctypes.byref(inf) if inf is not None else None, _ptr(ws), ws.numel(), _stream()))
+    return X, t, inf
 
 
 def nsrgs_objective(A: PackedA, X: torch.Tensor, ws=None) -> float:

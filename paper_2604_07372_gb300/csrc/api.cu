@@ -26,6 +26,10 @@ int num_sms() {
 // ------------------------------------------------- kernels in other units
 nsrgs_status pack_upper_impl(const float*, int, int, int, void*, cudaStream_t);
 nsrgs_status pack_dense_impl(const float*, int, int, int, void*, cudaStream_t);
+nsrgs_status pack_se_impl(const float*, const float*, int, int, float, int, void*, cudaStream_t);
+cudaError_t se_launch(int what, int d, const float* X, float* t, const float* Xa0, float* Ya, float* Xa1, int n,
+                      float eta, float eta_t, float kappa, int K, double tol, Ctl* ctl, float* Xout,
+                      cudaStream_t st);
 long long dense_pitch(int n, int d);
 cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
                          const int* skip, cudaStream_t st);
@@ -712,6 +716,96 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
       set_error("an iterate became non-finite");
       return NSRGS_ERR_NONFINITE;
     }
+  }
+  return NSRGS_OK;
+}
+
+// ------------------------------------------------------------ SE(d) form
+// FP8 is left out: its per-row scale stores the unit pair weights w_ij only to
+// within ~6% of 1, which skews the translation Laplacian (measured: +4.5% on the
+// translation error at n = 400 against the oracle, BF16 +0.1%).
+static bool se_storage(int storage) { return storage == NSRGS_F32 || storage == NSRGS_BF16; }
+
+size_t nsrgs_se_packed_bytes(int n, int d, int storage) {
+  if (d < 1 || d > 7 || !se_storage(storage)) return 0;
+  return nsrgs_packed_bytes(n, d + 1, storage);
+}
+
+size_t nsrgs_se_workspace_bytes(int n, int d) {
+  if (d < 1 || d > 7) return 0;
+  return nsrgs_workspace_bytes(n, d + 1);
+}
+
+nsrgs_status nsrgs_se_pack(const float* upper_a, const float* upper_c, int n, int d, float kappa, int storage,
+                           void* packed, void* stv) {
+  nsrgs_status s = check_nd(n, d);
+  if (s != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(d <= 7, "the SE(d) form covers d <= 7 (augmented blocks of d + 1 <= 8)");
+  NSRGS_CHECK_ARG(se_storage(storage), "the SE(d) form stores NSRGS_F32 or NSRGS_BF16 panels");
+  NSRGS_CHECK_ARG(kappa >= 0.f && isfinite(kappa), "kappa must be finite and >= 0");
+  NSRGS_CHECK_ARG(upper_a && upper_c && packed && aligned16(packed), "null or misaligned pointer");
+  return pack_se_impl(upper_a, upper_c, n, d, kappa, storage, packed, (cudaStream_t)stv);
+}
+
+nsrgs_status nsrgs_se_solve(const nsrgs_A* B, float kappa, float eta, float eta_t, int T, int K, double tol,
+                            float* X, float* t, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
+  NSRGS_CHECK_ARG(B != nullptr, "B is null");
+  NSRGS_CHECK_ARG(B->d >= 2 && B->d <= 8 && se_storage(B->storage),
+                  "B must be an nsrgs_se_pack result: d + 1 in [2, 8], panel storage");
+  PanelGeom g{};
+  nsrgs_status s = check_A(B, &g);
+  if (s != NSRGS_OK) return s;
+  const int n = B->n, D = B->d, d = D - 1;
+  if ((s = check_ws(ws, ws_bytes, n, D)) != NSRGS_OK) return s;
+  NSRGS_CHECK_ARG(kappa >= 0.f && isfinite(kappa), "kappa must be finite and >= 0");
+  NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
+  NSRGS_CHECK_ARG(eta_t >= 0.f && isfinite(eta_t), "eta_t must be finite and >= 0");
+  NSRGS_CHECK_ARG(K >= 0 && K <= 64, "K must be in [0, 64]");
+  NSRGS_CHECK_ARG(T >= 0 && T <= 100000, "T must be in [0, 100000]");
+  NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
+  NSRGS_CHECK_ARG(X && t && aligned16(X) && aligned16(t), "X and t must be 16-byte aligned device pointers");
+  cudaStream_t st = (cudaStream_t)stv;
+  Workspace w = map_workspace(ws, n, D);
+  int dev = 0;
+  NSRGS_CUDA_TRY(cudaGetDevice(&dev));
+  const bool timing = g_timing != 0;
+  if (timing) NSRGS_CUDA_TRY(ensure_events(dev, T));
+  const cudaEvent_t* ev = timing ? g_timing_state[dev].ev.data() : nullptr;
+  NSRGS_CUDA_TRY(reset_ws(w, n, D, st));
+  NSRGS_CUDA_TRY(se_launch(0, d, X, t, nullptr, nullptr, w.X[0], n, eta, eta_t, kappa, K, tol, w.ctl, nullptr, st));
+  for (int it = 0; it < T; ++it) {
+    if (ev) NSRGS_CUDA_TRY(cudaEventRecord(ev[2 * it], st));
+    NSRGS_CUDA_TRY(stream_AX(B, g, w.X[it & 1], w, &w.ctl->stop, st));
+    if (ev) NSRGS_CUDA_TRY(cudaEventRecord(ev[2 * it + 1], st));
+    NSRGS_CUDA_TRY(se_launch(1, d, nullptr, t, w.X[it & 1], w.Y, w.X[(it + 1) & 1], n, eta, eta_t, kappa, K, tol,
+                             w.ctl, nullptr, st));
+  }
+  NSRGS_CUDA_TRY(se_launch(2, d, nullptr, nullptr, w.X[0], nullptr, w.X[1], n, eta, eta_t, kappa, K, tol, w.ctl, X,
+                           st));
+  g_timing_state[dev].last_T = timing ? T : 0;
+  g_timing_state[dev].last_nodes = 2 * T + 2;
+  Ctl c{};
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->iters = c.iters_done;
+    info->last_update_norm = c.last_upd;
+    info->flags = c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND);
+    info->objective = NAN;
+    info->rel_decrease = NAN;
+  }
+  if (c.flags & FLAG_BAD_LAYOUT) {
+    set_error("the packed matrix is inconsistent: an index or address left its buffer (access skipped)");
+    return NSRGS_ERR_INVALID_ARG;
+  }
+  if (c.flags & FLAG_TIMEOUT) {
+    set_error("a device-side wait timed out");
+    return NSRGS_ERR_TIMEOUT;
+  }
+  if (c.flags & FLAG_NONFINITE) {
+    set_error("an iterate became non-finite");
+    return NSRGS_ERR_NONFINITE;
   }
   return NSRGS_OK;
 }

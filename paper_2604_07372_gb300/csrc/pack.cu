@@ -6,6 +6,7 @@
 // dense layout keeps the whole matrix with its diagonal blocks zeroed, so the
 // plain product A_off X needs no special case.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "src.cuh"
@@ -180,9 +181,11 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
     NSRGS_CUDA_TRY(cudaGetLastError());
     return NSRGS_OK;
   }
-  if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
-    NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, packed, st));
-    return NSRGS_OK;
+  if constexpr (!std::is_same_v<Src, SeAugSrc>) {  // the SE(d) form uses panels only
+    if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
+      NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, packed, st));
+      return NSRGS_OK;
+    }
   }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
@@ -224,6 +227,12 @@ nsrgs_status pack_upper_impl(const float* upper, int n, int d, int storage, void
     return NSRGS_OK;
   }
   return pack_any(UpperSrc{upper, n, d}, n, d, storage, packed, st);
+}
+
+// SE(d) form: the augmented (d+1)-block matrix in the symmetric panel layout.
+nsrgs_status pack_se_impl(const float* upper_a, const float* upper_c, int n, int d, float kappa, int storage,
+                          void* packed, cudaStream_t st) {
+  return pack_any(SeAugSrc{upper_a, upper_c, n, d, sqrtf(kappa)}, n, d + 1, storage, packed, st);
 }
 
 nsrgs_status pack_dense_impl(const float* A, int n, int d, int storage, void* packed, cudaStream_t st) {
