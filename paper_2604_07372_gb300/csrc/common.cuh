@@ -140,9 +140,11 @@ struct PanelGeom {
 // per CTA, 146 with 14).  NW*8*RT (NW from panel_nw) must be a multiple of d so that slabs
 // hold whole block rows.  Each step ends with a reduction of the CPT*d column partials over
 // 8 lanes whose cost does not depend on RT, so a larger RT amortises it: at d = 4, RT = 8
-// with 8 consumer warps ran 1.3x (FP32) to 1.7x (FP8) faster than RT = 4 with 12.
+// with 8 consumer warps ran 1.3x (FP32) to 1.7x (FP8) faster than RT = 4 with 12, and at
+// d = 3 BF16 / FP8 (issue-bound) RT = 12 with 8 warps ran 10% / 8% faster than RT = 6 with 12;
+// FP32 at d = 3 (bandwidth-bound) keeps RT = 6 with 12 warps.
 __host__ __device__ constexpr int panel_rt(int d, int storage) {
-  return d <= 2 ? 8 : d == 3 ? 6 : d == 4 ? 8 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 4;
+  return d <= 2 ? 8 : d == 3 ? (storage == NSRGS_F32 ? 6 : 12) : d == 4 ? 8 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 4;
 }
 __host__ __device__ constexpr int panel_loadb(int d, int storage) {
   return storage == NSRGS_FP8E4M3 ? 8
@@ -151,14 +153,14 @@ __host__ __device__ constexpr int panel_loadb(int d, int storage) {
                                   : (storage == NSRGS_F32 ? 16 : 8);
 }
 
-// Consumer warps per CTA.  At d <= 3, 12 consumer warps (3 per scheduler) hide
-// more of each step's latency (shared-memory loads, shuffles, barrier waits) and
-// make each stage's bulk copy 1.5x larger: FP32 reaches the copy bandwidth with
-// them, and BF16 / FP8 (2d FMAs per element on a half or a quarter of the bytes,
-// issue-bound) gain ~10%.  From d = 4 on the per-thread tiles (RT = 8 at d = 4)
-// need the registers of 8 warps.
+// Consumer warps per CTA.  With the small tiles of d <= 2 and of FP32 at d = 3,
+// 12 consumer warps (3 per scheduler) hide more of each step's latency
+// (shared-memory loads, shuffles, barrier waits) and make each stage's bulk copy
+// 1.5x larger: FP32 at d = 3 reaches the copy bandwidth with them (0.92 with 8).
+// The larger per-thread tiles (BF16 / FP8 at d = 3, RT = 8 at d = 4, everything
+// above) need the registers of 8 warps.
 __host__ __device__ constexpr int panel_nw(int d, int storage) {
-  return d <= 3 ? 12 : 8;
+  return (d <= 2 || (d == 3 && storage == NSRGS_F32)) ? 12 : 8;
 }
 
 // Rows of X/Y padding needed by a layout (columns of the last step run past n*D).

@@ -33,15 +33,15 @@ def loadb(d, storage):
 
 
 def nw(d, storage):
-    """Consumer warps per CTA: 12 at d <= 3, else 8."""
-    return 12 if d <= 3 else 8
+    """Consumer warps per CTA: 12 at d <= 2 and for FP32 at d = 3, else 8."""
+    return 12 if (d <= 2 or (d == 3 and storage == 0)) else 8
 
 
 class Geom:
     def __init__(self, n, d, storage):
         self.n, self.D, self.st = n, d, storage
         self.E = E_OF[storage]
-        self.RT = RT_OF[d]
+        self.RT = 12 if (d == 3 and storage != 0) else RT_OF[d]
         self.LOADB = loadb(d, storage)
         self.CPT = self.LOADB // self.E
         self.SC = 4 * self.CPT
