@@ -142,9 +142,10 @@ struct PanelGeom {
 // 8 lanes whose cost does not depend on RT, so a larger RT amortises it: at d = 4, RT = 8
 // with 8 consumer warps ran 1.3x (FP32) to 1.7x (FP8) faster than RT = 4 with 12, and at
 // d = 3 BF16 / FP8 (issue-bound) RT = 12 with 8 warps ran 10% / 8% faster than RT = 6 with 12;
-// FP32 at d = 3 (bandwidth-bound) keeps RT = 6 with 12 warps.
+// FP32 at d = 3 (bandwidth-bound) keeps RT = 6 with 12 warps; at d = 8, RT = 6 (three quarters
+// of a block row per thread) ran 24% (FP32) / 28% (BF16) faster than RT = 4.
 __host__ __device__ constexpr int panel_rt(int d, int storage) {
-  return d <= 2 ? 8 : d == 3 ? (storage == NSRGS_F32 ? 6 : 12) : d == 4 ? 8 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 4;
+  return d <= 2 ? 8 : d == 3 ? (storage == NSRGS_F32 ? 6 : 12) : d == 4 ? 8 : d == 5 ? 5 : d == 6 ? 6 : d == 7 ? 7 : 6;
 }
 __host__ __device__ constexpr int panel_loadb(int d, int storage) {
   return storage == NSRGS_FP8E4M3 ? 8

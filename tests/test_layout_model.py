@@ -18,7 +18,7 @@ import synth
 
 E_OF = {0: 4, 1: 2, 2: 1}
 # scalar rows per thread, per d
-RT_OF = {1: 8, 2: 8, 3: 6, 4: 8, 5: 5, 6: 6, 7: 7, 8: 4}
+RT_OF = {1: 8, 2: 8, 3: 6, 4: 8, 5: 5, 6: 6, 7: 7, 8: 6}
 
 
 def loadb(d, storage):
