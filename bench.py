@@ -62,6 +62,7 @@ def parse_args():
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
+    ap.add_argument("--se-n", type=int, default=10000, help="n of the SE(d) leg (--leg se)")
     ap.add_argument("--sweep-storages", default="", help="comma-separated subset of the sweep's storages")
     ap.add_argument("--sparse-ps", default="0.05,0.2,0.5", help="observation probabilities of the sparse leg")
     return ap.parse_args()
@@ -411,6 +412,7 @@ def se_leg(P, synth, seed: int, n: int = 10000, d: int = 3, T: int = 100, K: int
     noise 0.1, kappa = 1/(4d), eta = 1/n, eta_t = 1/(kappa n), from the spectral start of
     the rotation part and t = 0: T iterations streaming the augmented (d+1)-block matrix
     (FP32 and BF16 panels); per-launch A-stream time with CUDA events around each launch."""
+    import numpy as np
     import torch
 
     sigma = synth.sigma_rule(c, n, d)
@@ -443,8 +445,8 @@ def se_leg(P, synth, seed: int, n: int = 10000, d: int = 3, T: int = 100, K: int
             sec = e0.elapsed_time(e1) / 1e3
             ab = n * (n - 1) // 2 * (d + 1) ** 2 * {"f32": 4, "bf16": 2}[name]
             # translation error after the gauge (X -> X Q, t -> Q^T t + v), Q from the rotations
-            U, _, Vh = torch.linalg.svd(Zs.double().T @ X.double())
-            Q = U @ Vh
+            U, _, Vh = np.linalg.svd((Zs.double().T @ X.double()).cpu().numpy())  # d x d, on the host
+            Q = torch.from_numpy(U @ Vh).to(X.device)
             e = t.double() - tau.double() @ Q
             e -= e.mean(dim=0, keepdim=True)
             out[name] = {
@@ -917,7 +919,7 @@ def main():
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
         elif args.leg == "se":
-            out = se_leg(P, synth, seed=args.seed + 5)
+            out = se_leg(P, synth, seed=args.seed + 5, n=args.se_n)
         elif args.leg == "sparse":
             out = sparse_leg(P, synth, seed=args.seed + 4, ps=tuple(float(x) for x in args.sparse_ps.split(",")))
         else:
