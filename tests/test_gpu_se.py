@@ -156,3 +156,40 @@ def test_unsupported_shapes_are_rejected(P):
         P.nsrgs_se_pack(dev(s.rot.upper), dev(s.c_upper), 10, 3, -1.0, P.F32)
     with pytest.raises(P.NsrgsError):
         P.nsrgs_se_pack(dev(s.rot.upper), dev(s.c_upper), 10, 3, 0.1, P.FP8E4M3)
+
+
+def test_zero_iterations_return_the_start(P):
+    n, d = 60, 3
+    s = make(n, d, seed=21)
+    X0, t0 = start(s)
+    X, t, info = P.nsrgs_se_solve(se_pack(P, s, 0.1, P.F32), 0.1, 1.0 / n, 1.0, 0, 2, dev(X0), dev(t0))
+    torch.cuda.synchronize()
+    assert info.iters == 0
+    assert torch.equal(X.cpu(), dev(X0).cpu()) and torch.equal(t.cpu(), dev(t0).cpu())
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_largest_d_one_iteration_matches_oracle(P, storage):
+    """d = 7: augmented 8 x 8 blocks, the widest panel shape the form uses."""
+    n, d = 45, 7
+    s = make(n, d, seed=77)
+    kappa = 1.0 / (4 * d)
+    eta, eta_t = 1.0 / n, 1.0 / (kappa * n)
+    X0, t0 = start(s)
+    B = se_pack(P, s, kappa, P.STORAGE[storage])
+    if storage == "f32":
+        A, C, W = oracle_inputs(s)
+    else:  # the oracle sees the same bfloat16-rounded measurements the GPU streams
+        bq = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float32)).bfloat16().float().numpy()
+        iu, ju = np.triu_indices(n, 1)
+        A = synth.dense_from_upper(bq(s.rot.upper), n, d)
+        C = np.zeros((n, n, d))
+        sk = np.sqrt(np.float32(kappa))  # the packer's float32 sqrt(kappa) and float32 product
+        C[iu, ju] = bq(sk * s.c_upper.astype(np.float32)).astype(np.float64) / float(sk)
+        W = s.mask_square()
+    Xo, to = O.se_iteration(A, C, W, X0, t0, n, d, eta, eta_t, kappa, 2)
+    X, t, info = P.nsrgs_se_solve(B, kappa, eta, eta_t, 1, 2, dev(X0), dev(t0))
+    torch.cuda.synchronize()
+    assert info.iters == 1 and info.flags == 0, info.as_dict()
+    assert np.max(np.abs(X.double().cpu().numpy() - Xo)) <= 2e-5
+    assert np.max(np.abs(t.double().cpu().numpy() - to)) <= 1e-4
