@@ -7,7 +7,7 @@ with G^X, G^t half its gradient (the term whose tangent projection vanishes on
 O(d) dropped, as Algorithm 2 drops X_j^T X_j).  These checks tie it to things
 other than itself: finite differences of f, the fixed point of noise-free data,
 the reduction to Algorithm 2 at kappa = 0, the gauge symmetry, a closed form of
-the translation step, and a planted-mistake check.
+the translation step, a planted-mistake check, and the gauge-aligned error metric.
 """
 import math
 
@@ -159,3 +159,20 @@ def test_planted_mistakes_are_caught():
         for j in range(i + 1, n):
             GXbad[i] += kappa * np.outer(C[i, j], t[j] - t[i])
     assert np.max(np.abs(O.tangent_projection(Xb, GXbad) - O.tangent_projection(Xb, GX))) > 1e-3
+
+
+def test_errors_are_gauge_invariant_and_exact():
+    """se_errors: the truth moved by any gauge (X Q, Q^T t + v) scores (0, 0); adding a
+    zero-mean perturbation e to the translations scores sqrt(sum ||e_i||^2 / n)."""
+    s, _, _, _ = inst(n=12)
+    n, d = 12, 3
+    rng = np.random.default_rng(8)
+    Q = synth.haar_orthogonal(rng, 1, d)[0]
+    v = rng.standard_normal(d)
+    Z = s.rot.Zstack()
+    eR, eT = O.se_errors(Z @ Q, s.tau @ Q + v[None, :], s.rot.Z, s.tau, n, d)
+    assert eR < 1e-12 and eT < 1e-12
+    e = rng.standard_normal((n, d))
+    e -= e.mean(axis=0, keepdims=True)
+    _, eT = O.se_errors(Z @ Q, (s.tau + e) @ Q + v[None, :], s.rot.Z, s.tau, n, d)
+    assert abs(eT - math.sqrt(float(np.sum(e * e)) / n)) < 1e-12
