@@ -183,11 +183,13 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
  *  - Scratch lives in one fixed 8 MiB (8388608-byte) device array inside the
  *    library; every GPU on which this is called keeps that memory until the
  *    process exits.  (n, d) whose nsrgs_workspace_bytes exceeds 8 MiB is
- *    rejected with NSRGS_ERR_INVALID_ARG (about n <= 170000 at d = 3,
- *    n <= 30000 at d = 4).
+ *    rejected with NSRGS_ERR_INVALID_ARG: n <= 46016 at d = 3,
+ *    n <= 25656 at d = 4, n <= 6025 at d = 8, n <= 1016 at d = 16; d >= 32
+ *    never fits.
  *  - The first call on a device resolves the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and caches it; make that
+ *    first call before any stream capture, and do not use this entry point
+ *    across a cudaDeviceReset of the device (the cached address goes stale).
  *  - No device memory is allocated or freed by any call.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other host threads) race and give wrong results; serialise them.
@@ -473,7 +475,7 @@ nsrgs_status nsrgs_dF(const float* X, const float* Y, int n, int d, double* out,
 nsrgs_status nsrgs_set_kernel_timing(int enable);
 nsrgs_status nsrgs_kernel_timing(int* launches, double* mean_ms, int* graph_kernel_nodes);
 
-/* Thread-local text of the last error on this thread ("" if none). *//* Thread-local text of the last error on this thread ("" if none). */
+/* Thread-local text of the last error on this thread ("" if none). */
 const char* nsrgs_last_error(void);
 
 /* Library version string. */

@@ -311,9 +311,10 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
         const uint32_t bytesA = (uint32_t)wk.W * C::WB;
         const uint8_t* srcA = panels + off;
         const float* srcX = v.X + (long long)wk.xcol() * D;
-        // a copy that would leave the panels or start off a 16-byte boundary is
-        // refused and flagged (the consumers then time out and return)
-        if (off + bytesA > v.g.panel_bytes ||
+        // a copy that would leave the panels (either end: the offsets come from
+        // the packed header) or start off a 16-byte boundary is refused and
+        // flagged (the consumers then time out and return)
+        if (off < 0 || off + bytesA > v.g.panel_bytes ||
             ((reinterpret_cast<uintptr_t>(srcA) | reinterpret_cast<uintptr_t>(srcX)) & 15u)) {
           atomicOr(&v.ctl->flags, FLAG_BAD_LAYOUT);
           ok = false;

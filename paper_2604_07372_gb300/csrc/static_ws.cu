@@ -11,7 +11,12 @@
 // Cost and limits: every GPU on which this entry point runs holds
 // kStaticWorkspaceBytes (8 MiB) of device memory for this array until the
 // process exits.  A problem whose workspace (nsrgs_workspace_bytes(n, d))
-// exceeds that size is rejected with NSRGS_ERR_INVALID_ARG.
+// exceeds that size is rejected with NSRGS_ERR_INVALID_ARG: the largest n is
+// 418368 at d = 1, 46016 at d = 3, 25656 at d = 4, 6025 at d = 8 and 1016 at
+// d = 16; d >= 32 never fits (the float64 per-CTA partials alone exceed it).
+// The array's device address is resolved once per device and cached, so the
+// entry point must not be used across a cudaDeviceReset of that device (the
+// module is reloaded and the cached address would be stale).
 #include <mutex>
 
 #include "common.cuh"
@@ -49,9 +54,14 @@ extern "C" nsrgs_status nsrgs_step_static(const nsrgs_A* A, float eta, int K, co
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+  if (e != cudaSuccess) {
     nsrgs::set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     return NSRGS_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= 64) {
+    nsrgs::set_error("nsrgs_step_static: device ordinal " + std::to_string(dev) +
+                     " is not supported (the per-device address table holds ordinals 0..63)");
+    return NSRGS_ERR_INVALID_ARG;
   }
   void* ptr = nullptr;
   {

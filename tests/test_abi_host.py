@@ -90,3 +90,36 @@ def test_bad_arguments_are_rejected_without_a_device(L):
     assert lib.nsrgs_se_pack(buf, buf, 100, 3, -0.1, 0, buf, None) == 1
     A = L._lib._A(16, 100, 9, 0)  # augmented blocks of 9: outside the form
     assert lib.nsrgs_se_solve(ctypes.byref(A), 0.1, 0.01, 1.0, 5, 2, 0.0, buf, buf, None, buf, 0, None) == 1
+
+
+def test_static_step_limits_match_the_documented_figures(L):
+    """nsrgs_step_static holds its scratch in a fixed 8 MiB array; the largest n per d
+    documented in include/nsrgs.h follows from nsrgs_workspace_bytes."""
+    cap = 8 << 20
+    lib = L.lib()
+
+    def largest_n(d):
+        if lib.nsrgs_workspace_bytes(2, d) > cap:
+            return None
+        lo, hi = 2, 1 << 22
+        while lo < hi:
+            m = (lo + hi + 1) // 2
+            if lib.nsrgs_workspace_bytes(m, d) <= cap:
+                lo = m
+            else:
+                hi = m - 1
+        return lo
+
+    header = open(os.path.join(ROOT, "include", "nsrgs.h")).read()
+    for d, n in ((3, 46016), (4, 25656), (8, 6025), (16, 1016)):
+        assert largest_n(d) == n, (d, largest_n(d))
+        assert f"n <= {n} at d = {d}" in header
+    assert largest_n(32) is None and largest_n(64) is None
+    assert "d >= 32\n *    never fits" in header
+    # the oversize check comes before any device access
+    fn = lib.nsrgs_step_static
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(L._lib._A), ctypes.c_float, ctypes.c_int] + [ctypes.c_void_p] * 4
+    a = L._lib._A(16, 46017, 3, 0)
+    assert fn(ctypes.byref(a), 0.1, 2, None, None, None, None) == 1
+    assert b"8 MiB" in lib.nsrgs_last_error()
