@@ -242,9 +242,14 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3 / reps
         bytes_A = sum(p.nbytes for p in packs[st])
+        # bytes of A streamed by one batch solve: each instance's packed A once per
+        # spectral pass and per iteration (the orthonormalising passes read no A)
+        streamed = sum(p.nbytes * (i.spectral_iters + i.iters) for p, i in zip(packs[st], infos))
         dF[name] = np.array([P.nsrgs_dF(X, Z, n, d, ws=None) for X, Z, n in zip(Xs, Zs, ns)])
         out[name] = {"solves_per_s": count / sec, "batch_ms": 1e3 * sec, "packed_GB": bytes_A / 1e9,
-                     "instances_with_T_iterations": iters_ok}
+                     "instances_with_T_iterations": iters_ok, "A_GB_streamed_per_batch": streamed / 1e9,
+                     "A_GBps": streamed / sec / 1e9,
+                     "hbm_frac": streamed / sec / 1e9 / measured_peaks()[0]["hbm_gbs"]}
         del ws
     for name in ("bf16", "fp8"):
         rel = np.abs(dF[name] - dF["f32"]) / dF["f32"]
@@ -876,6 +881,16 @@ def run_ours(args, world, rank, local):
                 traceback.print_exc()
                 line[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
             torch.cuda.empty_cache()
+        # the batched and served headline figures as short top-level keys
+        b, sv = line.get("batched", {}), line.get("serving", {})
+        for name in ("bf16", "fp8", "f32"):
+            if isinstance(b.get(name), dict):
+                line[f"batched_{name}_solves_per_s"] = b[name]["solves_per_s"]
+                line[f"batched_{name}_hbm_frac"] = b[name]["hbm_frac"]
+        if "p50_ms" in sv:
+            line["served_solves_per_s"] = sv["solves_per_s"]
+            line["served_p50_ms"] = sv["p50_ms"]
+            line["served_p99_ms"] = sv["p99_ms"]
         # CPU oracle on the host cores, bounded sample
         try:
             times, build_s, cores = cpu_oracle_iterations(inst, args, 3)

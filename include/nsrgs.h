@@ -114,7 +114,9 @@ typedef struct nsrgs_info {
   double spectral_residual;/* ||A V - V H||_F / ||H||_F at the end of the spectral initialisation */
   uint32_t flags;          /* bit 0: non-finite iterate; bit 1: NS precondition violated;
                               bit 2: spectral initialisation not converged;
-                              bit 4: the safeguarded Newton-Schulz start acted */
+                              bit 4: the safeguarded Newton-Schulz start acted;
+                              bit 6: the spectral initialisation restarted with a larger
+                              shift to reach the algebraic top-d (see nsrgs_spectral_init) */
   double objective;        /* nsrgs_solve_objective: F(X) of eq. (1) at the returned X; NaN otherwise */
   double rel_decrease;     /* nsrgs_solve_objective: the last relative decrease R^t formed; NaN otherwise */
 } nsrgs_info;
@@ -155,9 +157,18 @@ nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* p
 /* ---------------------------------------------------------- the method */
 
 /* Spectral initialisation (Algorithm 2): X0 (device, nd x d) = sgn_n(Y), Y an
- * orthonormal basis of the top-d eigenvectors of A, found by block subspace
- * iteration V <- orth(A V) with float64 d x d Gram/Cholesky steps, stopped when
- * ||A V - V (V^T A V)||_F / ||V^T A V||_F <= tol or after max_iters passes.
+ * orthonormal basis of the eigenvectors of the d largest (algebraic) eigenvalues
+ * of A, found by block subspace iteration V <- orth((A_off + cI) V) with float64
+ * d x d Gram/Cholesky steps, converged when
+ * ||A V - V (V^T A V)||_F / ||V^T A V||_F <= tol.  The shift starts at c = 1
+ * (iteration on A itself), which finds the d eigenvalues of largest magnitude.
+ * At convergence the basis is accepted when V^T (A_off + cI) V is positive
+ * definite: then no eigenvalue left out lies above the captured ones.  Otherwise
+ * a negative eigenvalue dominated, and the passes restart from the start vectors
+ * with c raised above the negative end of the spectrum (a Gershgorin bound of
+ * that d x d matrix), at most 3 times (info flags bit 6).  Restarts count
+ * against max_iters; a basis that still fails after the last restart is
+ * reported as not converged.
  * The per-block matrix sign is exact (float64 one-sided Jacobi SVD).  Returns
  * NSRGS_ERR_NOT_CONVERGED (X0 still written) when max_iters ran out; with
  * `residual` non-null the final residual is written there (host; synchronises). */

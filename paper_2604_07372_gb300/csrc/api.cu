@@ -41,8 +41,8 @@ int reduce_grid(long long rows);
 cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
                             cudaStream_t);
 cudaError_t launch_gpm_epilogue(const float*, float*, float*, int, int, double, Ctl*, cudaStream_t);
-cudaError_t launch_spec_v0(float*, long long, int, cudaStream_t);
-cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
+cudaError_t launch_spec_v0(float*, long long, int, double*, cudaStream_t);
+cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, int, const SpecScratch&, Ctl*,
                              cudaStream_t);
 cudaError_t launch_spec_update(const float*, const float*, float*, long long, int, const SpecScratch&, double, int,
                                Ctl*, cudaStream_t);
@@ -227,23 +227,26 @@ static cudaError_t reset_ws(const Workspace& w, int n, int d, cudaStream_t st) {
   return cudaSuccess;
 }
 
-// Subspace iteration for the top-d eigenvectors of A = A_off + I, then the exact
-// blockwise sign: X0 = sgn_n(V) (Algorithm 2's spectral initialisation).
+// Subspace iteration for the top-d eigenvectors of A, then the exact blockwise
+// sign: X0 = sgn_n(V) (Algorithm 2's spectral initialisation).  The passes
+// iterate on A_off + cI, starting with c = 1 (A itself); at convergence the
+// algebraic top-d test (spec_shift_after) either accepts the subspace or
+// restarts from V^0 with a larger c inside the same pass budget.
 // Leaves X0 in `out` (which may be w.X[0]); uses X[0], X[1], Y, W.
 static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, int max_iters,
                                     double tol, float* out, cudaStream_t st) {
   const int n = A->n, d = A->d;
   const long long rows = (long long)n * d;
   cudaError_t e;
-  if ((e = launch_spec_v0(w.X[0], rows, d, st)) != cudaSuccess) return e;
+  if ((e = launch_spec_v0(w.X[0], rows, d, w.s.scal + 3, st)) != cudaSuccess) return e;
   // orthonormalise the start: W = V0 (Y is zero), V1 = W chol(W^T W)^{-1}
-  if ((e = launch_spec_gram(w.X[0], w.Y, w.W, rows, d, 1.0f, w.s, w.ctl, st)) != cudaSuccess) return e;
+  if ((e = launch_spec_gram(w.X[0], w.Y, w.W, rows, d, 1.0f, 0, w.s, w.ctl, st)) != cudaSuccess) return e;
   if ((e = launch_spec_update(w.X[0], w.W, w.X[1], rows, d, w.s, tol, 0, w.ctl, st)) != cudaSuccess) return e;
   for (int k = 0; k < max_iters; ++k) {
     const float* V = w.X[(k + 1) & 1];
     float* Vn = w.X[k & 1];
-    if ((e = stream_AX(A, g, V, w, &w.ctl->spec_stop, st)) != cudaSuccess) return e;
-    if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, w.s, w.ctl, st)) != cudaSuccess) return e;
+    if ((e = stream_AX(A, g, V, w, &w.ctl->spec_skip, st)) != cudaSuccess) return e;
+    if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, 1, w.s, w.ctl, st)) != cudaSuccess) return e;
     if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, 1, w.ctl, st)) != cudaSuccess) return e;
   }
   // final basis -> W, then X0 = sgn_n(W)
@@ -702,7 +705,7 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     info->iters = c.iters_done;
     info->last_update_norm = c.last_upd;
     info->spectral_residual = c.spec_res;
-    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
+    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED | FLAG_SPEC_SHIFTED)) |
                   ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
     if (c.flags & FLAG_BAD_LAYOUT) {
       set_error("the packed A is inconsistent: an index or address left its buffer (access skipped)");

@@ -64,16 +64,6 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_stream_batch_ke
 }
 
 // ------------------------------------------------ per-instance kernels
-// Deterministic start V^0 of the spectral subspace iteration (any full-rank
-// start works; entries uniform in (-1, 1)).
-__device__ __forceinline__ float v0_entry(long long e) {
-  unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
-}
-
 // Prepares every instance in PHASE_ADMIT: clears its scratch, then either takes
 // X^0 from the caller (start_given) or writes the start V^0 of the spectral
 // subspace iteration, which the first (orthonormalising) pass turns into a basis.
@@ -96,11 +86,16 @@ __global__ void __launch_bounds__(256) batch_admit_kernel(const BatchDesc* descs
   if (d.start_given) {
     for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = d.Xout[e];
   } else {
-    for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = v0_entry(e);
+    for (long long e = threadIdx.x; e < (long long)rows * D; e += blockDim.x) d.X[0][e] = spec_v0_entry(e);
   }
   for (int e = threadIdx.x; e < kScrBytes / 8; e += blockDim.x) d.scr[e] = 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
+    d.scr[kScrShift] = 1.0;  // W = A_off V + V: subspace iteration on A itself
+    c->spec_skip = 0;
+    c->spec_restart = 0;
+    c->spec_round = 0;
+    c->spec_prev = 0;
     c->upd_acc = 0.0;
     c->last_upd = 0.0;
     c->spec_res = 0.0;
@@ -158,11 +153,16 @@ __device__ __forceinline__ double seg_sum(double v, int lane, int head) {
 //          stop decision (convergence or the pass cap moves the instance to
 //          PHASE_POLAR, the orthonormalising pass to PHASE_SPEC).
 // Basis buffers: pass s (spec_iters = s) reads V = X[(s + 1) & 1] and writes
-// X[s & 1]; the orthonormalising pass reads X[0] and writes X[1].
+// X[s & 1]; the orthonormalising pass reads X[0] and writes X[1], and so does a
+// restart pass (PHASE_SPECR), whose V^0 is regenerated from its formula
+// (spec_v0_entry) rather than read.
+// Shift: passes iterate on A_off + cI (W = Y + cV), c = scr[kScrShift], starting
+// at 1; when a pass converges, the algebraic top-d test (spec_shift_after)
+// accepts the basis or moves the instance to PHASE_SPECR with a larger c.
 template <int D>
 __device__ __forceinline__ void spec_buffers(const BatchDesc& d, int ph, const float*& V, float*& Vn) {
   const int si = d.ctl->spec_iters;
-  if (ph == PHASE_SPEC0) {
+  if (ph == PHASE_SPEC0 || ph == PHASE_SPECR) {
     V = d.X[0];
     Vn = d.X[1];
   } else {
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) batch_spec_gram_kernel(const BatchDesc* d
     const long long g = g0 + threadIdx.x;
     const int inst = chunk_instance(bbase, cnt, g0, total, g, s_range);
     const int ph = inst >= 0 ? descs[inst].ctl->phase : (int)PHASE_IDLE;
-    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0;
+    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0 || ph == PHASE_SPECR;
     double ww[DD], vw[DD];
 #pragma unroll
     for (int o = 0; o < DD; ++o) ww[o] = vw[o] = 0.0;
@@ -193,14 +193,16 @@ __global__ void __launch_bounds__(256) batch_spec_gram_kernel(const BatchDesc* d
       float* Vn;
       spec_buffers<D>(d, ph, V, Vn);
       const long long r0 = (g - bbase[inst]) * D;
+      // the orthonormalising passes take W = V^0 (Y is zero there)
+      const float shift = ph == PHASE_SPEC ? (float)d.scr[kScrShift] : 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         float v[D], w[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const long long e = (r0 + k) * D + c;
-          v[c] = V[e];
-          w[c] = d.Y[e] + v[c];
+          v[c] = ph == PHASE_SPECR ? spec_v0_entry(e) : V[e];
+          w[c] = ph == PHASE_SPEC ? d.Y[e] + shift * v[c] : v[c];
           d.W[e] = w[c];
           d.Y[e] = 0.f;
         }
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256) batch_spec_update_kernel(const BatchDesc*
     const long long g = g0 + threadIdx.x;
     const int inst = chunk_instance(bbase, cnt, g0, total, g, s_range);
     const int ph = inst >= 0 ? descs[inst].ctl->phase : (int)PHASE_IDLE;
-    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0;
+    const bool act = ph == PHASE_SPEC || ph == PHASE_SPEC0 || ph == PHASE_SPECR;
     double res = 0.0;
     if (act) {
       const BatchDesc& d = descs[inst];
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(256) batch_spec_update_kernel(const BatchDesc*
         double v[D], w[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          v[c] = V[(r0 + k) * D + c];
+          v[c] = ph == PHASE_SPECR ? spec_v0_entry((r0 + k) * D + c) : V[(r0 + k) * D + c];
           w[c] = d.W[(r0 + k) * D + c];
         }
 #pragma unroll
@@ -314,15 +316,35 @@ __global__ void __launch_bounds__(256) batch_spec_update_kernel(const BatchDesc*
         __threadfence();
         const double tot = atomicAdd(&d.scr[kScrRes], 0.0);
         d.scr[kScrRes] = 0.0;
-        if (ph == PHASE_SPEC0) {
+        if (ph == PHASE_SPEC0 || ph == PHASE_SPECR) {
           c->phase = PHASE_SPEC;
         } else {
           const int si = c->spec_iters;
           const double rel = sqrt(tot / fmax(d.scr[kScrH2], 1e-300));
           c->spec_res = rel;
           c->spec_iters = si + 1;
-          if (rel <= d.spec_tol) c->spec_stop = 1;
-          if (rel <= d.spec_tol || si + 1 >= d.smax) {
+          bool done = c->spec_prev + si + 1 >= d.smax;  // the pass cap counts every round
+          if (rel <= d.spec_tol) {
+            // algebraic top-d test on H = V^T (A_off + cI) V of this pass
+            double Hm[DD], tmp[DD];
+#pragma unroll
+            for (int o = 0; o < DD; ++o) Hm[o] = d.scr[kScrH + o];
+            const double c2 = spec_shift_after(Hm, D, d.scr[kScrShift], tmp);
+            if (c2 == 0.0) {
+              c->spec_stop = 1;
+              done = true;
+            } else if (c->spec_round >= kSpecMaxRestarts) {
+              done = true;  // spec_stop stays clear: reported as not converged
+            } else if (!done) {
+              d.scr[kScrShift] = c2;
+              c->spec_round += 1;
+              c->spec_prev += si + 1;
+              c->spec_iters = 0;
+              c->flags |= FLAG_SPEC_SHIFTED;
+              c->phase = PHASE_SPECR;
+            }
+          }
+          if (done) {
             c->phase = PHASE_POLAR;
             atomicSub(nspec, 1);
           }
@@ -423,7 +445,7 @@ __global__ void batch_report_kernel(const BatchDesc* descs, int count, BatchRepo
   const Ctl* c = descs[i].ctl;
   BatchReport r;
   r.phase = c->phase;
-  r.spec_iters = c->spec_iters;
+  r.spec_iters = c->spec_prev + c->spec_iters;
   r.iters = c->iters_done;
   r.flags = c->flags;
   r.last_upd = c->last_upd;
@@ -788,7 +810,7 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
       info[i].spectral_residual = rep[i].spec_res;
       info[i].objective = NAN;
       info[i].rel_decrease = NAN;
-      info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED)) |
+      info[i].flags = (rep[i].flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED | FLAG_SPEC_SHIFTED)) |
                       ((init && rep[i].spec_res > 1e-6) ? FLAG_SPEC_NOT_CONVERGED : 0u);
       timeout = timeout || (rep[i].flags & FLAG_TIMEOUT);
       bad = bad || (rep[i].flags & FLAG_BAD_LAYOUT);

@@ -11,6 +11,10 @@ namespace nsrgs {
 constexpr int PHASE_POLAR = 5;
 // First, orthonormalising spectral pass (W = V^0, no A-stream), after admission.
 constexpr int PHASE_SPEC0 = 6;
+// Orthonormalising pass of a restart: the spectral passes converged to a basis
+// that failed the algebraic top-d test and start again from V^0 under a larger
+// shift (spec_shift_after); like PHASE_SPEC0, but V^0 is regenerated, not read.
+constexpr int PHASE_SPECR = 7;
 
 // Per-instance float64 scratch of the spectral passes (doubles, D <= 4).
 constexpr int kScrWW = 0;     // W^T W accumulator, D x D
@@ -19,6 +23,7 @@ constexpr int kScrRinv = 32;  // R^{-1} of the Cholesky of W^T W
 constexpr int kScrH = 48;     // H = V^T W
 constexpr int kScrH2 = 64;    // ||H||_F^2
 constexpr int kScrRes = 65;   // residual accumulator
+constexpr int kScrShift = 66; // shift c of W = A_off V + c V
 constexpr int kScrBytes = 1024;
 
 struct BatchDesc {

@@ -198,6 +198,98 @@ __device__ inline void chol_inv(const double* G, double* Rinv, int D, double* Rt
   }
 }
 
+// Is sym(H) - sigma I positive definite?  Cholesky with a relative pivot floor;
+// one thread, M: D x D float64 scratch.
+__device__ inline bool sym_shift_pd(const double* H, int D, double sigma, double floor_abs, double* M) {
+  for (int j = 0; j < D; ++j) {
+    double p = H[j * D + j] - sigma;
+    for (int k = 0; k < j; ++k) p -= M[k * D + j] * M[k * D + j];
+    if (!(p > floor_abs)) return false;
+    const double rjj = sqrt(p);
+    M[j * D + j] = rjj;
+    for (int i = j + 1; i < D; ++i) {
+      double t = 0.5 * (H[j * D + i] + H[i * D + j]);
+      for (int k = 0; k < j; ++k) t -= M[k * D + j] * M[k * D + i];
+      M[j * D + i] = t / rjj;
+    }
+  }
+  return true;
+}
+
+// Spectral start, algebraic top-d test (Algorithm 2 asks for the eigenvectors of
+// the d largest eigenvalues of A).  Subspace iteration on A_off + cI converges to
+// the d eigenvalues of largest |lambda + c|.  At a converged basis V,
+// H = V^T (A_off + cI) V holds the Ritz values theta_k + c.  When the symmetric
+// part of H is positive definite, every eigenvalue left out has
+// |lambda + c| <= min_k (theta_k + c), hence lambda <= min_k theta_k: the captured
+// ones are the algebraic top d.  Otherwise a negative eigenvalue dominated and
+// the start must run again with a shift that lifts the spectrum's negative end.
+// The smallest eigenvalue mu of sym(H) (mu = min_k theta_k + c < 0) is bracketed
+// by bisection between the Gershgorin lower bound and 0, each probe a Cholesky
+// test (Sylvester's law of inertia), keeping the lower end lo <= mu; then
+// c' = c - 5/4 lo + 1 > -min_k theta_k.
+// Returns 0 when sym(H) is positive definite, else c'.  M: D x D float64
+// scratch.  One thread; D <= 64.
+__device__ inline double spec_shift_after(const double* H, int D, double c, double* M) {
+  double dmax = 0.0;
+  for (int k = 0; k < D; ++k) dmax = fmax(dmax, fabs(H[k * D + k]));
+  const double floor_abs = 1e-12 * dmax;
+  if (dmax > 0.0 && sym_shift_pd(H, D, 0.0, floor_abs, M)) return 0.0;
+  double lo = 0.0;
+  for (int k = 0; k < D; ++k) {
+    double r = H[k * D + k];
+    for (int l = 0; l < D; ++l)
+      if (l != k) r -= 0.5 * fabs(H[k * D + l] + H[l * D + k]);
+    lo = fmin(lo, r);
+  }
+  lo -= 1e-9 * dmax + 1e-300;  // strictly below the spectrum
+  double hi = 0.0;
+  for (int it = 0; it < 48 && hi - lo > 1e-6 * (fabs(lo) + 1.0); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sym_shift_pd(H, D, mid, 0.0, M)) lo = mid;
+    else hi = mid;
+  }
+  return c - 1.25 * lo + 1.0;
+}
+
+// Entry e of the deterministic spectral start V^0 (any full-rank start works;
+// entries uniform in (-1, 1), a splitmix64 hash of e).
+__device__ __forceinline__ float spec_v0_entry(long long e) {
+  unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+// End of a counted spectral pass (one thread): `tot` = ||W - V H||_F^2.  A restart
+// pass only orthonormalises V^0.  Otherwise the relative residual is recorded
+// and, once it is <= tol, the algebraic top-d test decides: stop, or restart from
+// V^0 with the larger shift (at most kSpecMaxRestarts times; after that the
+// passes halt with spec_stop clear, reported as not converged).
+__device__ inline void spec_finish_pass(double tot, int D, double tol, const SpecScratch& s, Ctl* ctl) {
+  ctl->spec_iters += 1;
+  if (ctl->spec_restart) {
+    ctl->spec_restart = 0;
+    return;
+  }
+  const double rel = sqrt(tot / fmax(s.scal[0], 1e-300));
+  ctl->spec_res = rel;
+  if (!(rel <= tol)) return;
+  const double c2 = spec_shift_after(s.H, D, s.scal[3], s.M);
+  if (c2 == 0.0) {
+    ctl->spec_stop = 1;
+    ctl->spec_skip = 1;
+  } else if (ctl->spec_round >= kSpecMaxRestarts) {
+    ctl->spec_skip = 1;
+  } else {
+    s.scal[3] = c2;
+    ctl->spec_restart = 1;
+    ctl->spec_round += 1;
+    ctl->flags |= FLAG_SPEC_SHIFTED;
+  }
+}
+
 // ---------------------------------------------------- Algorithm 2, one block
 // For block i (Algorithm 2's loop body, §2.2 projection):
 //   G = (n-1) X_i - Y_i,  P = (G - X_i G^T X_i)/2,  F = X_i - eta P,

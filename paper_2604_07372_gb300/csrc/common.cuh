@@ -48,8 +48,16 @@ struct Ctl {
   int spec_iters;          // subspace iterations run
   int spec_stop;           // set when the subspace residual fell below tol
   int phase;               // batched / served instances: PHASE_*
+  int spec_skip;           // spectral passes return at once (converged, or halted)
+  int spec_restart;        // the next spectral pass restarts from V^0 with a larger shift
+  int spec_round;          // restarts taken so far
+  int spec_prev;           // batched / served instances: passes run before the last restart
   int pad;
 };
+
+// Restarts the spectral start may take with a larger shift before it gives up
+// (then it reports the subspace as not converged).
+constexpr int kSpecMaxRestarts = 3;
 
 // Phase of an instance in the batched and served forms.
 enum : int {
@@ -67,6 +75,7 @@ enum : unsigned int {
   FLAG_TIMEOUT = 1u << 3,
   FLAG_NS_SAFEGUARDED = 1u << 4,  // the safeguarded Newton-Schulz start was used for some block
   FLAG_BAD_LAYOUT = 1u << 5,      // a packed buffer's index or address left its buffer (access skipped)
+  FLAG_SPEC_SHIFTED = 1u << 6,    // the spectral start restarted with a larger shift (see spec_shift_after)
 };
 
 // float64 scratch of the spectral initialisation and of d_F (all d x d unless noted).
@@ -76,7 +85,7 @@ struct SpecScratch {
   double* Rinv;      // chol(W^T W)^{-1}
   double* M;         // scratch / Y^T X
   double* Q;         // sgn(Y^T X)
-  double* scal;      // [0] ||H||_F^2, [1] d_F^2, [2] residual accumulator
+  double* scal;      // [0] ||H||_F^2, [1] d_F^2, [2] residual accumulator, [3] shift c of W = A_off V + c V
   double* partials;  // per-CTA partial sums
 };
 

@@ -298,14 +298,18 @@ constexpr int kRowsPerCta = 64;
 
 __global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restrict__ V, float* __restrict__ Yv,
                                                            float* __restrict__ W, const float* __restrict__ Xq,
-                                                           long long rows, int D, float shift, int mode,
-                                                           SpecScratch s, Ctl* ctl) {
+                                                           long long rows, int D, float shift, int dev_shift,
+                                                           int mode, SpecScratch s, Ctl* ctl) {
   // mode 0: spectral Gram (W = Y + shift V; outputs W^T W and V^T W); mode 1: M = Yv^T Xq.
   // The chunk is staged as float64 (exact conversions, once per element), so the
   // inner products are float64 FMAs alone: GB300 runs float64 conversions on the
   // same slow pipe as float64 arithmetic.
   extern __shared__ __align__(16) double smg[];
-  if (mode == 0 && ctl->spec_stop) return;
+  if (mode == 0 && ctl->spec_skip) return;
+  // spectral mode: W = Y + c V, c the orthonormalising pass's `shift` or the current
+  // shift; a restart pass (after a failed algebraic top-d test) takes W = V^0
+  const bool restart = mode == 0 && dev_shift && ctl->spec_restart;
+  const float c = (mode == 0 && dev_shift) ? (float)s.scal[3] : shift;
   const int DD = D * D;
   const int nout = mode == 0 ? 2 * DD : DD;
   double* P = smg;                     // kRowsPerCta x D
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restri
       const long long ge = r0 * D + e;
       if (mode == 0) {
         const float v = V[ge];
-        const float w = Yv[ge] + shift * v;
+        const float w = restart ? spec_v0_entry(ge) : Yv[ge] + c * v;
         W[ge] = w;
         Yv[ge] = 0.f;
         P[e] = v;
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
                                                              SpecScratch s, double tol, int count_pass, Ctl* ctl) {
   extern __shared__ __align__(16) double smu[];
   __shared__ double sh[32];
-  if (ctl->spec_stop) return;
+  if (ctl->spec_skip) return;
   const int DD = D * D;
   double* rinv = smu;
   double* hh = smu + DD;
@@ -427,12 +431,7 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
     if (threadIdx.x == 0) {
       const double tot = atomicAdd(&s.scal[2], 0.0);
       ctl->counter = 0u;
-      if (count_pass) {
-        const double rel = sqrt(tot / fmax(s.scal[0], 1e-300));
-        ctl->spec_res = rel;
-        ctl->spec_iters += 1;
-        if (rel <= tol) ctl->spec_stop = 1;
-      }
+      if (count_pass) spec_finish_pass(tot, D, tol, s, ctl);
     }
   }
 }
@@ -507,9 +506,9 @@ cudaError_t launch_gpm_generic(const float* X, float* Y, float* Xout, int n, int
 }
 
 cudaError_t launch_spec_gram_generic(const float* V, float* Y, float* W, long long rows, int d, float shift,
-                                     const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+                                     int dev_shift, const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
   gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(V, Y, W, nullptr, rows, d,
-                                                                                        shift, 0, s, ctl);
+                                                                                        shift, dev_shift, 0, s, ctl);
   return cudaGetLastError();
 }
 
@@ -528,8 +527,8 @@ cudaError_t launch_polar_generic(const float* V, float* X0, int n, int d, cudaSt
 cudaError_t launch_dF_generic(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
                               cudaStream_t st) {
   gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(nullptr, const_cast<float*>(Yv),
-                                                                                        nullptr, X, rows, d, 0.f, 1, s,
-                                                                                        ctl);
+                                                                                        nullptr, X, rows, d, 0.f, 0, 1,
+                                                                                        s, ctl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   polar_single_kernel<<<1, 256, 4 * d * d * sizeof(double), st>>>(s, d);

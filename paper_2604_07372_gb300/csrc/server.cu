@@ -359,7 +359,7 @@ extern "C" nsrgs_status nsrgs_server_step(nsrgs_server* s, int* active, int* que
       res.iters = r.iters;
       res.spectral_iters = r.spec_iters;
       res.last_update_norm = r.last_upd;
-      res.flags = r.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND);
+      res.flags = r.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_SPEC_SHIFTED);
       s->finished.push_back(res);
       s->alloc.release(sl.a_off, sl.a_bytes);
       s->alloc.release(sl.w_off, sl.w_bytes);

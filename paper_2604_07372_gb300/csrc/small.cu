@@ -97,26 +97,30 @@ __global__ void __launch_bounds__(128) gpm_epilogue_kernel(const float* __restri
 
 // ------------------------------------------- spectral init: subspace steps
 // Deterministic start V0 (any full-rank start works; entries uniform in (-1, 1)).
-__global__ void spec_v0_kernel(float* V, long long rows, int D) {
+// With shift_slot non-null the spectral shift starts at c = 1 (W = A_off V + V,
+// i.e. subspace iteration on A itself, A_ii = I).
+__global__ void spec_v0_kernel(float* V, long long rows, int D, double* shift_slot) {
   const long long total = rows * D;
+  if (shift_slot && blockIdx.x == 0 && threadIdx.x == 0) *shift_slot = 1.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    V[e] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
-  }
+       e += (long long)gridDim.x * blockDim.x)
+    V[e] = spec_v0_entry(e);
 }
 
-// W = Y + shift V (written to W, Y zeroed), partial sums of W^T W and V^T W;
+// W = Y + c V (written to W, Y zeroed), partial sums of W^T W and V^T W;
 // the last CTA reduces them, forms H = V^T W, ||H||_F^2 and Rinv = chol(W^T W)^{-1}.
+// c is `shift` for the orthonormalising pass (dev_shift = 0) and the current
+// shift s.scal[3] otherwise.  A pass after a failed algebraic top-d test
+// (ctl->spec_restart) takes W = V^0 instead: the start again, to be
+// orthonormalised under the new shift.
 template <int D>
 __global__ void __launch_bounds__(256) spec_gram_kernel(const float* __restrict__ V, float* __restrict__ Y,
                                                         float* __restrict__ W, long long rows, float shift,
-                                                        SpecScratch s, Ctl* ctl) {
+                                                        int dev_shift, SpecScratch s, Ctl* ctl) {
   __shared__ double sh[32];
-  if (ctl->spec_stop) return;
+  if (ctl->spec_skip) return;
+  const bool restart = dev_shift && ctl->spec_restart;
+  const float c = dev_shift ? (float)s.scal[3] : shift;
   double ww[D][D], vw[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(256) spec_gram_kernel(const float* __restrict_
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       v[k] = V[r * D + k];
-      w[k] = Y[r * D + k] + shift * v[k];
+      w[k] = restart ? spec_v0_entry(r * D + k) : Y[r * D + k] + c * v[k];
       W[r * D + k] = w[k];
       Y[r * D + k] = 0.f;
     }
@@ -171,14 +175,15 @@ __global__ void __launch_bounds__(256) spec_gram_kernel(const float* __restrict_
 }
 
 // Vnew = W Rinv and the residual ||W - V H||_F; the last CTA finishes the
-// residual ||A V - V H||_F / ||H||_F and sets spec_stop when it is <= tol.
+// residual ||A V - V H||_F / ||H||_F and, when it is <= tol, applies the
+// algebraic top-d test (spec_finish_pass).
 template <int D>
 __global__ void __launch_bounds__(256) spec_update_kernel(const float* __restrict__ V, const float* __restrict__ W,
                                                           float* __restrict__ Vnew, long long rows, SpecScratch s,
                                                           double tol, int count_pass, Ctl* ctl) {
   __shared__ double sh[32];
   __shared__ double rinv[D * D], hh[D * D];
-  if (ctl->spec_stop) return;
+  if (ctl->spec_skip) return;
   for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
     rinv[o] = s.Rinv[o];
     hh[o] = s.H[o];
@@ -212,12 +217,7 @@ __global__ void __launch_bounds__(256) spec_update_kernel(const float* __restric
     if (threadIdx.x == 0) {
       const double tot = atomicAdd(&s.scal[2], 0.0);
       ctl->counter = 0u;
-      if (count_pass) {
-        const double rel = sqrt(tot / fmax(s.scal[0], 1e-300));
-        ctl->spec_res = rel;
-        ctl->spec_iters += 1;
-        if (rel <= tol) ctl->spec_stop = 1;
-      }
+      if (count_pass) spec_finish_pass(tot, D, tol, s, ctl);
     }
   }
 }
@@ -353,8 +353,8 @@ __global__ void select_copy_kernel(const float* __restrict__ B0, const float* __
 // Runtime-d versions for 8 < d <= 64 (generic.cu).
 cudaError_t launch_epilogue_generic(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
                                     cudaStream_t);
-cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, const SpecScratch&, Ctl*,
-                                     cudaStream_t);
+cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, int, const SpecScratch&,
+                                     Ctl*, cudaStream_t);
 cudaError_t launch_spec_update_generic(const float*, const float*, float*, long long, int, const SpecScratch&,
                                        double, int, Ctl*, cudaStream_t);
 cudaError_t launch_polar_generic(const float*, float*, int, int, cudaStream_t);
@@ -390,16 +390,16 @@ int reduce_grid(long long rows) {
   return (int)g;
 }
 
-cudaError_t launch_spec_v0(float* V, long long rows, int d, cudaStream_t st) {
-  spec_v0_kernel<<<reduce_grid(rows), 256, 0, st>>>(V, rows, d);
+cudaError_t launch_spec_v0(float* V, long long rows, int d, double* shift_slot, cudaStream_t st) {
+  spec_v0_kernel<<<reduce_grid(rows), 256, 0, st>>>(V, rows, d, shift_slot);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows, int d, float shift,
+cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows, int d, float shift, int dev_shift,
                              const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
-  if (d > kDmaxSmall) return launch_spec_gram_generic(V, Y, W, rows, d, shift, s, ctl, st);
+  if (d > kDmaxSmall) return launch_spec_gram_generic(V, Y, W, rows, d, shift, dev_shift, s, ctl, st);
   const int grid = reduce_grid(rows);
-#define L(DD) spec_gram_kernel<DD><<<grid, 256, 0, st>>>(V, Y, W, rows, shift, s, ctl)
+#define L(DD) spec_gram_kernel<DD><<<grid, 256, 0, st>>>(V, Y, W, rows, shift, dev_shift, s, ctl)
   NSRGS_DISPATCH_D(d, L)
 #undef L
   return cudaGetLastError();

@@ -193,6 +193,31 @@ def make_instance(n: int, d: int, sigma: float, seed: int, p: float = 1.0, dtype
     return Instance(n=n, d=d, sigma=float(sigma), p=float(p), seed=int(seed), Z=Z, upper=up)
 
 
+def make_negative_dominated(n: int, d: int, seed: int, beta: float = 1.5, sigma: float = 0.2,
+                            dtype=np.float32) -> Instance:
+    """An instance whose largest-magnitude eigenvalues are negative.
+
+    The measurement model above (small noise sigma) minus beta * n * M_off, where
+    M = U U^T for a random orthonormal nd x d basis U and M_off is M with its
+    diagonal blocks zeroed (so A_ii = I still holds).  The spectrum then has d
+    eigenvalues near n (the ground truth Z, the algebraic top d) and d near
+    -beta * n, which dominate in magnitude for beta > 1.  Input for checking
+    that a spectral start finds the algebraic top d; a seeded second stream
+    [seed, 1] draws U.
+    """
+    base = make_instance(n, d, sigma, seed, dtype=np.float64)
+    U = dense_from_upper(base.upper, n, d) - np.eye(n * d)
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    Q, _ = np.linalg.qr(rng.standard_normal((n * d, d)))
+    U -= beta * n * (Q @ Q.T)
+    up = np.empty((num_upper_blocks(n), d, d), dtype=dtype)
+    for i in range(n - 1):
+        for j in range(i + 1, n):
+            up[upper_index(i, j, n)] = U[i * d : (i + 1) * d, j * d : (j + 1) * d]
+    return Instance(n=n, d=d, sigma=float(sigma), p=1.0, seed=int(seed), Z=base.Z, upper=up,
+                    meta={"beta": float(beta)})
+
+
 @dataclass
 class SEInstance:
     """Poses (Z_i, tau_i) and measurements of the SE(d) form.

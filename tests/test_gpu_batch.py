@@ -132,3 +132,22 @@ def test_block_sparse_batch_alone_and_against_oracle(P, storage):
         if storage == "bcsr_f32" and I.n > 2:
             Xo, _ = O.nsrgs(I.dense(), I.n, d, 1.0 / I.n, T, K)
             assert O.dF(to64(X), Xo, d) / math.sqrt(I.n * d) <= 1e-5
+
+
+def test_batched_spectral_start_takes_the_algebraic_top_d(P):
+    """An instance whose magnitude-dominant eigenvalues are negative, batched with
+    ordinary ones: its spectral phase restarts under a larger shift (flag bit 6)
+    and every instance's start and final iterate match the oracle's."""
+    d, T, K = 3, 20, 2
+    insts = [synth.make_negative_dominated(120, d, seed=3), inst(150, d, 0.3, seed=8),
+             synth.make_negative_dominated(90, d, seed=5, beta=2.0), inst(60, d, 0.3, seed=9)]
+    packs = [pack(P, I, P.F32) for I in insts]
+    Xs, infos = P.nsrgs_batch_solve(packs, [1.0 / I.n for I in insts], T, K, init=True, spectral_max_iters=400)
+    torch.cuda.synchronize()
+    for k, (I, X, info) in enumerate(zip(insts, Xs, infos)):
+        A = I.dense()
+        Xo, _ = O.nsrgs(A, I.n, d, 1.0 / I.n, T, K)
+        shifted = bool(info.flags & (1 << 6))
+        assert shifted == (k in (0, 2)), (k, info.as_dict())
+        assert info.iters == T and info.spectral_residual <= 1e-6, info.as_dict()
+        assert O.dF(to64(X), Xo, d) / math.sqrt(I.n * d) <= 1e-5, (k, info.as_dict())

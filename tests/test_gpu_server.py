@@ -138,3 +138,37 @@ def test_sparse_and_dense_requests_share_ticks(P):
         assert abs(r.iters - ia.iters) <= 1
         assert O.dF(to64(Xs[k]), to64(Xa), d) / math.sqrt(I.n * d) <= 1e-5
     srv.close()
+
+
+def test_served_requests_match_the_oracle(P):
+    """Served results against the FP64 oracle (not only against the GPU alone):
+    a small sparse request (n = 150, p = 0.08, where the signal eigenvalue pn is
+    not far above the noise edge), a dense one, and one whose magnitude-dominant
+    eigenvalues are negative (its spectral phase must restart under a larger
+    shift to take the algebraic top d).  Each result is compared with the oracle
+    run for the same number of iterations from its own (eigh) spectral start."""
+    d, tol, Tmax = 3, 1e-6, 1500
+    insts = [synth.make_instance(150, d, synth.sigma_rule(0.3, 150, d), seed=61, p=0.08, dtype=np.float32),
+             synth.make_instance(200, d, synth.sigma_rule(0.3, 200, d), seed=62, dtype=np.float32),
+             synth.make_negative_dominated(110, d, seed=63)]
+    ups = [torch.from_numpy(I.upper).cuda() for I in insts]
+    srv = P.Server(d, P.F32, max_slots=3, arena_bytes=128 << 20, ticks_per_step=4, spectral_max_iters=400)
+    Xs = [torch.empty(I.n * d, d, device="cuda") for I in insts]
+    ids, done = {}, {}
+    for k, I in enumerate(insts):
+        ids[srv.submit(ups[k], I.n, 1.0 / I.n, Tmax, tol, Xs[k])] = k
+    for _ in range(3000):
+        srv.step()
+        for r in srv.poll():
+            done[ids[r.id]] = r
+        if len(done) == len(insts):
+            break
+    assert len(done) == len(insts)
+    torch.cuda.synchronize()
+    assert done[2].flags & (1 << 6), "the negative-dominated request did not restart its spectral phase"
+    for k, I in enumerate(insts):
+        r = done[k]
+        assert r.status == 0 and r.last_update_norm < tol, (k, r.status, r.iters, r.last_update_norm)
+        Xo, _ = O.nsrgs(I.dense(), I.n, d, 1.0 / I.n, r.iters, 2)
+        assert O.dF(to64(Xs[k]), Xo, d) / math.sqrt(I.n * d) <= 1e-5, (k, r.iters)
+    srv.close()

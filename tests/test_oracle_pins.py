@@ -478,3 +478,35 @@ def test_stiefel_fixed_point_at_sigma_zero():
     X = Xb.reshape(n * d, p)
     X1 = O.stiefel_iteration(A, X, n, d, 1.0 / n, 2)
     assert np.allclose(X1, X, atol=1e-12)
+
+
+# ------------------------------------------------- update norm (retire rule)
+@pytest.mark.parametrize("th", [math.pi / 3, 0.25, 2.0])
+def test_update_norm_closed_form_two_blocks(th):
+    """||X' - X||_F / sqrt(nd) on n = 2 blocks in O(2): X = (I; I), X' = (R(th); I).
+    By hand ||R(th) - I||_F^2 = 2((cos th - 1)^2 + sin^2 th) = 4 - 4 cos th, and
+    nd = 4 rows, so the norm is sqrt(1 - cos th): a sqrt(n) or sqrt(n d^2)
+    normaliser, or a norm over one block only, gives another number."""
+    X = np.vstack([np.eye(2), np.eye(2)])
+    Xn = np.vstack([rot(th), np.eye(2)])
+    assert O.update_norm(Xn, X) == pytest.approx(math.sqrt(1.0 - math.cos(th)), rel=1e-14)
+    # symmetric in its arguments and zero at no change
+    assert O.update_norm(X, Xn) == pytest.approx(O.update_norm(Xn, X), rel=1e-15)
+    assert O.update_norm(X, X) == 0.0
+    # three nodes, d = 1: X' - X = (3, 0, 4) gives 5 / sqrt(3)
+    assert O.update_norm(np.array([[3.0], [0.0], [4.0]]), np.zeros((3, 1))) == pytest.approx(5.0 / math.sqrt(3.0))
+
+
+def test_se_update_norm_closed_form():
+    """sqrt((||X' - X||_F^2 + ||t' - t||^2) / (nd)) with n = 2, d = 2: the rotation
+    part as above (4 - 4 cos th) and a translation change (3, 4) at node 0
+    (25), so the norm is sqrt((29 - 4 cos th) / 4)."""
+    th = 0.7
+    X = np.vstack([np.eye(2), np.eye(2)])
+    Xn = np.vstack([rot(th), np.eye(2)])
+    t = np.zeros((2, 2))
+    tn = np.array([[3.0, 4.0], [0.0, 0.0]])
+    want = math.sqrt((29.0 - 4.0 * math.cos(th)) / 4.0)
+    assert O.se_update_norm(Xn, X, tn, t, 2, 2) == pytest.approx(want, rel=1e-14)
+    # with no translation change it is the rotation-only norm
+    assert O.se_update_norm(Xn, X, t, t, 2, 2) == pytest.approx(O.update_norm(Xn, X), rel=1e-14)
