@@ -140,9 +140,17 @@ def test_product_uses_exactly_the_stored_values(P, n, d, storage):
 
 @pytest.mark.parametrize("n,d", [(131, 3), (200, 4)])
 def test_dense_and_upper_sources_pack_the_same_bytes(P, n, d):
+    """The tables, the FP8 scales and the panels are the same from either source
+    (the header's alignment padding is left unwritten by both)."""
     inst = synth.make_instance(n, d, 0.4, seed=5 * n + d, dtype=np.float32)
     for storage in (BF16, FP8):
         a = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, storage)
         b = P.nsrgs_pack_dense(torch.from_numpy(inst.dense(dtype=np.float32)).cuda(), n, d, storage)
         torch.cuda.synchronize()
-        assert torch.equal(a.buf, b.buf)
+        g = Geom(n, d, storage)
+        tab = 16 * (g.nslabs + 1)
+        parts = [(0, tab), (g.header_bytes(), g.header_bytes() + g.panel_bytes())]
+        if storage == FP8:
+            parts.append((tab, tab + 4 * n))
+        for lo, hi in parts:
+            assert torch.equal(a.buf[lo:hi], b.buf[lo:hi]), (storage, lo, hi)
