@@ -375,19 +375,46 @@ size_t nsrgs_batch_workspace_bytes(const int* n, int count, int d);
 /* Solves `count` independent instances (Algorithm 2 for each: spectral start
  * when init != 0, then T iterations with K Newton-Schulz steps; tol > 0 stops
  * an instance after its first iteration with update norm below tol) in one
- * CUDA-graph replay.  All instances share d (1..4) and the storage (F32, BF16
- * or FP8E4M3 panels, or BCSR_F32 / BCSR_BF16 block-sparse rows, streamed by a
- * warp-per-row kernel); n and eta differ per instance.  Each tick is one
- * A-stream launch over every active instance (their steps concatenated and
- * split evenly over the SMs) plus one launch with a CTA per instance for the
- * d x d work, so instances in their spectral phase and in their iterations
- * advance in the same tick.  `info` (host array of count, nullable) is filled
+ * CUDA-graph replay or one persistent launch (nsrgs_batch_set_path).  All
+ * instances share d (1..4) and the storage (F32, BF16 or FP8E4M3 panels, or
+ * BCSR_F32 / BCSR_BF16 block-sparse rows, streamed by a warp-per-row kernel);
+ * n and eta differ per instance.  On the tick path each tick is one A-stream
+ * launch over every active instance (their steps concatenated and split evenly
+ * over the SMs) plus grid-wide launches for the d x d work, so instances in
+ * their spectral phase and in their iterations advance in the same tick.  `info` (host array of count, nullable) is filled
  * after a synchronisation.  items, the packed buffers and X must stay valid
  * until the work on `st` completes.  The batched form has no counterpart in
  * the paper beyond running Algorithm 2 on each instance. */
 nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int count, int d, int storage, int T, int K,
                                double tol, int init, int spectral_max_iters, nsrgs_info* info, void* ws,
                                size_t ws_bytes, void* st);
+
+/* How nsrgs_batch_solve runs a batch of panel-stored instances (block-sparse
+ * batches always take the tick path):
+ *  NSRGS_BATCH_TICKS      : the tick path above -- per tick one A-stream launch over
+ *                           every active instance plus grid-wide d x d launches,
+ *                           replayed from a CUDA graph;
+ *  NSRGS_BATCH_PERSISTENT : one persistent launch (a CTA per SM) in which each CTA
+ *                           takes whole instances from a device work counter,
+ *                           largest first, and runs each one's spectral start and
+ *                           T iterations alone: A passes through the same panel
+ *                           pipeline, the d x d work with CTA-local reductions, no
+ *                           grid-wide step.  An instance whose panels (stored
+ *                           densely with each step's X rows) fit the CTA's stage
+ *                           space is loaded into shared memory once and read from
+ *                           there on every later pass;
+ *  NSRGS_BATCH_AUTO       : (default) the first call for a batch shape (sizes, d,
+ *                           storage, T, K, tol, start, pass cap, workspace) runs both
+ *                           paths, each a complete solve, times them with CUDA events
+ *                           and keeps the faster for later calls of that shape.
+ * Both paths compute the same iteration per instance; results agree to the
+ * run-to-run spread of the float32 atomic sums.  The setting is process-wide.
+ * No counterpart in the paper: these are execution strategies. */
+enum { NSRGS_BATCH_AUTO = 0, NSRGS_BATCH_TICKS = 1, NSRGS_BATCH_PERSISTENT = 2 };
+nsrgs_status nsrgs_batch_set_path(int path);
+/* The path (NSRGS_BATCH_TICKS or NSRGS_BATCH_PERSISTENT) the most recent
+ * nsrgs_batch_solve on the calling thread ran with (0 before any call). */
+int nsrgs_batch_last_path(void);
 
 /* -------------------------------------------------------- served form */
 

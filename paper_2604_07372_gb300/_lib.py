@@ -554,6 +554,25 @@ def nsrgs_batch_solve(
     return Xs, (list(infos) if infos is not None else None)
 
 
+BATCH_AUTO, BATCH_TICKS, BATCH_PERSISTENT = 0, 1, 2
+
+
+def nsrgs_batch_set_path(path: int) -> None:
+    """Path of nsrgs_batch_solve: BATCH_AUTO (timed once per batch shape), BATCH_TICKS, BATCH_PERSISTENT."""
+    fn = lib().nsrgs_batch_set_path
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int]
+    _check(fn(path))
+
+
+def nsrgs_batch_last_path() -> int:
+    """The path the most recent nsrgs_batch_solve on this thread ran with."""
+    fn = lib().nsrgs_batch_last_path
+    fn.restype = ctypes.c_int
+    fn.argtypes = []
+    return int(fn())
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [
         ("d", ctypes.c_int),

@@ -599,12 +599,14 @@ size_t batch_instance_bytes(int n, int d) {
 }
 
 // Table region: descriptors | panel step bases | reports | block-sparse row bases |
-// block bases | counters (256 bytes: instances in a spectral phase).
+// block bases | counters (256 bytes: instances in a spectral phase, the
+// persistent form's work counter) | the persistent form's instance order.
 size_t batch_table_bytes(int count) {
   const size_t t = ((size_t)count * sizeof(BatchDesc) + 255) / 256 * 256;
   const size_t b = ((size_t)(count + 1) * sizeof(long long) + 255) / 256 * 256;
   const size_t r = ((size_t)count * sizeof(BatchReport) + 255) / 256 * 256;
-  return t + 3 * b + r + 256;
+  const size_t o = ((size_t)count * sizeof(int) + 255) / 256 * 256;
+  return t + 3 * b + r + 256 + o;
 }
 
 void fill_instance(BatchDesc& ds, uint8_t* region, int n, int d) {
@@ -636,6 +638,11 @@ struct BatchGraphKey {
 std::mutex g_bmu;
 std::vector<std::pair<BatchGraphKey, cudaGraphExec_t>> g_bgraphs;
 cudaStream_t g_bcap[64] = {};
+// Path of the batched form: requested (process-wide) and chosen per batch shape
+// by timing both paths once (cached with the graph key).
+int g_batch_path_req = NSRGS_BATCH_AUTO;
+thread_local int g_batch_last_path = 0;
+std::vector<std::pair<BatchGraphKey, int>> g_btuned;
 
 uint64_t fnv(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
   const unsigned char* c = static_cast<const unsigned char*>(p);
@@ -697,6 +704,8 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   long long* d_rbase = reinterpret_cast<long long*>(base + tbytes + bbytes + rbytes);
   long long* d_bbase = reinterpret_cast<long long*>(base + tbytes + 2 * bbytes + rbytes);
   int* d_nspec = reinterpret_cast<int*>(base + tbytes + 3 * bbytes + rbytes);
+  int* d_next = d_nspec + 1;
+  int* d_order = reinterpret_cast<int*>(base + tbytes + 3 * bbytes + rbytes + 256);
   std::vector<BatchDesc> descs(count);
   std::vector<long long> bases(count + 1), rbases(count + 1), bbases(count + 1);
   size_t off = batch_table_bytes(count);
@@ -730,13 +739,24 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
     ds.smax = init ? spectral_max_iters : 0;
     ds.start_given = init ? 0 : 1;
     ds.safeguard = items[i].ns_safeguard ? 1 : 0;
+    ds.resident = sparse ? 0 : (persist_fits_resident(ds.g) ? 1 : 0);
     bases[i] = steps;
     steps += ds.g.total_steps;
   }
   bases[count] = steps;
   rbases[count] = rows;
   bbases[count] = blocks;
-  if (!sparse) NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
+  // persistent form: instances in decreasing order of panel steps (the longest
+  // solves start first, the short ones fill the tail)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return descs[a].g.total_steps > descs[b].g.total_steps; });
+  if (!sparse) {
+    NSRGS_CUDA_TRY(batch_stream(nullptr, nullptr, 0, d, storage, st, true));
+    NSRGS_CUDA_TRY(batch_persist(nullptr, nullptr, 0, nullptr, d, storage, st, true));
+  }
+  NSRGS_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_base, bases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(d_rbase, rbases.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
@@ -757,53 +777,104 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   key.tol = tol;
   key.ws = ws;
   key.dev = dev;
+  // ---- the tick path: admit + (passes + T) ticks replayed from a graph
+  auto prepare_ticks = [&](cudaGraphExec_t* out) -> nsrgs_status {
+    cudaGraphExec_t exec = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_bmu);
+      for (auto& e : g_bgraphs)
+        if (e.first == key) exec = e.second;
+    }
+    if (!exec) {
+      if (!g_bcap[dev]) NSRGS_CUDA_TRY(cudaStreamCreateWithFlags(&g_bcap[dev], cudaStreamNonBlocking));
+      cudaStream_t cs = g_bcap[dev];
+      NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = batch_reset(d_descs, count, d_nspec, cs);
+      if (e == cudaSuccess) e = batch_admit(d_descs, count, d, d_nspec, cs);
+      // + the orthonormalising pass, + one orthonormalising pass per spectral restart
+      const int ticks = (init ? spectral_max_iters + 1 + kSpecMaxRestarts : 0) + T;
+      for (int t = 0; t < ticks && e == cudaSuccess; ++t) {
+        e = sparse ? batch_bcsr_stream(d_descs, d_rbase, count, d, storage == NSRGS_BCSR_BF16, rows, cs)
+                   : batch_stream(d_descs, d_base, count, d, storage, cs, false);
+        if (e == cudaSuccess) e = batch_spec(d_descs, d_bbase, count, d, blocks, d_nspec, cs);
+        if (e == cudaSuccess) e = batch_block(d_descs, d_bbase, count, d, blocks, cs);
+      }
+      if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error(std::string("batch graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return NSRGS_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return NSRGS_ERR_CUDA;
+      }
+      std::lock_guard<std::mutex> lk(g_bmu);
+      g_bgraphs.emplace_back(key, exec);
+      if (g_bgraphs.size() > 8) {
+        cudaGraphExecDestroy(g_bgraphs.front().second);
+        g_bgraphs.erase(g_bgraphs.begin());
+      }
+    }
+    *out = exec;
+    return NSRGS_OK;
+  };
+  // ---- the persistent path: one launch over every instance, then the report
+  auto launch_persist = [&]() -> nsrgs_status {
+    NSRGS_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(int), st));
+    NSRGS_CUDA_TRY(batch_persist(d_descs, d_order, count, d_next, d, storage, st, false));
+    NSRGS_CUDA_TRY(batch_report(d_descs, count, d_rep, st));
+    return NSRGS_OK;
+  };
+  int path = sparse ? NSRGS_BATCH_TICKS : g_batch_path_req;
+  if (path == NSRGS_BATCH_AUTO) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto& e : g_btuned)
+      if (e.first == key) path = e.second;
+  }
   cudaGraphExec_t exec = nullptr;
-  {
+  if (path == NSRGS_BATCH_AUTO) {
+    // autotune: time both paths once on this batch (each run is a complete,
+    // valid solve; the second one's results are the call's) and keep the faster
+    nsrgs_status s2 = prepare_ticks(&exec);
+    if (s2 != NSRGS_OK) return s2;
+    cudaEvent_t ev[3];
+    for (auto& e : ev) NSRGS_CUDA_TRY(cudaEventCreate(&e));
+    NSRGS_CUDA_TRY(cudaEventRecord(ev[0], st));
+    NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
+    NSRGS_CUDA_TRY(cudaEventRecord(ev[1], st));
+    if ((s2 = launch_persist()) != NSRGS_OK) return s2;
+    NSRGS_CUDA_TRY(cudaEventRecord(ev[2], st));
+    NSRGS_CUDA_TRY(cudaEventSynchronize(ev[2]));
+    float t_ticks = 0.f, t_persist = 0.f;
+    NSRGS_CUDA_TRY(cudaEventElapsedTime(&t_ticks, ev[0], ev[1]));
+    NSRGS_CUDA_TRY(cudaEventElapsedTime(&t_persist, ev[1], ev[2]));
+    for (auto& e : ev) cudaEventDestroy(e);
+    path = t_persist <= t_ticks ? NSRGS_BATCH_PERSISTENT : NSRGS_BATCH_TICKS;
     std::lock_guard<std::mutex> lk(g_bmu);
-    for (auto& e : g_bgraphs)
-      if (e.first == key) exec = e.second;
+    g_btuned.emplace_back(key, path);
+    if (g_btuned.size() > 64) g_btuned.erase(g_btuned.begin());
+  } else if (path == NSRGS_BATCH_PERSISTENT) {
+    nsrgs_status s2 = launch_persist();
+    if (s2 != NSRGS_OK) return s2;
+  } else {
+    nsrgs_status s2 = prepare_ticks(&exec);
+    if (s2 != NSRGS_OK) return s2;
+    NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
   }
-  if (!exec) {
-    if (!g_bcap[dev]) NSRGS_CUDA_TRY(cudaStreamCreateWithFlags(&g_bcap[dev], cudaStreamNonBlocking));
-    cudaStream_t cs = g_bcap[dev];
-    NSRGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = batch_reset(d_descs, count, d_nspec, cs);
-    if (e == cudaSuccess) e = batch_admit(d_descs, count, d, d_nspec, cs);
-    const int ticks = (init ? spectral_max_iters + 1 : 0) + T;  // + the orthonormalising pass
-    for (int t = 0; t < ticks && e == cudaSuccess; ++t) {
-      e = sparse ? batch_bcsr_stream(d_descs, d_rbase, count, d, storage == NSRGS_BCSR_BF16, rows, cs)
-                 : batch_stream(d_descs, d_base, count, d, storage, cs, false);
-      if (e == cudaSuccess) e = batch_spec(d_descs, d_bbase, count, d, blocks, d_nspec, cs);
-      if (e == cudaSuccess) e = batch_block(d_descs, d_bbase, count, d, blocks, cs);
-    }
-    if (e == cudaSuccess) e = batch_report(d_descs, count, d_rep, cs);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      set_error(std::string("batch graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
-      return NSRGS_ERR_CUDA;
-    }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-      return NSRGS_ERR_CUDA;
-    }
-    std::lock_guard<std::mutex> lk(g_bmu);
-    g_bgraphs.emplace_back(key, exec);
-    if (g_bgraphs.size() > 8) {
-      cudaGraphExecDestroy(g_bgraphs.front().second);
-      g_bgraphs.erase(g_bgraphs.begin());
-    }
-  }
-  NSRGS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  g_batch_last_path = path;
   if (info) {
     std::vector<BatchReport> rep(count);
     NSRGS_CUDA_TRY(cudaMemcpyAsync(rep.data(), d_rep, sizeof(BatchReport) * count, cudaMemcpyDeviceToHost, st));
     NSRGS_CUDA_TRY(cudaStreamSynchronize(st));
     bool timeout = false, nonfinite = false, bad = false;
     for (int i = 0; i < count; ++i) {
+      // an instance the persistent form did not finish (its CTA stopped on a flag)
+      if (rep[i].phase != PHASE_DONE && path == NSRGS_BATCH_PERSISTENT) timeout = true;
       info[i].spectral_iters = rep[i].spec_iters;
       info[i].iters = rep[i].iters;
       info[i].last_update_norm = rep[i].last_upd;
@@ -831,3 +902,12 @@ extern "C" nsrgs_status nsrgs_batch_solve(const nsrgs_batch_item* items, int cou
   }
   return NSRGS_OK;
 }
+
+extern "C" nsrgs_status nsrgs_batch_set_path(int path) {
+  NSRGS_CHECK_ARG(path == NSRGS_BATCH_AUTO || path == NSRGS_BATCH_TICKS || path == NSRGS_BATCH_PERSISTENT,
+                  "path must be NSRGS_BATCH_AUTO, NSRGS_BATCH_TICKS or NSRGS_BATCH_PERSISTENT");
+  g_batch_path_req = path;
+  return NSRGS_OK;
+}
+
+extern "C" int nsrgs_batch_last_path(void) { return g_batch_last_path; }

@@ -42,6 +42,7 @@ struct BatchDesc {
   int start_given;        // 1: X^0 comes from Xout, no spectral initialisation
   int safeguard;          // 1: safeguarded Newton-Schulz start (beyond the paper)
   int sparse;             // 1: block-sparse rows (streamed by the row kernel, no panel steps)
+  int resident;           // persistent form: the panels fit a CTA's stage space (kept in shared memory)
   double tol;             // stop when the update norm falls below it (0: run T iterations)
   double spec_tol;        // spectral residual target
 };
@@ -71,5 +72,9 @@ cudaError_t batch_block(const BatchDesc* descs, const long long* bbase, int coun
                         cudaStream_t st);
 cudaError_t batch_report(const BatchDesc* descs, int count, BatchReport* out, cudaStream_t st);
 cudaError_t batch_reset(const BatchDesc* descs, int count, int* nspec, cudaStream_t st);
+// Persistent form (batch_persist.cu): one launch, a CTA per instance at a time.
+bool persist_fits_resident(const PanelGeom& g);
+cudaError_t batch_persist(const BatchDesc* descs, const int* order, int count, int* next, int d, int storage,
+                          cudaStream_t st, bool prepare);
 
 }  // namespace nsrgs

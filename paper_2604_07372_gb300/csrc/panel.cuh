@@ -259,41 +259,72 @@ __device__ __forceinline__ void for_segments(const Src& src, long long g0, long 
   }
 }
 
-template <int D, int ST, class Src>
-__device__ __forceinline__ void panel_stream_body(const Src& src, long long total_steps) {
+// Pipeline position of one thread across calls of panel_stream_range: stage and
+// ring indices with their mbarrier phases and the running step count, so a
+// persistent kernel can stream the same CTA through many passes without
+// re-initialising its barriers.
+struct PanelPipe {
+  int st = 0;        // stage ring index (producer, consumers)
+  uint32_t ph = 0;   // its phase
+  int slot = 0;      // column-partial ring index (consumers, reducer)
+  uint32_t cph = 0;  // its phase
+  long long it = 0;  // steps issued (producer) / consumed (consumers) so far
+};
+
+// Residency modes of panel_stream_range.  RES_RING streams every step through
+// the ring of stages.  A CTA that owns a whole small instance can keep it in
+// shared memory: RES_LOAD copies every step's stored warp slices and X rows to
+// its own place in a dense area (step s at the sum of the earlier steps'
+// W*WB + STAGE_X bytes, no stage reused), RES_KEEP copies only the X rows
+// there and reads the warp slices left by the RES_LOAD pass.
+enum : int { RES_RING = 0, RES_LOAD = 1, RES_KEEP = 2 };
+
+// Initialises the stage and ring barriers (thread 0; the caller synchronises).
+template <int D, int ST>
+__device__ __forceinline__ void panel_init_barriers() {
   using C = PCfg<D, ST>;
   extern __shared__ __align__(128) uint8_t smem[];
-  const long long g0 = total_steps * blockIdx.x / gridDim.x;
-  const long long g1 = total_steps * (blockIdx.x + 1) / gridDim.x;
-  if (g0 >= g1) return;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BARS);
+  uint64_t* empty = full + C::NSTAGE;
+  uint64_t* cfull = empty + C::NSTAGE;
+  uint64_t* cempty = cfull + C::RING;
+  for (int s = 0; s < C::NSTAGE; ++s) {
+    mbar_init(&full[s], 1);
+    mbar_init(&empty[s], C::NW);
+  }
+  for (int s = 0; s < C::RING; ++s) {
+    mbar_init(&cfull[s], C::NW);
+    mbar_init(&cempty[s], 1);
+  }
+  fence_mbar_init();
+}
 
+// Streams the global step range [g0, g1) of `src` through this CTA.  Every
+// thread of the CTA calls it; warps leave it at different times (the caller
+// synchronises afterwards when it needs the result).  Barriers must have been
+// initialised; `pp` carries the thread's pipeline position between calls.
+template <int D, int ST, class Src>
+__device__ __forceinline__ void panel_stream_range(const Src& src, long long g0, long long g1, PanelPipe& pp,
+                                                   int res_mode) {
+  using C = PCfg<D, ST>;
+  extern __shared__ __align__(128) uint8_t smem[];
   float* ring = reinterpret_cast<float*>(smem + C::OFF_RING);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BARS);
   uint64_t* empty = full + C::NSTAGE;
   uint64_t* cfull = empty + C::NSTAGE;
   uint64_t* cempty = cfull + C::RING;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < C::NSTAGE; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], C::NW);
-    }
-    for (int s = 0; s < C::RING; ++s) {
-      mbar_init(&cfull[s], C::NW);
-      mbar_init(&cempty[s], 1);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-
+  const bool resident = res_mode != RES_RING;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
   if (warp == C::NW) {
     // ------------------------------------------------------------- producer
-    if (lane != 0) return;
-    int st = 0;
-    uint32_t ph = 0;
-    int issued = 0;
+    if (lane == 0) {
+    int& st = pp.st;
+    uint32_t& ph = pp.ph;
+    long long& issued = pp.it;
+    const long long issued0 = issued;
+    uint32_t roff = 0;  // resident modes: dense offset of the current step
     bool ok = true;
     for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
       if (v.skip) return true;
@@ -320,10 +351,29 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           ok = false;
           return false;
         }
-        uint8_t* stage = smem + st * C::STAGE_BYTES;
-        mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
-        bulk_g2s(stage, srcA, bytesA, &full[st]);
-        bulk_g2s(stage + C::STAGE_A, srcX, C::STAGE_X, &full[st]);
+        if (resident) {
+          // each step keeps its own place: A slices, then the step's X rows; the
+          // dense area is the stage ring's space
+          if (roff + bytesA + C::STAGE_X > (uint32_t)C::OFF_RING) {
+            atomicOr(&v.ctl->flags, FLAG_BAD_LAYOUT);
+            ok = false;
+            return false;
+          }
+          uint8_t* dst = smem + roff;
+          if (res_mode == RES_LOAD) {
+            mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
+            bulk_g2s(dst, srcA, bytesA, &full[st]);
+          } else {
+            mbar_arrive_expect_tx(&full[st], C::STAGE_X);
+          }
+          bulk_g2s(dst + bytesA, srcX, C::STAGE_X, &full[st]);
+          roff += bytesA + C::STAGE_X;
+        } else {
+          uint8_t* stage = smem + st * C::STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
+          bulk_g2s(stage, srcA, bytesA, &full[st]);
+          bulk_g2s(stage + C::STAGE_A, srcX, C::STAGE_X, &full[st]);
+        }
         off += bytesA;
         if (wk.advance() && wk.b < wk.nslabs) off = byte_off[wk.b];
         ++issued;
@@ -336,16 +386,18 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     });
     (void)ok;
     // Do not leave while copies into this CTA's shared memory may be in flight.
-    const int first = issued > C::NSTAGE ? issued - C::NSTAGE : 0;
-    for (int k = first; k < issued; ++k)
+    const long long first = issued - C::NSTAGE > issued0 ? issued - C::NSTAGE : issued0;
+    for (long long k = first; k < issued; ++k)
       if (!mbar_wait_bounded(&full[k % C::NSTAGE], (uint32_t)((k / C::NSTAGE) & 1), kWaitLimitNs)) break;
+    }
+    __syncwarp();
     return;
   }
 
   if (warp == C::NW + 1) {
     // -------------------------------------------------------------- reducer
-    int slot = 0;
-    uint32_t ph = 0;
+    int& slot = pp.slot;
+    uint32_t& ph = pp.cph;
     for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
       if (v.skip) return true;
       // the column offsets of a step keep 16-byte alignment; Y's base must too
@@ -388,9 +440,12 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
   using Vec = typename Unp::V;
   const int rg = lane >> 2;
   const int cg = lane & 3;
-  int st = 0, slot = 0;
-  uint32_t ph = 0, cph = 0;
-  int it = 0;  // steps consumed by this CTA so far (all segments)
+  int& st = pp.st;
+  int& slot = pp.slot;
+  uint32_t& ph = pp.ph;
+  uint32_t& cph = pp.cph;
+  long long& it = pp.it;  // steps consumed by this CTA so far (all segments and calls)
+  uint32_t roff = 0;      // resident modes: dense offset of the current step
 
   for_segments(src, g0, g1, [&](const InstView& v, long long lo, long long hi) {
     if (v.skip) return true;
@@ -444,7 +499,9 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
         atomicOr(&v.ctl->flags, FLAG_TIMEOUT);
         return false;
       }
-      const uint8_t* stage = smem + st * C::STAGE_BYTES;
+      const uint8_t* stage = resident ? smem + roff : smem + st * C::STAGE_BYTES;
+      const uint32_t xoff = resident ? (uint32_t)wk.W * C::WB : (uint32_t)C::STAGE_A;
+      if (resident) roff += (uint32_t)wk.W * C::WB + C::STAGE_X;
       float cacc[C::NV];
 #pragma unroll
       for (int k = 0; k < C::NV; ++k) cacc[k] = 0.f;
@@ -456,14 +513,14 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
           raw[rt] = *reinterpret_cast<const Vec*>(stage + warp * C::WB + (rt * 32 + lane) * C::LOADB);
         float xc[C::NV];
         if constexpr (C::NV % 4 == 0) {
-          const float4* xs = reinterpret_cast<const float4*>(stage + C::STAGE_A) + cg * (C::NV / 4);
+          const float4* xs = reinterpret_cast<const float4*>(stage + xoff) + cg * (C::NV / 4);
 #pragma unroll
           for (int k = 0; k < C::NV / 4; ++k) {
             const float4 t = xs[k];
             xc[4 * k + 0] = t.x; xc[4 * k + 1] = t.y; xc[4 * k + 2] = t.z; xc[4 * k + 3] = t.w;
           }
         } else {
-          const float2* xs = reinterpret_cast<const float2*>(stage + C::STAGE_A) + cg * (C::NV / 2);
+          const float2* xs = reinterpret_cast<const float2*>(stage + xoff) + cg * (C::NV / 2);
 #pragma unroll
           for (int k = 0; k < C::NV / 2; ++k) {
             const float2 t = xs[k];
@@ -544,6 +601,18 @@ __device__ __forceinline__ void panel_stream_body(const Src& src, long long tota
     if (wk.q != 0) flush_rows(wk.b);
     return true;
   });
+}
+
+// One launch over all steps of `src`, split evenly over the CTAs.
+template <int D, int ST, class Src>
+__device__ __forceinline__ void panel_stream_body(const Src& src, long long total_steps) {
+  const long long g0 = total_steps * blockIdx.x / gridDim.x;
+  const long long g1 = total_steps * (blockIdx.x + 1) / gridDim.x;
+  if (g0 >= g1) return;
+  if (threadIdx.x == 0) panel_init_barriers<D, ST>();
+  __syncthreads();
+  PanelPipe pp;
+  panel_stream_range<D, ST>(src, g0, g1, pp, RES_RING);
 }
 
 }  // namespace nsrgs
