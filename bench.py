@@ -241,6 +241,19 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
         e1.record()
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3 / reps
+        auto_path = P.nsrgs_batch_last_path()
+        # both execution paths of the batched form, each forced and timed the same way
+        path_ms = {}
+        for pname, pcode in (("ticks", P.BATCH_TICKS), ("persistent", P.BATCH_PERSISTENT)):
+            P.nsrgs_batch_set_path(pcode)
+            P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=False)
+            e0.record()
+            for _ in range(reps):
+                P.nsrgs_batch_solve(packs[st], etas, T, K, spectral_max_iters=SMAX, Xs=Xs, ws=ws, info=False)
+            e1.record()
+            torch.cuda.synchronize()
+            path_ms[pname] = e0.elapsed_time(e1) / reps
+        P.nsrgs_batch_set_path(P.BATCH_AUTO)
         bytes_A = sum(p.nbytes for p in packs[st])
         # bytes of A streamed by one batch solve: each instance's packed A once per
         # spectral pass and per iteration (the orthonormalising passes read no A)
@@ -249,7 +262,9 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
         out[name] = {"solves_per_s": count / sec, "batch_ms": 1e3 * sec, "packed_GB": bytes_A / 1e9,
                      "instances_with_T_iterations": iters_ok, "A_GB_streamed_per_batch": streamed / 1e9,
                      "A_GBps": streamed / sec / 1e9,
-                     "hbm_frac": streamed / sec / 1e9 / measured_peaks()[0]["hbm_gbs"]}
+                     "hbm_frac": streamed / sec / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                     "path": {1: "ticks", 2: "persistent"}.get(auto_path, str(auto_path)),
+                     "batch_ms_by_path": path_ms}
         del ws
     for name in ("bf16", "fp8"):
         rel = np.abs(dF[name] - dF["f32"]) / dF["f32"]
