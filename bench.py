@@ -56,9 +56,10 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/FP8/dense/e2e/CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="storage of the main leg")
-    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving", "sparse", "se"],
+    ap.add_argument("--leg", default="all", choices=["all", "sweep", "batched", "serving", "sparse", "se", "batch_paths"],
                     help="run only one extra leg (prints its JSON, no metric line), for profiling")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-n", type=int, default=500, help="n of every instance in --leg batch_paths")
     ap.add_argument("--sweep-dims", default="3,8,16,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
@@ -293,6 +294,35 @@ def batched_leg(P, synth, seed: int, count: int = 512, T: int = 60, K: int = 2, 
         "solves_per_s": 1.0 / seq,
         "sample": f"first {len(sub)} instances, one nsrgs_solve each, device time with its graph already captured",
     }
+    return out
+
+
+def batch_paths_leg(P, synth, seed: int, count: int = 152, n: int = 500, T: int = 4):
+    """count equal instances (d = 3, FP32 panels) from a given start (identity
+    blocks), T iterations, once through each execution path of the batched form:
+    the small case the profile of the two paths is taken on."""
+    import torch
+
+    d = 3
+    packs = []
+    for k in range(count):
+        _, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + k)
+        packs.append(P.nsrgs_pack_upper(up, n, d, P.F32))
+        del up
+    X0 = torch.eye(d, device="cuda").repeat(n, 1).contiguous()
+    ws = torch.empty(P.nsrgs_batch_workspace_bytes([n] * count, d), dtype=torch.uint8, device="cuda")
+    out = {"instances": count, "n": n, "T": T}
+    for name, code in (("ticks", P.BATCH_TICKS), ("persistent", P.BATCH_PERSISTENT)):
+        P.nsrgs_batch_set_path(code)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Xs = [X0.clone() for _ in range(count)]
+        torch.cuda.synchronize()
+        e0.record()
+        P.nsrgs_batch_solve(packs, [1.0 / n] * count, T, 2, init=False, Xs=Xs, ws=ws, info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1)
+    P.nsrgs_batch_set_path(P.BATCH_AUTO)
     return out
 
 
@@ -948,6 +978,8 @@ def main():
             out = dsweep_leg(P, synth, seed=args.seed + 3, n=args.sweep_n, dims=dims, reps=args.sweep_reps, only=only)
         elif args.leg == "batched":
             out = batched_leg(P, synth, seed=args.seed + 1, count=args.batch_count, seq_subset=8)
+        elif args.leg == "batch_paths":
+            out = batch_paths_leg(P, synth, seed=args.seed + 6, count=args.batch_count, n=args.batch_n, T=args.T)
         elif args.leg == "se":
             out = se_leg(P, synth, seed=args.seed + 5, n=args.se_n)
         elif args.leg == "sparse":
