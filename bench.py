@@ -337,7 +337,8 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     out = {}
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
-        storages = ["dense_f32"] + (["f32", "bf16"] if d <= 8 else []) + (["dense_bf16", "bf16"] if d in (16, 32, 64) else [])
+        # f32: panels for d <= 8, the float32 tile-upper stream above (CUDA cores, half the dense bytes)
+        storages = ["dense_f32", "f32"] + (["bf16"] if d <= 8 else []) + (["dense_bf16", "bf16"] if d in (16, 32, 64) else [])
         if only:
             storages = [x for x in storages if x in only]
         res = {}

@@ -56,7 +56,10 @@ typedef enum {
 } nsrgs_status;
 
 /* Storage precision of the packed A.  Arithmetic is float32 in every case.
- *  F32     : A stored as float32.
+ *  F32     : A stored as float32.  For d <= 8 the panel layout on the CUDA cores;
+ *            for 8 < d <= 64 the float32 tile-upper layout (64 x 64 tiles of the
+ *            upper triangle, each feeding Y_I += A_IJ X_J and Y_J += A_IJ^T X_I on
+ *            the CUDA cores): half the bytes of DENSE_F32.
  *  BF16    : A rounded to bfloat16 (round to nearest even).  For d <= 8 the panel
  *            layout on the CUDA cores; for d in {16, 32, 64} the tile-upper layout
  *            on the tensor cores (128 x 128 tiles of the upper triangle, each feeding
@@ -124,7 +127,7 @@ typedef struct nsrgs_info {
 /* ---------------------------------------------------------------- sizes */
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
- * supported (F32: d <= 8; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4;
+ * supported (F32: any d <= 64; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4;
  * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}; BCSR_*: d <= 8, the
  * bound for fully observed data -- see nsrgs_bcsr_packed_bytes for the exact size). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
@@ -195,7 +198,7 @@ nsrgs_status nsrgs_step(const nsrgs_A* A, float eta, int K, const float* X_in, f
  *    library; every GPU on which this is called keeps that memory until the
  *    process exits.  (n, d) whose nsrgs_workspace_bytes exceeds 8 MiB is
  *    rejected with NSRGS_ERR_INVALID_ARG: n <= 46016 at d = 3,
- *    n <= 25656 at d = 4, n <= 6025 at d = 8, n <= 1016 at d = 16; d >= 32
+ *    n <= 25656 at d = 4, n <= 6025 at d = 8, n <= 931 at d = 16; d >= 32
  *    never fits.
  *  - The first call on a device resolves the array's device address
  *    (cudaGetSymbolAddress) with that device current and caches it; make that

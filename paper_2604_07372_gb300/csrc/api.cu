@@ -71,6 +71,12 @@ long long tc_sym_xt_bytes(int n, int d);
 cudaError_t tc_sym_prepare(int d);
 cudaError_t tc_sym_product(const void* packed, int n, int d, const float* X, uint8_t* xt, float* Y, Ctl* ctl,
                            const int* skip, cudaStream_t st);
+bool fs_sym_supported(int d);
+long long fs_sym_bytes(int n, int d);
+long long fs_sym_xt_bytes(int n, int d);
+cudaError_t fs_sym_prepare(int d);
+cudaError_t fs_sym_product(const void* packed, int n, int d, const float* X, float* xt, float* Y, Ctl* ctl,
+                           const int* skip, cudaStream_t st);
 size_t obj_partials_doubles(int n, int D);
 cudaError_t launch_objective(const float* Xc, const float* Yc, const float* Xp, float* Yp, int n, int D,
                              double rel_tol, const ObjScratch& o, Ctl* ctl, cudaStream_t st);
@@ -122,10 +128,16 @@ static Workspace map_workspace(void* base, int n, int d) {
   w.obj.total = reinterpret_cast<double*>(take(dd + 3 * sizeof(double)));
   w.obj.partials = reinterpret_cast<double*>(take(obj_partials_doubles(n, d) * sizeof(double)));
   w.obj.Yprev = reinterpret_cast<float*>(take(vec));
-  if (d >= 16) {
-    // X^T in bfloat16: row-major for the dense stream, swizzled tiles for the tile-upper stream
-    const long long a = (long long)d * dense_bf16_pitch(n, d) * 2, b = tc_sym_xt_bytes(n, d);
-    w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)(a > b ? a : b)));
+  if (d > 8) {
+    // X^T: bfloat16 row-major for the dense tensor-core stream, swizzled bfloat16 tiles
+    // for the tile-upper tensor-core stream, float32 64-row tiles for the float32 tile stream
+    long long a = fs_sym_xt_bytes(n, d);
+    if (d >= 16) {
+      const long long b = (long long)d * dense_bf16_pitch(n, d) * 2, c = tc_sym_xt_bytes(n, d);
+      a = a > b ? a : b;
+      a = a > c ? a : c;
+    }
+    w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)a));
   }
   w.bytes = off;
   return w;
@@ -174,8 +186,12 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     NSRGS_CUDA_TRY(tc_sym_prepare(A->d));
     return NSRGS_OK;
   }
+  if (A->storage == NSRGS_F32 && fs_sym_supported(A->d)) {
+    NSRGS_CUDA_TRY(fs_sym_prepare(A->d));
+    return NSRGS_OK;
+  }
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
-    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4) or BF16 with d in {16, 32, 64}; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   NSRGS_CUDA_TRY(stream_panel_prepare(*g));
@@ -200,6 +216,8 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
   if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d))
     return tc_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl, skip, st);
+  if (A->storage == NSRGS_F32 && fs_sym_supported(A->d))
+    return fs_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<float*>(w.XT), w.Y, w.ctl, skip, st);
   if (bcsr_storage(A->storage)) return bcsr_stream(A->packed, A->n, A->d, A->storage, X, w.Y, skip, w.ctl, st);
   return stream_panel(A->packed, g, X, w.Y, w.ctl, skip, st);
 }
@@ -374,6 +392,7 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (storage == NSRGS_DENSE_BF16)
     return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
   if (storage == NSRGS_BF16 && tc_sym_supported(d)) return (size_t)tc_sym_bytes(n, d);
+  if (storage == NSRGS_F32 && fs_sym_supported(d)) return (size_t)fs_sym_bytes(n, d);
   if (bcsr_storage(storage)) return d <= 8 ? (size_t)bcsr_bytes(n, d, storage, (long long)n * (n - 1)) : 0;
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) return 0;

@@ -271,6 +271,8 @@ long long dense_pitch(int n, int d);
 long long dense_bf16_pitch(int n, int d);
 bool tc_sym_supported(int d);
 long long tc_sym_bytes(int n, int d);
+bool fs_sym_supported(int d);
+long long fs_sym_bytes(int n, int d);
 
 cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const PanelGeom& g, const ObjScratch& o,
                          Ctl* ctl, cudaStream_t st) {
@@ -289,6 +291,10 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
     // tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), tc_sym_bytes(n, d) / 2, 2.0,
                                             o, ctl);
+  } else if (storage == NSRGS_F32 && fs_sym_supported(d)) {
+    // float32 tile-upper layout: the upper triangle once, everything else zero
+    norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(packed), fs_sym_bytes(n, d) / 4, 2.0, o,
+                                            ctl);
   } else if (storage == NSRGS_F32) {
     const uint8_t* p = reinterpret_cast<const uint8_t*>(packed) + g.header_bytes;
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(p), g.panel_bytes / 4, 2.0, o, ctl);

@@ -166,6 +166,9 @@ long long dense_bf16_pitch(int n, int d);
 bool tc_sym_supported(int d);
 template <class Src>
 cudaError_t tc_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st);
+bool fs_sym_supported(int d);
+template <class Src>
+cudaError_t fs_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st);
 
 template <class Src>
 static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, cudaStream_t st) {
@@ -186,10 +189,14 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
       NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, packed, st));
       return NSRGS_OK;
     }
+    if (storage == NSRGS_F32 && fs_sym_supported(d)) {
+      NSRGS_CUDA_TRY(fs_sym_pack(src, n, d, packed, st));
+      return NSRGS_OK;
+    }
   }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
-    set_error("symmetric storage needs 1 <= d <= 8 (FP8: d <= 4) or BF16 with d in {16, 32, 64}; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   std::vector<long long> tab;

@@ -12,7 +12,7 @@
 // kStaticWorkspaceBytes (8 MiB) of device memory for this array until the
 // process exits.  A problem whose workspace (nsrgs_workspace_bytes(n, d))
 // exceeds that size is rejected with NSRGS_ERR_INVALID_ARG: the largest n is
-// 418368 at d = 1, 46016 at d = 3, 25656 at d = 4, 6025 at d = 8 and 1016 at
+// 418368 at d = 1, 46016 at d = 3, 25656 at d = 4, 6025 at d = 8 and 931 at
 // d = 16; d >= 32 never fits (the float64 per-CTA partials alone exceed it).
 // The array's device address is resolved once per device and cached, so the
 // entry point must not be used across a cudaDeviceReset of that device (the

@@ -39,10 +39,12 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_version_and_sizes(L):
     assert "sm_103a" in L.nsrgs_version()
-    # symmetric layouts cover d <= 8 (FP8 d <= 4); the dense layout any d <= 64
+    # symmetric layouts: F32 any d <= 64 (panels up to 8, float32 tiles above), BF16 d <= 8
+    # and d in {16, 32, 64}, FP8 d <= 4; the dense layout any d <= 64
     assert L.nsrgs_packed_bytes(200, 3, L.F32) > 0
     assert L.nsrgs_packed_bytes(200, 8, L.F32) > 0 and L.nsrgs_packed_bytes(200, 5, L.BF16) > 0
-    assert L.nsrgs_packed_bytes(200, 9, L.F32) == 0
+    assert L.nsrgs_packed_bytes(200, 9, L.F32) > 0 and L.nsrgs_packed_bytes(200, 64, L.F32) > 0
+    assert L.nsrgs_packed_bytes(200, 65, L.F32) == 0 and L.nsrgs_packed_bytes(200, 9, L.BF16) == 0
     assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0
     # block-sparse rows: the bound for fully observed data, both triangles, d <= 8
     assert L.nsrgs_packed_bytes(200, 3, L.BCSR_F32) >= 200 * 199 * 9 * 4
@@ -111,7 +113,7 @@ def test_static_step_limits_match_the_documented_figures(L):
         return lo
 
     header = open(os.path.join(ROOT, "include", "nsrgs.h")).read()
-    for d, n in ((3, 46016), (4, 25656), (8, 6025), (16, 1016)):
+    for d, n in ((3, 46016), (4, 25656), (8, 6025), (16, 931)):
         assert largest_n(d) == n, (d, largest_n(d))
         assert f"n <= {n} at d = {d}" in header
     assert largest_n(32) is None and largest_n(64) is None

@@ -56,8 +56,6 @@ def random_orthogonal_blocks(n, d, seed):
 @pytest.mark.parametrize("storage", ["f32", "dense_f32"])
 @pytest.mark.parametrize("n,d", [(2, 3), (200, 3), (131, 4), (90, 8), (40, 25)])
 def test_objective_matches_oracle(P, n, d, storage):
-    if storage == "f32" and d > 8:
-        pytest.skip("symmetric storage covers d <= 8")
     inst = make(n, d, seed=n + d)
     A = inst.dense()
     pa = packed(P, inst, P.STORAGE[storage])

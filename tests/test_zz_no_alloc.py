@@ -39,10 +39,10 @@ def _static_step(P, pa, eta, K, Xin, Xout, upd=None):
 
 
 # (300, 3) FP32 and (1000, 2) BF16 run the panel stream with the per-block
-# epilogue in registers; (1000, 16) BF16 runs the tile-upper tensor-core stream
+# epilogue in registers; (900, 16) BF16 runs the tile-upper tensor-core stream
 # and the shared-memory epilogue, whose scratch (X^T tiles, float64 partials)
 # also lives in the array.
-@pytest.mark.parametrize("n,d,storage", [(300, 3, 0), (1000, 2, 1), (1000, 16, 1)])
+@pytest.mark.parametrize("n,d,storage", [(300, 3, 0), (1000, 2, 1), (900, 16, 1)])
 def test_static_step_matches_workspace_step_twice(P, n, d, storage):
     inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=n + d, dtype=np.float32)
     pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, storage)
