@@ -300,13 +300,13 @@ __global__ void __launch_bounds__(FsCfg<C>::THREADS, 1) fs_sym_kernel(const __gr
           fail();
           break;
         }
+        // scratch order [range][X column][tile column]: a thread's 4 columns are one
+        // float4, and the 8 threads of a quarter-warp write 8 consecutive float4s
         if (busy) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 8; c += 4)
-              *reinterpret_cast<float4*>(red + ((s * kFsT + 4 * g + j) * F::DP + 8 * cc + c)) =
-                  make_float4(acc[j][c], acc[j][c + 1], acc[j][c + 2], acc[j][c + 3]);
+          for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<float4*>(red + ((s * F::DP + 8 * cc + c) * kFsT + 4 * g)) =
+                make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(rb_full);
@@ -314,17 +314,19 @@ __global__ void __launch_bounds__(FsCfg<C>::THREADS, 1) fs_sym_kernel(const __gr
           fail();
           break;
         }
-        // 64 columns x DP values, 4 per thread and pass: sum over the ranges, add to Y
-        for (int e = u * 4; e < kFsT * F::DP; e += 128 * 4) {
-          const int col = e / F::DP, xc = e % F::DP;
+        // 64 columns x DP values, 4 consecutive X columns per thread and pass (one
+        // float4 of Y): sum over the ranges, add to Y; consecutive threads take
+        // consecutive tile columns, so the scratch reads are conflict-free
+        for (int e = u; e < kFsT * (F::DP / 4); e += 128) {
+          const int col = e % kFsT, xc = (e / kFsT) * 4;
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int r2 = 0; r2 < S; ++r2) {
-            const float4 w = *reinterpret_cast<const float4*>(red + (r2 * kFsT + col) * F::DP + xc);
-            v.x += w.x;
-            v.y += w.y;
-            v.z += w.z;
-            v.w += w.w;
+            const float* w = red + (r2 * F::DP + xc) * kFsT + col;
+            v.x += w[0];
+            v.y += w[kFsT];
+            v.z += w[2 * kFsT];
+            v.w += w[3 * kFsT];
           }
           const int row = J * kFsT + col;
           if (row < a.rows && xc < a.d) {
