@@ -74,7 +74,11 @@ struct FsCfg {
   static constexpr int XB = DP * kFsT * 4;          // one X^T tile
   static constexpr int STAGE = kFsTileBytes + XB;   // A tile + X_J^T tile
   static constexpr int RED = S > 1 ? S * kFsT * DP * 4 : 0;  // column-product range partials
-  static constexpr int BUDGET = 200 * 1024;
+  // CTAs per SM: two (18 warps, 96 registers a thread) hide more latency for DP <= 32
+  // (n = 2000: d = 16 1.29 -> 1.08 ms, d = 32 8.11 -> 7.40 ms); at DP = 64 the
+  // 32-accumulator loop wants the registers of one CTA (48.7 vs 52.3 ms)
+  static constexpr int MINB = C <= 4 ? 2 : 1;
+  static constexpr int BUDGET = MINB == 2 ? 104 * 1024 : 200 * 1024;
   static constexpr int NSTAGE_RAW = (BUDGET - XB - RED) / STAGE;
   static constexpr int NSTAGE = NSTAGE_RAW > 8 ? 8 : NSTAGE_RAW;
   static constexpr int OFF_XI = NSTAGE * STAGE;
@@ -85,7 +89,7 @@ struct FsCfg {
   static constexpr int THREADS = 9 * 32;
   static_assert(TASKS <= 128, "tasks");
   static_assert(NSTAGE >= 2, "stages");
-  static_assert(SMEM <= 227 * 1024, "shared memory");
+  static_assert(SMEM * MINB <= 227 * 1024, "shared memory");
 };
 
 struct FsArgs {
@@ -100,7 +104,7 @@ struct FsArgs {
 };
 
 template <int C>
-__global__ void __launch_bounds__(FsCfg<C>::THREADS, 1) fs_sym_kernel(const __grid_constant__ FsArgs a) {
+__global__ void __launch_bounds__(FsCfg<C>::THREADS, FsCfg<C>::MINB) fs_sym_kernel(const __grid_constant__ FsArgs a) {
   using F = FsCfg<C>;
   constexpr int S = F::S, R = F::RANGE;
   if (*a.skip) return;  // uniform: written only by earlier launches
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(FsCfg<C>::THREADS, 1) fs_sym_kernel(const __gr
     if (rowp) {
       const float* XJ = reinterpret_cast<const float*>(A + kFsTileBytes) + (8 * cc) * kFsT;
       if (busy) {
-#pragma unroll 4
+#pragma unroll(F::MINB == 2 ? 2 : 4)
         for (int k = s * R; k < (s + 1) * R; k += 4) {
           float4 av[4];
 #pragma unroll
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(FsCfg<C>::THREADS, 1) fs_sym_kernel(const __gr
     } else {
       const float* XI = reinterpret_cast<const float*>(smem + F::OFF_XI) + (8 * cc) * kFsT;
       if (busy) {
-#pragma unroll 4
+#pragma unroll(F::MINB == 2 ? 2 : 4)
         for (int r = s * R; r < (s + 1) * R; r += 4) {
           float4 av[4];
 #pragma unroll
@@ -408,7 +412,7 @@ static cudaError_t launch_fs(const FsArgs& a, cudaStream_t st, bool prepare) {
   using F = FsCfg<C>;
   if (prepare) return cudaFuncSetAttribute(fs_sym_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
   const long long total = fs_tiles(a.NT);
-  const int grid = (int)std::min<long long>(total, num_sms());
+  const int grid = (int)std::min<long long>(total, (long long)F::MINB * num_sms());
   fs_sym_kernel<C><<<grid, F::THREADS, F::SMEM, st>>>(a);
   return cudaGetLastError();
 }
