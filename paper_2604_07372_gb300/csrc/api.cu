@@ -36,6 +36,8 @@ cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X,
 cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float* Y, const int* skip,
                          cudaStream_t st);
 cudaError_t stream_panel_prepare(const PanelGeom& g);
+cudaError_t iterate_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, float* Xout, float eta,
+                          int K, int safeguard, double tol, Ctl* ctl, const int* skip, cudaStream_t st);
 
 int reduce_grid(long long rows);
 cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
@@ -274,6 +276,14 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
 
 enum { METHOD_NSRGS = 0, METHOD_GPM = 1, METHOD_NSRGS_OBJECTIVE = 2 };
 
+// The panel layouts (symmetric storage at d <= 7) run Algorithm 2's iteration as
+// one fused launch (A stream, grid barrier, block updates); at d = 8 the fused
+// kernel would spill the block update's 8 x 8 registers, so the epilogue stays a
+// launch of its own there.
+static bool panel_storage(const nsrgs_A* A) {
+  return (A->storage == NSRGS_F32 || A->storage == NSRGS_BF16 || A->storage == NSRGS_FP8E4M3) && A->d <= 7;
+}
+
 static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, const Workspace& w, float eta, int T,
                                       int K, double tol, int method, int safeguard, cudaStream_t st,
                                       const cudaEvent_t* ev = nullptr) {
@@ -281,6 +291,13 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
   for (int t = 0; t < T; ++t) {
     const float* Xt = w.X[t & 1];
     float* Xn = w.X[(t + 1) & 1];
+    if (method == METHOD_NSRGS && panel_storage(A)) {
+      if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+      e = iterate_panel(A->packed, g, Xt, w.Y, Xn, eta, K, safeguard, tol, w.ctl, &w.ctl->stop, st);
+      if (e != cudaSuccess) return e;
+      if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+      continue;
+    }
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = stream_AX(A, g, Xt, w, &w.ctl->stop, st)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2 * t + 1], st, cudaEventRecordExternal)) != cudaSuccess) return e;

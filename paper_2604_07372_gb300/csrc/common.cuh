@@ -52,6 +52,8 @@ struct Ctl {
   int spec_restart;        // the next spectral pass restarts from V^0 with a larger shift
   int spec_round;          // restarts taken so far
   int spec_prev;           // batched / served instances: passes run before the last restart
+  unsigned int gbar_count; // fused iteration kernel: CTAs arrived at the grid barrier
+  unsigned int gbar_gen;   // fused iteration kernel: grid barrier generation
   int pad;
 };
 
