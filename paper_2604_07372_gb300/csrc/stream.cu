@@ -39,34 +39,42 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_stream_kernel(c
   panel_stream_body<D, ST>(src, a.g.total_steps);
 }
 
-// ------------------------------------------------------ fused iteration
-// One launch per iteration of Algorithm 2 on the panel layout: the A stream
-// Y = A_off X^t as above, a grid-wide barrier, then each CTA applies the block
-// update (gradient, tangent projection, step, K Newton-Schulz steps) to its
-// share of the n blocks, so the separate epilogue launch and its launch gap
-// disappear from the loop.  The grid is one CTA per SM (the stream's shared
-// memory admits one), all resident at once; the barrier's wait is bounded (a
-// timeout sets FLAG_TIMEOUT, and later launches then return at once).
-struct IterArgs {
-  StreamArgs s;     // packed A, X^t, Y (zero on entry, zero again on exit), ctl, skip
-  float* Xout;      // X^{t+1}
+// ------------------------------------------------------ fused iteration loop
+// All T iterations of Algorithm 2 on the panel layout in ONE launch: per
+// iteration the A stream Y = A_off X^t (the tuned pipeline, whose stage and ring
+// positions carry over from pass to pass), a grid-wide barrier, each CTA's share
+// of the block updates (gradient, tangent projection, step, K Newton-Schulz
+// steps; Y cleared), and a second barrier whose last arrival finishes the update
+// norm and the stop test before the next pass.  No kernel boundary, launch gap or
+// pipeline set-up remains between iterations.  The grid is one CTA per SM (the
+// stream's shared memory admits one), all resident at once; every barrier wait
+// is bounded (a timeout sets FLAG_TIMEOUT and the CTA leaves).
+struct LoopArgs {
+  StreamArgs s;     // packed A, Y (zero on entry and on exit), ctl, skip; s.X unused
+  float* X0;        // X^t for even t
+  float* X1;        // X^t for odd t
   float eta;
   int K;
   int safeguard;
-  double tol;       // > 0: the last CTA sets ctl->stop when the update norm falls below it
+  int T;
+  double tol;       // > 0: stop after the first iteration whose update norm is below it
 };
 
 // Grid-wide barrier on two counters of the control block.  Every thread calls
-// it; returns false (in every thread) after a timeout.
-__device__ __forceinline__ bool grid_barrier_bounded(Ctl* ctl) {
+// it; `last` runs in the last arriving CTA's thread 0 before the others are
+// released.  Returns false (in every thread of the CTA) after a timeout.
+template <class Last>
+__device__ __forceinline__ bool grid_barrier_bounded(Ctl* ctl, Last&& last) {
   __shared__ int s_ok;
-  __threadfence();  // this thread's Y reductions are visible before the arrival
+  __threadfence();  // this thread's global writes and reductions before the arrival
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* gen = &ctl->gbar_gen;
     const unsigned int g = *gen;
     int ok = 1;
     if (atomicAdd(&ctl->gbar_count, 1u) == gridDim.x - 1) {
+      __threadfence();
+      last();
       ctl->gbar_count = 0u;
       __threadfence();
       atomicAdd(&ctl->gbar_gen, 1u);
@@ -87,44 +95,56 @@ __device__ __forceinline__ bool grid_barrier_bounded(Ctl* ctl) {
   return s_ok != 0;
 }
 
+// Generic-proxy writes of X by this thread become visible to the TMA engine
+// (the async proxy) that reads X rows in the next pass.
+__device__ __forceinline__ void fence_x_for_tma() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 template <int D, int ST>
-__global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_iter_kernel(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_loop_kernel(const __grid_constant__ LoopArgs a) {
   Ctl* ctl = a.s.ctl;
   // uniform: both are written only by earlier launches
   if (*a.s.skip || (*reinterpret_cast<volatile unsigned int*>(&ctl->flags) & FLAG_TIMEOUT)) return;
   __shared__ double sh[32];
+  __shared__ int s_stop;
   const long long total = a.s.g.total_steps;
   const long long g0 = total * blockIdx.x / gridDim.x;
   const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
-  if (threadIdx.x == 0) panel_init_barriers<D, ST>();
-  __syncthreads();
-  if (g0 < g1) {
-    SingleSrc src{&a.s};
-    PanelPipe pp;
-    panel_stream_range<D, ST>(src, g0, g1, pp, RES_RING);
-  }
-  if (!grid_barrier_bounded(ctl)) return;
-  // this CTA's blocks of Algorithm 2's update
   const int n = a.s.g.n;
   const long long b0 = (long long)n * blockIdx.x / gridDim.x;
   const long long b1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
-  double diff2 = 0.0;
-  unsigned int flags = 0;
-  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
-    block_update<D>(a.s.X, a.s.Y, a.Xout, i, n, a.eta, a.K, a.safeguard != 0, diff2, flags);
-  if (flags) atomicOr(&ctl->flags, flags);
-  const double bs = block_sum(diff2, sh);
-  if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
-  if (last_block(&ctl->counter)) {
-    if (threadIdx.x == 0) {
-      const double tot = atomicAdd(&ctl->upd_acc, 0.0);
-      const double un = sqrt(tot / ((double)n * D));
+  if (threadIdx.x == 0) panel_init_barriers<D, ST>();
+  __syncthreads();
+  PanelPipe pp;
+  StreamArgs sa = a.s;
+  for (int t = 0; t < a.T; ++t) {
+    const float* Xt = (t & 1) ? a.X1 : a.X0;
+    float* Xn = (t & 1) ? a.X0 : a.X1;
+    if (g0 < g1) {
+      sa.X = Xt;
+      SingleSrc src{&sa};
+      panel_stream_range<D, ST>(src, g0, g1, pp, RES_RING);
+    }
+    if (!grid_barrier_bounded(ctl, [] {})) return;
+    // this CTA's blocks of Algorithm 2's update
+    double diff2 = 0.0;
+    unsigned int flags = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+      block_update<D>(Xt, a.s.Y, Xn, i, n, a.eta, a.K, a.safeguard != 0, diff2, flags);
+    if (flags) atomicOr(&ctl->flags, flags);
+    fence_x_for_tma();
+    const double bs = block_sum(diff2, sh);
+    if (threadIdx.x == 0) atomicAdd(&ctl->upd_acc, bs);
+    const bool ok = grid_barrier_bounded(ctl, [&] {
+      const double un = sqrt(atomicAdd(&ctl->upd_acc, 0.0) / ((double)n * D));
       ctl->last_upd = un;
       ctl->iters_done += 1;
-      if (a.tol > 0.0 && un < a.tol) ctl->stop = 1;
       ctl->upd_acc = 0.0;
-      ctl->counter = 0u;
-    }
+      if (a.tol > 0.0 && un < a.tol) ctl->stop = 1;
+    });
+    if (!ok) return;
+    if (threadIdx.x == 0) s_stop = *reinterpret_cast<volatile int*>(&ctl->stop);
+    __syncthreads();
+    if (s_stop) break;
   }
 }
 
@@ -187,7 +207,9 @@ static cudaError_t prepare_panel() {
   using C = PCfg<D, ST>;
   cudaError_t e = cudaFuncSetAttribute(panel_stream_kernel<D, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(panel_iter_kernel<D, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if constexpr (D <= 7)
+    return cudaFuncSetAttribute(panel_loop_kernel<D, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  return cudaSuccess;
 }
 
 template <int D, int ST>
@@ -227,38 +249,38 @@ cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X,
 }
 
 template <int D, int ST>
-static cudaError_t launch_iter(const IterArgs& a, cudaStream_t st) {
+static cudaError_t launch_loop(const LoopArgs& a, cudaStream_t st) {
   using C = PCfg<D, ST>;
-  panel_iter_kernel<D, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(a);
+  panel_loop_kernel<D, ST><<<num_sms(), C::THREADS, C::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int D>
-static cudaError_t launch_iter_st(const IterArgs& a, cudaStream_t st) {
+static cudaError_t launch_loop_st(const LoopArgs& a, cudaStream_t st) {
   switch (a.s.g.storage) {
-    case NSRGS_F32: return launch_iter<D, NSRGS_F32>(a, st);
-    case NSRGS_BF16: return launch_iter<D, NSRGS_BF16>(a, st);
+    case NSRGS_F32: return launch_loop<D, NSRGS_F32>(a, st);
+    case NSRGS_BF16: return launch_loop<D, NSRGS_BF16>(a, st);
     case NSRGS_FP8E4M3:
-      if constexpr (D <= 4) return launch_iter<D, NSRGS_FP8E4M3>(a, st);
+      if constexpr (D <= 4) return launch_loop<D, NSRGS_FP8E4M3>(a, st);
       break;
   }
   return cudaErrorInvalidValue;
 }
 
-// One fused iteration on the panel layout: X_out = NS_K(X - eta P(G)), Y = A_off X
-// formed and consumed inside the launch (zero again on exit).
-cudaError_t iterate_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, float* Xout, float eta,
-                          int K, int safeguard, double tol, Ctl* ctl, const int* skip, cudaStream_t st) {
-  IterArgs a{StreamArgs{reinterpret_cast<const uint8_t*>(packed), X, Y, ctl, skip, g}, Xout, eta, K, safeguard, tol};
+// T iterations on the panel layout in one launch, from X0 (X^t alternates between
+// X0 and X1; ctl->iters_done counts the iterations run).
+cudaError_t iterate_panel_loop(const void* packed, const PanelGeom& g, float* X0, float* X1, float* Y, float eta, int K,
+                               int safeguard, int T, double tol, Ctl* ctl, const int* skip, cudaStream_t st) {
+  LoopArgs a{StreamArgs{reinterpret_cast<const uint8_t*>(packed), X0, Y, ctl, skip, g}, X0, X1, eta, K, safeguard, T,
+             tol};
   switch (g.D) {
-    case 1: return launch_iter_st<1>(a, st);
-    case 2: return launch_iter_st<2>(a, st);
-    case 3: return launch_iter_st<3>(a, st);
-    case 4: return launch_iter_st<4>(a, st);
-    case 5: return launch_iter_st<5>(a, st);
-    case 6: return launch_iter_st<6>(a, st);
-    case 7: return launch_iter_st<7>(a, st);
-    case 8: return launch_iter_st<8>(a, st);
+    case 1: return launch_loop_st<1>(a, st);
+    case 2: return launch_loop_st<2>(a, st);
+    case 3: return launch_loop_st<3>(a, st);
+    case 4: return launch_loop_st<4>(a, st);
+    case 5: return launch_loop_st<5>(a, st);
+    case 6: return launch_loop_st<6>(a, st);
+    case 7: return launch_loop_st<7>(a, st);
   }
   return cudaErrorInvalidValue;
 }
