@@ -52,9 +52,9 @@ struct Ctl {
   int spec_restart;        // the next spectral pass restarts from V^0 with a larger shift
   int spec_round;          // restarts taken so far
   int spec_prev;           // batched / served instances: passes run before the last restart
-  unsigned int gbar_count; // fused iteration kernel: CTAs arrived at the grid barrier
-  unsigned int gbar_gen;   // fused iteration kernel: grid barrier generation
+  unsigned int gbar_count; // fused iteration loop: grid-barrier arrivals of the launch (monotonic)
   int pad;
+  double upd_acc2[2];      // fused iteration loop: update-norm sums of even / odd iterations
 };
 
 // Restarts the spectral start may take with a larger shift before it gives up

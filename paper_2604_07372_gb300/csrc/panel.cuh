@@ -320,6 +320,9 @@ __device__ __forceinline__ void panel_stream_range(const Src& src, long long g0,
   if (warp == C::NW) {
     // ------------------------------------------------------------- producer
     if (lane == 0) {
+    // X may have been written by generic stores since the last pass (of this
+    // launch, in a persistent kernel): order them before this thread's bulk copies
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     int& st = pp.st;
     uint32_t& ph = pp.ph;
     long long& issued = pp.it;
