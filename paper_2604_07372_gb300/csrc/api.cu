@@ -37,8 +37,7 @@ cudaError_t stream_dense(const void* packed, int n, int d, const float* X, float
                          cudaStream_t st);
 cudaError_t stream_panel_prepare(const PanelGeom& g);
 cudaError_t iterate_panel_loop(const void* packed, const PanelGeom& g, float* X0, float* X1, float* Y, float eta, int K,
-                               int safeguard, int T, double tol, double* rate, Ctl* ctl, const int* skip,
-                               cudaStream_t st);
+                               int safeguard, int T, double tol, Ctl* ctl, const int* skip, cudaStream_t st);
 
 int reduce_grid(long long rows);
 cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
@@ -283,7 +282,7 @@ enum { METHOD_NSRGS = 0, METHOD_GPM = 1, METHOD_NSRGS_OBJECTIVE = 2 };
 // block update's 8 x 8 registers, so there each iteration stays a stream launch
 // plus an epilogue launch.
 static bool fused_loop(const nsrgs_A* A, int method) {
-  return method == METHOD_NSRGS && A->d <= 7 && num_sms() <= kMaxReduceGrid &&
+  return method == METHOD_NSRGS && A->d <= 7 &&
          (A->storage == NSRGS_F32 || A->storage == NSRGS_BF16 || A->storage == NSRGS_FP8E4M3);
 }
 
@@ -294,10 +293,7 @@ static cudaError_t enqueue_iterations(const nsrgs_A* A, const PanelGeom& g, cons
   if (fused_loop(A, method)) {
     if (T == 0) return cudaSuccess;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    // the per-CTA rates (two per SM) live in the spectral passes' partial-sum
-    // scratch (idle now; at least 2 * kMaxReduceGrid doubles)
-    e = iterate_panel_loop(A->packed, g, w.X[0], w.X[1], w.Y, eta, K, safeguard, T, tol, w.s.partials, w.ctl,
-                           &w.ctl->stop, st);
+    e = iterate_panel_loop(A->packed, g, w.X[0], w.X[1], w.Y, eta, K, safeguard, T, tol, w.ctl, &w.ctl->stop, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;

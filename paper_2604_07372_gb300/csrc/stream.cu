@@ -58,36 +58,8 @@ struct LoopArgs {
   int safeguard;
   int T;
   double tol;       // > 0: stop after the first iteration whose update norm is below it
-  double* rate;     // 2 gridDim.x doubles of scratch: each CTA's measured steps per ns, by parity
 };
 
-// The CTAs' step ranges of the next pass, from their measured rates: the split
-// point before CTA b moves halfway towards total * (sum of the rates of CTAs < b)
-// / (sum of all rates), so every CTA's share tracks its speed.  Warp 0 computes
-// the two boundaries of its CTA (every CTA gets the same numbers for a shared
-// boundary: the same inputs in the same order).
-__device__ __forceinline__ void rebalance(const double* rate, long long total, long long& g0, long long& g1) {
-  const int lane = threadIdx.x & 31, G = gridDim.x, b = blockIdx.x;
-  double below0 = 0.0, below1 = 0.0, all = 0.0;
-  for (int c = lane; c < G; c += 32) {
-    const double r = *reinterpret_cast<const volatile double*>(rate + c);
-    all += r;
-    if (c < b) below0 += r;
-    if (c < b + 1) below1 += r;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    all += __shfl_xor_sync(0xffffffffu, all, o);
-    below0 += __shfl_xor_sync(0xffffffffu, below0, o);
-    below1 += __shfl_xor_sync(0xffffffffu, below1, o);
-  }
-  if (!(all > 0.0)) return;
-  const long long t0 = b == 0 ? 0 : (long long)((double)total * (below0 / all));
-  const long long t1 = b == G - 1 ? total : (long long)((double)total * (below1 / all));
-  g0 = (g0 + (t0 < total ? t0 : total)) / 2;
-  g1 = (g1 + (t1 < total ? t1 : total)) / 2;
-  if (b == 0) g0 = 0;
-  if (b == G - 1) g1 = total;
-}
 
 // Grid-wide barrier on a monotonic arrival counter of the control block: barrier
 // number k of a launch completes when the counter reaches (k + 1) * gridDim.x
@@ -135,10 +107,9 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_loop_kernel(con
   if (*a.s.skip || (*reinterpret_cast<volatile unsigned int*>(&ctl->flags) & FLAG_TIMEOUT)) return;
   __shared__ double sh[32];
   __shared__ int s_stop;
-  __shared__ long long s_range[2];
   const long long total = a.s.g.total_steps;
-  long long g0 = total * blockIdx.x / gridDim.x;
-  long long g1 = total * (blockIdx.x + 1) / gridDim.x;
+  const long long g0 = total * blockIdx.x / gridDim.x;
+  const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
   const int n = a.s.g.n;
   const long long b0 = (long long)n * blockIdx.x / gridDim.x;
   const long long b1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
@@ -149,19 +120,10 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_loop_kernel(con
   for (int t = 0; t < a.T; ++t) {
     const float* Xt = (t & 1) ? a.X1 : a.X0;
     float* Xn = (t & 1) ? a.X0 : a.X1;
-    const uint64_t t_start = globaltimer_ns();
     if (g0 < g1) {
       sa.X = Xt;
       SingleSrc src{&sa};
       panel_stream_range<D, ST>(src, g0, g1, pp, RES_RING);
-    }
-    __syncthreads();
-    // this CTA's streaming rate, into the half of the rate table of this pass's
-    // parity (the other half may still be read for the split of the last pass)
-    double* rate = a.rate + (t & 1) * gridDim.x;
-    if (threadIdx.x == 0) {
-      const double dt = (double)(globaltimer_ns() - t_start);
-      rate[blockIdx.x] = (g1 > g0 && dt > 0.0) ? (double)(g1 - g0) / dt : 0.0;
     }
     if (!grid_barrier_bounded(ctl, (2u * t + 1u) * gridDim.x)) return;
     // this CTA's blocks of Algorithm 2's update
@@ -192,16 +154,7 @@ __global__ void __launch_bounds__(PCfg<D, ST>::THREADS, 1) panel_loop_kernel(con
       }
       s_stop = stop;
     }
-    if (threadIdx.x < 32) {  // the next pass's step range from the rates measured in this one
-      rebalance(rate, total, g0, g1);
-      if (threadIdx.x == 0) {
-        s_range[0] = g0;
-        s_range[1] = g1;
-      }
-    }
     __syncthreads();
-    g0 = s_range[0];
-    g1 = s_range[1];
     if (s_stop) break;
   }
 }
@@ -328,10 +281,9 @@ static cudaError_t launch_loop_st(const LoopArgs& a, cudaStream_t st) {
 // T iterations on the panel layout in one launch, from X0 (X^t alternates between
 // X0 and X1; ctl->iters_done counts the iterations run).
 cudaError_t iterate_panel_loop(const void* packed, const PanelGeom& g, float* X0, float* X1, float* Y, float eta, int K,
-                               int safeguard, int T, double tol, double* rate, Ctl* ctl, const int* skip,
-                               cudaStream_t st) {
+                               int safeguard, int T, double tol, Ctl* ctl, const int* skip, cudaStream_t st) {
   LoopArgs a{StreamArgs{reinterpret_cast<const uint8_t*>(packed), X0, Y, ctl, skip, g}, X0, X1, eta, K, safeguard, T,
-             tol, rate};
+             tol};
   switch (g.D) {
     case 1: return launch_loop_st<1>(a, st);
     case 2: return launch_loop_st<2>(a, st);
