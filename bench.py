@@ -89,7 +89,7 @@ def profiled_traffic(kernel_tag: str):
         return None
     csrc = os.path.join(ROOT, "paper_2604_07372_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("stream.cu", "panel.cuh", "common.cuh"):
+    for name in ("stream.cu", "panel.cuh", "common.cuh", "blockops.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -779,7 +779,7 @@ def run_ours(args, world, rank, local):
 
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    tag = f"panel_stream_{main_st}_n{n}_d{d}"
+    tag = f"panel_loop_{main_st}_n{n}_d{d}"
     roofline = {
         "bound": "hbm",
         "achieved": achieved,
@@ -787,7 +787,8 @@ def run_ours(args, world, rank, local):
         "unit": "GB/s",
         "frac": achieved / peaks["hbm_gbs"],
         "traffic": profiled_traffic(tag),
-        "kernel": f"panel_stream_kernel<D={d},{main_st.upper()}> (symmetric A-stream, one launch per iteration)",
+        "kernel": (f"panel_loop_kernel<D={d},{main_st.upper()}> (all T iterations in one launch; per pass: symmetric "
+                   "A-stream, grid barrier, block updates, grid barrier; time per pass = launch / T)"),
         "algorithmic_bytes_per_launch": alg_bytes,
         "mean_launch_ms": kern_ms,
         "launches_timed": launches,
