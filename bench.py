@@ -342,7 +342,8 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
         # f32: panels for d <= 8, the float32 tile-upper stream above (CUDA cores, half the dense bytes)
-        storages = ["dense_f32", "f32"] + (["bf16"] if d <= 8 else []) + (["dense_bf16", "bf16"] if d in (16, 32, 64) else [])
+        storages = (["dense_f32", "f32"] + (["bf16"] if d <= 8 else []) +
+                    (["dense_bf16", "bf16", "fp8"] if d in (16, 32, 64) else []))
         if only:
             storages = [x for x in storages if x in only]
         res = {}
@@ -363,7 +364,8 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / reps
-                alg = {"dense_f32": 2 * nb * 4, "dense_bf16": 2 * nb * 2, "f32": nb * 4, "bf16": nb * 2}[name]
+                alg = {"dense_f32": 2 * nb * 4, "dense_bf16": 2 * nb * 2, "f32": nb * 4, "bf16": nb * 2,
+                       "fp8": nb}[name]
                 ent = {"product_ms": ms, "alg_GB": alg / 1e9, "GBps": alg / (ms / 1e3) / 1e9,
                        "flops_TFs": 2 * 2 * nb * d / (ms / 1e3) / 1e12}
                 Xs, info = P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, ws=ws)
@@ -373,6 +375,7 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                 torch.cuda.synchronize()
                 ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
                 ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
+                ent["spectral_iters"], ent["flags"] = info.spectral_iters, info.flags
                 # the A stream alone inside a solve (CUDA events around each launch in the graph)
                 P.nsrgs_set_kernel_timing(True)
                 P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, X=Xs, ws=ws, info=False)
@@ -449,6 +452,7 @@ def sparse_leg(P, synth, seed: int, n: int = 8000, d: int = 3, ps=(0.05, 0.2, 0.
                 torch.cuda.synchronize()
                 ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
                 ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
+                ent["spectral_iters"], ent["flags"] = info.spectral_iters, info.flags
                 res[name] = ent
                 del pa, ws, X, Y
             except Exception as e:

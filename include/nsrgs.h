@@ -68,7 +68,15 @@ typedef enum {
  *  FP8E4M3 : A stored as FP8 E4M3 (round to nearest, saturating at +-448) with one
  *            float32 scale per block row i: s_i = max_{j>i} max|A_ij| / 448 and
  *            A_ij ~ s_i * q_ij.  The per-block-row scale is this library's choice;
- *            the paper does not discuss reduced precision.
+ *            the paper does not discuss reduced precision.  For d <= 4 the panel
+ *            layout on the CUDA cores (X float32).  For d in {16, 32, 64} the
+ *            tile-upper layout of BF16 with one byte per element (16 KB tiles, the n
+ *            scales behind them) on the tensor cores (tcgen05 kind::f8f6f4): X
+ *            enters as two E4M3 planes hi = RN(g X), lo = RN(g X - hi) at a
+ *            power-of-two g from max |X| (about 2^-8 relative together), the column
+ *            product takes the rows s_i X_i as its operand (the scale runs along K
+ *            there) and the row product's result is multiplied by s_i; float32
+ *            accumulation in TMEM.  A quarter of DENSE_BF16's bytes.
  *  DENSE_F32: the full nd x nd float32 matrix, both triangles, no symmetric reuse
  *            (twice the bytes of F32).  Works for every d; it is the plain form the
  *            symmetric layouts are measured against.
@@ -119,7 +127,9 @@ typedef struct nsrgs_info {
                               bit 2: spectral initialisation not converged;
                               bit 4: the safeguarded Newton-Schulz start acted;
                               bit 6: the spectral initialisation restarted with a larger
-                              shift to reach the algebraic top-d (see nsrgs_spectral_init) */
+                              shift to reach the algebraic top-d (see nsrgs_spectral_init);
+                              bit 7: the spectral initialisation stopped at its product's
+                              precision floor, above tol (tensor-core storage only) */
   double objective;        /* nsrgs_solve_objective: F(X) of eq. (1) at the returned X; NaN otherwise */
   double rel_decrease;     /* nsrgs_solve_objective: the last relative decrease R^t formed; NaN otherwise */
 } nsrgs_info;
@@ -127,7 +137,7 @@ typedef struct nsrgs_info {
 /* ---------------------------------------------------------------- sizes */
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
- * supported (F32: any d <= 64; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4;
+ * supported (F32: any d <= 64; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4 and d in {16, 32, 64};
  * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}; BCSR_*: d <= 8, the
  * bound for fully observed data -- see nsrgs_bcsr_packed_bytes for the exact size). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
@@ -171,7 +181,12 @@ nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* p
  * with c raised above the negative end of the spectrum (a Gershgorin bound of
  * that d x d matrix), at most 3 times (info flags bit 6).  Restarts count
  * against max_iters; a basis that still fails after the last restart is
- * reported as not converged.
+ * reported as not converged.  The tensor-core storages (NSRGS_DENSE_BF16, and
+ * BF16 / FP8E4M3 at d in {16, 32, 64}) multiply a rounded V (bfloat16, or E4M3
+ * hi + lo planes, about 2^-8 relative), which puts a floor under the residual,
+ * typically 1e-4 .. 1e-3: there the passes also count as converged once the
+ * residual is at most 1e-2 and no smaller than the previous pass's (info flags
+ * bit 7), and the same positive-definiteness test follows.
  * The per-block matrix sign is exact (float64 one-sided Jacobi SVD).  Returns
  * NSRGS_ERR_NOT_CONVERGED (X0 still written) when max_iters ran out; with
  * `residual` non-null the final residual is written there (host; synchronises). */

@@ -69,10 +69,16 @@ cudaError_t bcsr_count_upper(const float* upper, int n, int d, unsigned long lon
 cudaError_t bcsr_count_dense(const float* A, int n, int d, unsigned long long* d_total, cudaStream_t st);
 bool tc_sym_supported(int d);
 long long tc_sym_bytes(int n, int d);
-long long tc_sym_xt_bytes(int n, int d);
-cudaError_t tc_sym_prepare(int d);
-cudaError_t tc_sym_product(const void* packed, int n, int d, const float* X, uint8_t* xt, float* Y, Ctl* ctl,
-                           const int* skip, cudaStream_t st);
+long long tc_sym8_bytes(int n, int d);
+long long tc_sym8_xt_bytes(int n, int d);
+cudaError_t tc_sym_prepare(int d, bool f8);
+cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const float* X, uint8_t* xt, float* Y,
+                           Ctl* ctl, const int* skip, cudaStream_t st);
+
+// Tile-upper tensor-core storage: BF16 or FP8 at d in {16, 32, 64}.
+static bool tile_upper(int storage, int d) {
+  return (storage == NSRGS_BF16 || storage == NSRGS_FP8E4M3) && tc_sym_supported(d);
+}
 bool fs_sym_supported(int d);
 long long fs_sym_bytes(int n, int d);
 long long fs_sym_xt_bytes(int n, int d);
@@ -132,10 +138,11 @@ static Workspace map_workspace(void* base, int n, int d) {
   w.obj.Yprev = reinterpret_cast<float*>(take(vec));
   if (d > 8) {
     // X^T: bfloat16 row-major for the dense tensor-core stream, swizzled bfloat16 tiles
-    // for the tile-upper tensor-core stream, float32 64-row tiles for the float32 tile stream
+    // (or two sets of E4M3 hi / lo planes) for the tile-upper tensor-core stream,
+    // float32 64-row tiles for the float32 tile stream
     long long a = fs_sym_xt_bytes(n, d);
     if (d >= 16) {
-      const long long b = (long long)d * dense_bf16_pitch(n, d) * 2, c = tc_sym_xt_bytes(n, d);
+      const long long b = (long long)d * dense_bf16_pitch(n, d) * 2, c = tc_sym8_xt_bytes(n, d);
       a = a > b ? a : b;
       a = a > c ? a : c;
     }
@@ -184,8 +191,8 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     return NSRGS_OK;
   }
   NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
-  if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d)) {
-    NSRGS_CUDA_TRY(tc_sym_prepare(A->d));
+  if (tile_upper(A->storage, A->d)) {
+    NSRGS_CUDA_TRY(tc_sym_prepare(A->d, A->storage == NSRGS_FP8E4M3));
     return NSRGS_OK;
   }
   if (A->storage == NSRGS_F32 && fs_sym_supported(A->d)) {
@@ -193,7 +200,7 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     return NSRGS_OK;
   }
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
-    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4 or d in {16, 32, 64}; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   NSRGS_CUDA_TRY(stream_panel_prepare(*g));
@@ -216,8 +223,9 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
                              const int* skip, cudaStream_t st) {
   if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, w.Y, skip, st);
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
-  if (A->storage == NSRGS_BF16 && tc_sym_supported(A->d))
-    return tc_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl, skip, st);
+  if (tile_upper(A->storage, A->d))
+    return tc_sym_product(A->packed, A->n, A->d, A->storage == NSRGS_FP8E4M3, X, reinterpret_cast<uint8_t*>(w.XT),
+                          w.Y, w.ctl, skip, st);
   if (A->storage == NSRGS_F32 && fs_sym_supported(A->d))
     return fs_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<float*>(w.XT), w.Y, w.ctl, skip, st);
   if (bcsr_storage(A->storage)) return bcsr_stream(A->packed, A->n, A->d, A->storage, X, w.Y, skip, w.ctl, st);
@@ -257,6 +265,9 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
                                     double tol, float* out, cudaStream_t st) {
   const int n = A->n, d = A->d;
   const long long rows = (long long)n * d;
+  // the tensor-core streams round V (bfloat16, or E4M3 hi / lo planes): their passes
+  // may also stop at the residual floor that rounding sets
+  const int counted = (A->storage == NSRGS_DENSE_BF16 || tile_upper(A->storage, d)) ? 2 : 1;
   cudaError_t e;
   if ((e = launch_spec_v0(w.X[0], rows, d, w.s.scal + 3, st)) != cudaSuccess) return e;
   // orthonormalise the start: W = V0 (Y is zero), V1 = W chol(W^T W)^{-1}
@@ -267,7 +278,7 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
     float* Vn = w.X[k & 1];
     if ((e = stream_AX(A, g, V, w, &w.ctl->spec_skip, st)) != cudaSuccess) return e;
     if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, 1, w.s, w.ctl, st)) != cudaSuccess) return e;
-    if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, 1, w.ctl, st)) != cudaSuccess) return e;
+    if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, counted, w.ctl, st)) != cudaSuccess) return e;
   }
   // final basis -> W, then X0 = sgn_n(W)
   if ((e = launch_select_copy(w.X[0], w.X[1], w.W, rows * d, w.ctl, st)) != cudaSuccess) return e;
@@ -413,6 +424,7 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (storage == NSRGS_DENSE_BF16)
     return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
   if (storage == NSRGS_BF16 && tc_sym_supported(d)) return (size_t)tc_sym_bytes(n, d);
+  if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) return (size_t)tc_sym8_bytes(n, d);
   if (storage == NSRGS_F32 && fs_sym_supported(d)) return (size_t)fs_sym_bytes(n, d);
   if (bcsr_storage(storage)) return d <= 8 ? (size_t)bcsr_bytes(n, d, storage, (long long)n * (n - 1)) : 0;
   PanelGeom g;
@@ -747,7 +759,8 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
     info->iters = c.iters_done;
     info->last_update_norm = c.last_upd;
     info->spectral_residual = c.spec_res;
-    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED | FLAG_SPEC_SHIFTED)) |
+    info->flags = (c.flags & (FLAG_NONFINITE | FLAG_NS_PRECOND | FLAG_NS_SAFEGUARDED | FLAG_SPEC_SHIFTED |
+                             FLAG_SPEC_AT_FLOOR)) |
                   ((init && !c.spec_stop) ? FLAG_SPEC_NOT_CONVERGED : 0);
     if (c.flags & FLAG_BAD_LAYOUT) {
       set_error("the packed A is inconsistent: an index or address left its buffer (access skipped)");

@@ -55,7 +55,17 @@ struct Ctl {
   unsigned int gbar_count; // fused iteration loop: grid-barrier arrivals of the launch (monotonic)
   int pad;
   double upd_acc2[2];      // fused iteration loop: update-norm sums of even / odd iterations
+  unsigned int ts8_max[2]; // FP8 tile-upper product: max |X| and max |s_i X_i| (float bits)
+  double spec_prev_res;    // relative residual of the previous counted spectral pass (0: none since a start)
 };
+
+// A spectral start whose product rounds its operand (the tensor-core streams take
+// V in bfloat16 or as E4M3 hi / lo planes) settles at a residual floor of about
+// the operand's precision times ||A_off V_perp|| / ||A_off V||: below the floor
+// further passes only move V within that rounding.  Such a start also stops once
+// its residual, at most kSpecFloorMax, failed to decrease from one pass to the
+// next (and reports FLAG_SPEC_AT_FLOOR).
+constexpr double kSpecFloorMax = 1e-2;
 
 // Restarts the spectral start may take with a larger shift before it gives up
 // (then it reports the subspace as not converged).
@@ -78,6 +88,7 @@ enum : unsigned int {
   FLAG_NS_SAFEGUARDED = 1u << 4,  // the safeguarded Newton-Schulz start was used for some block
   FLAG_BAD_LAYOUT = 1u << 5,      // a packed buffer's index or address left its buffer (access skipped)
   FLAG_SPEC_SHIFTED = 1u << 6,    // the spectral start restarted with a larger shift (see spec_shift_after)
+  FLAG_SPEC_AT_FLOOR = 1u << 7,   // the spectral start stopped at its product's precision floor, above tol
 };
 
 // float64 scratch of the spectral initialisation and of d_F (all d x d unless noted).

@@ -24,6 +24,7 @@
 
 #include "bcsr.cuh"
 #include "blockops.cuh"
+#include "tc_sym.cuh"
 
 namespace nsrgs {
 
@@ -260,6 +261,50 @@ __global__ void __launch_bounds__(256) norm2_fp8_panel_kernel(const uint8_t* __r
   }
 }
 
+// FP8 tile-upper layout: the stored triangle once, each E4M3 code times its
+// block row's scale.  A CTA walks a contiguous range of the tile order.
+template <int R>
+__global__ void __launch_bounds__(256) norm2_ts8_kernel(const uint8_t* __restrict__ packed, int n, int d, ObjScratch o,
+                                                       Ctl* ctl) {
+  __shared__ double sh[32];
+  __shared__ int tile_i;
+  const int NT = ts_tile_rows(n, d);
+  const long long rows = (long long)n * d;
+  const float* scale = reinterpret_cast<const float*>(packed + ts8_scale_offset(n, d));
+  const long long total = ts_tiles(NT);
+  const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+  TsWalk<R> w;
+  w.NT = NT;
+  if (threadIdx.x == 0 && t0 < t1) w.seek(t0);
+  double acc = 0.0;
+  for (long long t = t0; t < t1; ++t) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tile_i = w.I();
+      bool se, ge;
+      w.next(se, ge);
+    }
+    __syncthreads();
+    const uint8_t* tile = packed + t * (long long)kTs8TileBytes;
+    for (int e = threadIdx.x; e < kTs8TileBytes; e += blockDim.x) {
+      const long long row = (long long)tile_i * kTsTile + ts8_row_of(e);
+      if (row >= rows) continue;
+      const __half_raw h = __nv_cvt_fp8_to_halfraw(tile[e], __NV_E4M3);
+      const double v = (double)__half2float(__half(h)) * scale[row / d];
+      acc += v * v;
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) o.partials[blockIdx.x] = acc;
+  if (!last_block(&ctl->counter)) return;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) v += o.partials[c];
+    o.scal[OBJ_A2] = 2.0 * v;
+    ctl->counter = 0u;
+  }
+}
+
 // ------------------------------------------------------------- launchers
 cudaError_t launch_objective(const float* Xc, const float* Yc, const float* Xp, float* Yp, int n, int D,
                              double rel_tol, const ObjScratch& o, Ctl* ctl, cudaStream_t st) {
@@ -291,6 +336,10 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
     // tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), tc_sym_bytes(n, d) / 2, 2.0,
                                             o, ctl);
+  } else if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) {
+    const uint8_t* p = reinterpret_cast<const uint8_t*>(packed);
+    if (d == 64) norm2_ts8_kernel<ts_strip_rows(64)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    else norm2_ts8_kernel<ts_strip_rows(16)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
   } else if (storage == NSRGS_F32 && fs_sym_supported(d)) {
     // float32 tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(packed), fs_sym_bytes(n, d) / 4, 2.0, o,

@@ -165,7 +165,8 @@ long long dense_pitch(int n, int d) { return ((long long)n * d + 3) / 4 * 4; }
 long long dense_bf16_pitch(int n, int d);
 bool tc_sym_supported(int d);
 template <class Src>
-cudaError_t tc_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st);
+cudaError_t tc_sym_pack(Src src, int n, int d, bool f8, void* packed, cudaStream_t st);
+long long tc_sym8_scale_offset(int n, int d);
 bool fs_sym_supported(int d);
 template <class Src>
 cudaError_t fs_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st);
@@ -186,7 +187,13 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
   }
   if constexpr (!std::is_same_v<Src, SeAugSrc>) {  // the SE(d) form uses panels only
     if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
-      NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, packed, st));
+      NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, false, packed, st));
+      return NSRGS_OK;
+    }
+    if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) {  // block-row scales first, behind the tiles
+      fp8_scale_kernel<<<n, 256, 0, st>>>(src, n, d, (float*)((uint8_t*)packed + tc_sym8_scale_offset(n, d)));
+      NSRGS_CUDA_TRY(cudaGetLastError());
+      NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, true, packed, st));
       return NSRGS_OK;
     }
     if (storage == NSRGS_F32 && fs_sym_supported(d)) {
@@ -196,7 +203,7 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
   }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
-    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4 or d in {16, 32, 64}; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   std::vector<long long> tab;

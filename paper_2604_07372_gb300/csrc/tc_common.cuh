@@ -1,6 +1,7 @@
 // tcgen05 building blocks shared by the tensor-core A-streams: shared-memory
 // matrix descriptors (128-byte swizzle), MMA issue and commit, TMEM loads and
-// the thread-sync fences.  BF16 x BF16 -> FP32 (kind::f16), one CTA (cta_group::1).
+// the thread-sync fences.  BF16 x BF16 -> FP32 (kind::f16) and E4M3 x E4M3 -> FP32
+// (kind::f8f6f4), one CTA (cta_group::1).
 #pragma once
 
 #include "common.cuh"
@@ -30,11 +31,26 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N, bool a_mn_major) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: D = f32, A = B = E4M3 (format code 0), N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t tc8_idesc(int M, int N, bool a_mn_major) {
+  return (1u << 4) | (a_mn_major ? (1u << 15) : 0u) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// D (+)= A B with one-byte E4M3 operands: K = 32 elements (32 bytes) per instruction.
+__device__ __forceinline__ void tc_mma8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }

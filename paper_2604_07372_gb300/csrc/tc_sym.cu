@@ -1,5 +1,6 @@
 // Y = A_off X on the tensor cores reading only the upper triangle of A, for
-// d in {16, 32, 64} with A stored in bfloat16 (NSRGS_BF16 at these d).
+// d in {16, 32, 64} with A stored in bfloat16 (NSRGS_BF16 at these d) or in
+// FP8-E4M3 with one float32 scale per block row (NSRGS_FP8E4M3 at these d).
 //
 // Layout ("tile-upper"): the nd x nd matrix is cut into 128 x 128 tiles; tile
 // (I, J) is stored for J >= I only, in the order the kernel visits them (groups
@@ -7,28 +8,38 @@
 // so that every CTA streams one contiguous range of the buffer.
 // A diagonal tile keeps the blocks strictly above the block diagonal (d divides
 // 128, so blocks never straddle tiles); everything else in it is zero.  Each
-// tile is 32 KB, already in the 128-byte-swizzled order the tensor core reads:
-// 8-row groups 2048 bytes apart, inside a group the two 64-column halves 1024
-// bytes apart, rows 128 bytes apart, 16-byte chunk k of row r at k ^ (r % 8).
+// tile is already in the 128-byte-swizzled order the tensor core reads (32 KB
+// in bfloat16, 16 KB in E4M3: ts_swz / ts8_swz).  FP8 storage keeps
+// q_ij = RN(A_ij / s_i) with s_i = max_{j > i} max |A_ij| / 448 (the rule of the
+// FP8 panels), the n scales behind the tiles.
 // One tile feeds both products of the symmetric form:
 //   Y_I += A_IJ X_J     (A_IJ as a K-major operand, M = 128 rows, K = 128 columns)
 //   Y_J += A_IJ^T X_I   (the same bytes as an MN-major operand: M = 128 columns,
-//                        K = 128 rows; MN atoms 1024 bytes apart, K groups 2048)
-// X^T is rounded to bfloat16 and stored per 128-row tile in the same swizzled
-// order (N rows of 256 bytes), so every copy is a plain 1-D bulk copy.
+//                        K = 128 rows)
+// X^T is stored per 128-row tile in the same swizzled order (N rows), so every
+// copy is a plain 1-D bulk copy.  In bfloat16 it is X rounded to nearest.  With
+// FP8 tiles both MMA operands are E4M3, so X travels as two E4M3 planes, hi =
+// RN(g X) and lo = RN(g X - hi) with g a power of two that puts max |X| in
+// [128, 256): hi + lo carries X to about 2^-8 relative, and both planes
+// accumulate into the same TMEM columns.  The row product uses X (scale g_r;
+// its result is multiplied by s_i / g_r per output row), the column product
+// uses the rows s_i X_i (scale g_c, result times 1 / g_c): the block-row scale
+// runs along K there, so it is folded into the operand instead of the result.
 //
 // Per CTA (6 warps, persistent over a contiguous range of the processing order):
 // tiles are visited in column strips of R row tiles (a group of R row panels,
 // columns J = I0 .. NT-1, rows I0 .. I0+R-1 in each column), so the column
 // product accumulates over a whole strip (K = up to 128 R rows) before it is
 // added to Y, and the row products of the R panels stay in TMEM over the group.
-//   warp 0 lane 0 : producer.  cp.async.bulk of each tile (32 KB) with its X_J^T
-//                   tile into a ring of stages, and of the group's R X_I^T tiles
-//                   into one buffer when a group starts; mbarrier expect_tx.
+//   warp 0 lane 0 : producer.  cp.async.bulk of each tile into a ring of stages
+//                   (as many as shared memory holds), of X_J^T into one of two
+//                   slots when a strip starts (every tile of a strip shares J),
+//                   and of the group's R X_I^T tiles into one buffer when a group
+//                   starts; mbarrier expect_tx.
 //   warp 1        : allocates TMEM (D1: R slots of N columns, D2: two buffers of
-//                   N columns); lane 0 issues tcgen05.mma (eight K = 16 steps for
-//                   D1[r] += A X_J, eight for D2 += A^T X_I) and commits the
-//                   stage, D2 at a strip's end and D1 at a group's end.
+//                   N columns); lane 0 issues tcgen05.mma (D1[r] += A X_J over
+//                   the tile's columns, D2 += A^T X_I over its rows) and commits
+//                   the stage, D2 at a strip's end and D1 at a group's end.
 //   warps 2..5    : epilogue.  tcgen05.ld of their 32-lane quarter of D2 (rows =
 //                   the strip's columns) and of the used D1 slots, then
 //                   red.global.add.v4.f32 into Y.
@@ -37,44 +48,41 @@
 
 #include "src.cuh"
 #include "tc_common.cuh"
+#include "tc_sym.cuh"
 
 namespace nsrgs {
 
-constexpr int kTsTile = 128;
-constexpr int kTsTileBytes = kTsTile * kTsTile * 2;  // 32 KB
-
-__host__ __device__ inline int ts_tile_rows(int n, int d) { return (int)(((long long)n * d + kTsTile - 1) / kTsTile); }
-__host__ __device__ inline long long ts_tiles(int NT) { return (long long)NT * (NT + 1) / 2; }
-
-// Byte offset of element (r, c) inside a swizzled 128 x 128 tile, and of
-// element (n, k) (n < N rows, k < 128) inside a swizzled N x 128 X^T tile.
-__host__ __device__ inline int ts_swz(int r, int c) {
-  const int s = c >> 6, k = (c & 63) >> 3, e = c & 7;
-  return (r >> 3) * 2048 + s * 1024 + (r & 7) * 128 + ((k ^ (r & 7)) << 4) + e * 2;
-}
-
-template <int N>
+template <int N, bool F8>
 struct TsCfg {
-  static constexpr int R = N == 64 ? 4 : 8;              // row tiles per strip
-  static constexpr int XB = N * 256;                      // one X^T tile
-  static constexpr int STAGE = kTsTileBytes + XB;        // A tile + X_J^T tile
-  static constexpr int NSTAGE = N == 16 ? 5 : 3;
-  static constexpr int OFF_XI = NSTAGE * STAGE;          // X^T of the group's R row tiles
+  static constexpr int TILE = F8 ? kTs8TileBytes : kTsTileBytes;
+  static constexpr int R = ts_strip_rows(N);             // row tiles per strip
+  static constexpr int XB = N * 256;                      // one X^T tile (FP8: hi and lo planes)
+  static constexpr int STAGE = TILE;                      // the ring holds A tiles only
+  static constexpr int SMEM_MAX = 227 * 1024;
+  // as many stages as fit beside the two X_J^T slots and the group's R X_I^T tiles
+  static constexpr int NSTAGE_FIT = (SMEM_MAX - 1024 - 512 - (2 + R) * XB) / STAGE;
+  static constexpr int NSTAGE = NSTAGE_FIT > 12 ? 12 : NSTAGE_FIT;
+  static constexpr int OFF_XJ = NSTAGE * STAGE;          // X_J^T of the current / next strip
+  static constexpr int OFF_XI = OFF_XJ + 2 * XB;         // X^T of the group's R row tiles
   static constexpr int OFF_BARS = OFF_XI + R * XB;
-  static constexpr int NBARS = 2 * NSTAGE + 2 + 4 + 2;
+  static constexpr int NBARS = 2 * NSTAGE + 2 + 4 + 2 + 4;
   static constexpr int SMEM = 1024 + OFF_BARS + NBARS * 8 + 16;
   static constexpr int TMEM_NEED = (R + 2) * N;          // D1: R slots, D2: two buffers
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : (TMEM_NEED <= 128 ? 128 : (TMEM_NEED <= 256 ? 256 : 512));
-  static constexpr uint32_t IDESC_ROW = tc_idesc(128, N, false);  // D1 += A X_J
-  static constexpr uint32_t IDESC_COL = tc_idesc(128, N, true);   // D2 += A^T X_I (A read MN-major)
-  static_assert(STAGE % 1024 == 0 && XB % 1024 == 0, "1024-byte swizzle alignment");
-  static_assert(SMEM <= 227 * 1024, "shared memory");
+  // D1 += A X_J and D2 += A^T X_I (A read MN-major)
+  static constexpr uint32_t IDESC_ROW = F8 ? tc8_idesc(128, N, false) : tc_idesc(128, N, false);
+  static constexpr uint32_t IDESC_COL = F8 ? tc8_idesc(128, N, true) : tc_idesc(128, N, true);
+  static_assert(STAGE % 1024 == 0 && XB % 1024 == 0 && (N * 128) % 1024 == 0, "1024-byte swizzle alignment");
+  static_assert(NSTAGE >= 3, "pipeline depth");
+  static_assert(SMEM <= SMEM_MAX, "shared memory");
   static_assert(TMEM_NEED <= 512, "tensor memory");
 };
 
 struct TsArgs {
   const uint8_t* tiles;  // packed tiles
-  const uint8_t* xt;     // swizzled X^T tiles (NT x N*256 bytes)
+  const uint8_t* xt;     // swizzled X^T tiles for the row product (NT x N*256 bytes)
+  const uint8_t* xc;     // for the column product (the same as xt in bfloat16; rows s_i X_i in FP8)
+  const float* rscale;   // FP8: per-block-row scales s_i
   float* Y;              // padded, zero on entry
   const int* skip;
   Ctl* ctl;
@@ -82,64 +90,19 @@ struct TsArgs {
   int NT;
 };
 
-// Processing order: groups of R row tiles (I0 = g R), inside a group the
-// columns J = I0 .. NT-1, inside a column ("strip") the rows I = I0 .. min(I0 +
-// R, J + 1, NT) - 1.  Each tile appears once.  D1 (one slot per row of the
-// group) lives across the group; D2 (the strip's column tile) across the strip.
-template <int R>
-struct TsWalk {
-  int NT, g, I0, Rg, J, r;
-  __device__ int strip_len() const { return min(Rg, J - I0 + 1); }
-  __device__ void set_group(int gg) {
-    g = gg;
-    I0 = g * R;
-    Rg = min(R, NT - I0);
-    J = I0;
-    r = 0;
-  }
-  // Position of tile number t of the processing order.
-  __device__ void seek(long long t) {
-    long long base = 0;
-    int gg = 0;
-    for (;; ++gg) {
-      const int L = NT - gg * R, Rgg = min(R, L);
-      const long long cnt = (long long)Rgg * (Rgg + 1) / 2 + (long long)(L - Rgg) * Rgg;
-      if (t < base + cnt) break;
-      base += cnt;
-    }
-    set_group(gg);
-    long long u = t - base;
-    const long long tri = (long long)Rg * (Rg + 1) / 2;  // strips of 1, 2, .., Rg tiles, then Rg each
-    if (u < tri) {
-      int c = 0;
-      while (u >= c + 1) {
-        u -= c + 1;
-        ++c;
-      }
-      J = I0 + c;
-      r = (int)u;
-    } else {
-      u -= tri;
-      J = I0 + Rg + (int)(u / Rg);
-      r = (int)(u % Rg);
-    }
-  }
-  __device__ int I() const { return I0 + r; }
-  // Advances; reports whether the tile just left closed its strip / its group.
-  __device__ void next(bool& strip_end, bool& group_end) {
-    strip_end = group_end = false;
-    if (++r < strip_len()) return;
-    strip_end = true;
-    r = 0;
-    if (++J < NT) return;
-    group_end = true;
-    set_group(g + 1);
-  }
-};
+// FP8 operand scale: g = 2^(7 - floor(log2 m)) puts m = max |value| in [128, 256)
+// (m = 0: g = 1); `inverse` returns 1 / g.  Exponents are clamped so that g and
+// 1 / g stay normal floats.
+__device__ __forceinline__ float ts8_pow2(unsigned mbits, bool inverse) {
+  if (mbits == 0u) return 1.f;
+  int e = (int)((mbits >> 23) & 0xffu) - 127;
+  e = max(-100, min(e, 120));
+  return __uint_as_float((uint32_t)(inverse ? 127 - 7 + e : 127 + 7 - e) << 23);
+}
 
-template <int N>
+template <int N, bool F8>
 __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
-  using C = TsCfg<N>;
+  using C = TsCfg<N, F8>;
   constexpr int R = C::R;
   if (*a.skip) return;  // uniform: written only by earlier launches
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -152,7 +115,9 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
   uint64_t* d2_empty = d2_full + 2;   // [2]
   uint64_t* d1_full = d2_empty + 2;
   uint64_t* d1_empty = d1_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(d1_empty + 1);
+  uint64_t* xj_full = d1_empty + 1;   // [2]
+  uint64_t* xj_empty = xj_full + 2;   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xj_empty + 2);
   __shared__ volatile int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -172,6 +137,10 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
     }
     mbar_init(d1_full, 1);
     mbar_init(d1_empty, 4);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&xj_full[s], 1);
+      mbar_init(&xj_empty[s], 1);
+    }
     failed = 0;
     fence_mbar_init();
   }
@@ -195,8 +164,8 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
     w.seek(t0);
     int st = 0, p = 0;
     uint32_t ph = 0;
-    long long it = 0;
-    bool group_start = true;
+    long long it = 0, kx = 0;  // tiles issued, strips started
+    bool group_start = true, strip_start = true;
     for (long long t = t0; t < t1 && !failed; ++t, ++it) {
       if (group_start) {  // X^T of the group's row tiles (one buffer: wait for the previous group)
         if (p >= 1 && !mbar_wait_bounded(xi_empty, (uint32_t)((p - 1) & 1), kWaitLimitNs)) {
@@ -204,17 +173,25 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
           break;
         }
         mbar_arrive_expect_tx(xi_full, (uint32_t)(w.Rg * C::XB));
-        bulk_g2s(smem + C::OFF_XI, a.xt + (long long)w.I0 * C::XB, (uint32_t)(w.Rg * C::XB), xi_full);
+        bulk_g2s(smem + C::OFF_XI, a.xc + (long long)w.I0 * C::XB, (uint32_t)(w.Rg * C::XB), xi_full);
         ++p;
+      }
+      if (strip_start) {  // X_J^T once per strip, two slots (wait for the strip two back)
+        const int xs = (int)(kx & 1);
+        if (kx >= 2 && !mbar_wait_bounded(&xj_empty[xs], (uint32_t)(((kx - 2) >> 1) & 1), kWaitLimitNs)) {
+          fail();
+          break;
+        }
+        mbar_arrive_expect_tx(&xj_full[xs], C::XB);
+        bulk_g2s(smem + C::OFF_XJ + xs * C::XB, a.xt + (long long)w.J * C::XB, C::XB, &xj_full[xs]);
+        ++kx;
       }
       if (it >= C::NSTAGE && !mbar_wait_bounded(&empty[st], ph ^ 1u, kWaitLimitNs)) {
         fail();
         break;
       }
-      uint8_t* stage = smem + st * C::STAGE;
       mbar_arrive_expect_tx(&full[st], C::STAGE);
-      bulk_g2s(stage, a.tiles + t * (long long)kTsTileBytes, kTsTileBytes, &full[st]);
-      bulk_g2s(stage + kTsTileBytes, a.xt + (long long)w.J * C::XB, C::XB, &full[st]);
+      bulk_g2s(smem + st * C::STAGE, a.tiles + t * (long long)C::TILE, C::TILE, &full[st]);
       if (++st == C::NSTAGE) {
         st = 0;
         ph ^= 1u;
@@ -222,11 +199,14 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       bool se, ge;
       w.next(se, ge);
       group_start = ge;
+      strip_start = se;
     }
     // Do not leave while copies into this CTA's shared memory may be in flight.
     const long long first = it > C::NSTAGE ? it - C::NSTAGE : 0;
     for (long long k = first; k < it; ++k)
       if (!mbar_wait_bounded(&full[k % C::NSTAGE], (uint32_t)((k / C::NSTAGE) & 1), kWaitLimitNs)) break;
+    for (long long k = kx > 2 ? kx - 2 : 0; k < kx; ++k)
+      mbar_wait_bounded(&xj_full[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
     if (p >= 1) mbar_wait_bounded(xi_full, (uint32_t)((p - 1) & 1), kWaitLimitNs);
   } else if (t0 < t1 && warp == 1 && lane == 0) {
     // ------------------------------------------------------------- MMA issue
@@ -247,8 +227,9 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
         }
         started = 0;
       }
-      const int db = (int)(k & 1);
-      if (strip_start && k >= 2 && !mbar_wait_bounded(&d2_empty[db], (uint32_t)(((k - 2) >> 1) & 1), kWaitLimitNs)) {
+      const int db = (int)(k & 1);  // D2 buffer and X_J^T slot of strip k
+      if (strip_start && ((k >= 2 && !mbar_wait_bounded(&d2_empty[db], (uint32_t)(((k - 2) >> 1) & 1), kWaitLimitNs)) ||
+                          !mbar_wait_bounded(&xj_full[db], (uint32_t)((k >> 1) & 1), kWaitLimitNs))) {
         fail();
         break;
       }
@@ -259,23 +240,44 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       tc_fence_after();
       const int r = w.r;
       const uint32_t sa = smem_u32(smem + st * C::STAGE);
-      const uint32_t sxj = sa + kTsTileBytes;
+      const uint32_t sxj = smem_u32(smem + C::OFF_XJ + db * C::XB);
       const uint32_t sxi = smem_u32(smem + C::OFF_XI + r * C::XB);
       const bool first1 = !(started >> r & 1u);
-      // D1[r] += A_IJ X_J: K = the tile's 128 columns, two 64-column halves of four K = 16 steps
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
+      if constexpr (F8) {
+        // D1[r] += A_IJ (X_J hi + X_J lo): K = the tile's 128 columns, four K = 32 steps
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          tc_mma(tm_d1 + (uint32_t)(r * N), sw128_desc(sa + s * 1024 + kk * 32, 16, 2048),
-                 sw128_desc(sxj + s * 1024 + kk * 32, 16, 2048), C::IDESC_ROW, (first1 && s == 0 && kk == 0) ? 0u : 1u);
-      started |= 1u << r;
-      // D2 += A_IJ^T X_I: K = the tile's 128 rows, eight K = 16 steps of two 8-row groups
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        tc_mma(tm_d2 + (uint32_t)(db * N), sw128_desc(sa + kk * 4096, 1024, 2048),
-               sw128_desc(sxi + (kk >> 2) * 1024 + (kk & 3) * 32, 16, 2048), C::IDESC_COL,
-               (strip_start && kk == 0) ? 0u : 1u);
+          for (int pl = 0; pl < 2; ++pl)
+            tc_mma8(tm_d1 + (uint32_t)(r * N), sw128_desc(sa + kk * 32, 16, 1024),
+                    sw128_desc(sxj + pl * N * 128 + kk * 32, 16, 1024), C::IDESC_ROW,
+                    (first1 && kk == 0 && pl == 0) ? 0u : 1u);
+        started |= 1u << r;
+        // D2 += A_IJ^T (s X_I hi + lo): K = the tile's 128 rows, four K = 32 steps of four 8-row groups
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int pl = 0; pl < 2; ++pl)
+            tc_mma8(tm_d2 + (uint32_t)(db * N), sw128_desc(sa + kk * 4096, 1024, 1024),
+                    sw128_desc(sxi + pl * N * 128 + kk * 32, 16, 1024), C::IDESC_COL,
+                    (strip_start && kk == 0 && pl == 0) ? 0u : 1u);
+      } else {
+        // D1[r] += A_IJ X_J: K = the tile's 128 columns, two 64-column halves of four K = 16 steps
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc_mma(tm_d1 + (uint32_t)(r * N), sw128_desc(sa + s * 1024 + kk * 32, 16, 2048),
+                   sw128_desc(sxj + s * 1024 + kk * 32, 16, 2048), C::IDESC_ROW,
+                   (first1 && s == 0 && kk == 0) ? 0u : 1u);
+        started |= 1u << r;
+        // D2 += A_IJ^T X_I: K = the tile's 128 rows, eight K = 16 steps of two 8-row groups
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          tc_mma(tm_d2 + (uint32_t)(db * N), sw128_desc(sa + kk * 4096, 1024, 2048),
+                 sw128_desc(sxi + (kk >> 2) * 1024 + (kk & 3) * 32, 16, 2048), C::IDESC_COL,
+                 (strip_start && kk == 0) ? 0u : 1u);
+      }
       tc_commit(&empty[st]);
       if (++st == C::NSTAGE) {
         st = 0;
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       const bool last = (t + 1 == t1);
       if (se || last) {
         tc_commit(&d2_full[db]);
+        tc_commit(&xj_empty[db]);
         ++k;
       }
       if (ge || last) {
@@ -305,7 +308,13 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
     int p = 0;
     long long k = 0;
     uint32_t used = 0;  // D1 slots written in this group segment
-    auto drain = [&](uint32_t taddr, int row) -> bool {  // TMEM rows 32q.. -> Y rows row.., then release
+    // FP8: the row product is scaled by s_i / g_r per output row, the column product by 1 / g_c
+    float inv_gr = 1.f, inv_gc = 1.f;
+    if constexpr (F8) {
+      inv_gr = ts8_pow2(a.ctl->ts8_max[0], true);
+      inv_gc = ts8_pow2(a.ctl->ts8_max[1], true);
+    }
+    auto drain = [&](uint32_t taddr, int row, bool row_product) -> bool {  // TMEM rows 32q.. -> Y rows row..
       float v[N];
 #pragma unroll
       for (int c0 = 0; c0 < N; c0 += 16) {
@@ -316,6 +325,11 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       }
       tc_wait_ld();
       if (row < a.rows) {
+        if constexpr (F8) {
+          const float m = row_product ? a.rscale[row / N] * inv_gr : inv_gc;
+#pragma unroll
+          for (int c = 0; c < N; ++c) v[c] *= m;
+        }
         float* y = a.Y + (long long)row * N;
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 4) red_add_v4_f32(y + c0, v[c0], v[c0 + 1], v[c0 + 2], v[c0 + 3]);
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
           break;
         }
         tc_fence_after();
-        drain(tm_d2 + (uint32_t)(db * N), J * kTsTile + 32 * q + lane);
+        drain(tm_d2 + (uint32_t)(db * N), J * kTsTile + 32 * q + lane, false);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&d2_empty[db]);
@@ -348,7 +362,7 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
         }
         tc_fence_after();
         for (int r = 0; r < R; ++r)
-          if (used >> r & 1u) drain(tm_d1 + (uint32_t)(r * N), (I0 + r) * kTsTile + 32 * q + lane);
+          if (used >> r & 1u) drain(tm_d1 + (uint32_t)(r * N), (I0 + r) * kTsTile + 32 * q + lane, true);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(d1_empty);
@@ -366,12 +380,15 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
 }
 
 // ------------------------------------------------------------ packing
-// One CTA per tile (grid-stride): tile number t of the processing order, 2048
-// 16-byte chunks of 8 consecutive columns.
-template <int R, class Src>
-__global__ void __launch_bounds__(256) ts_pack_kernel(Src src, int NT, uint8_t* out) {
+// One CTA per tile (grid-stride): tile number t of the processing order, in
+// 16-byte chunks (8 bfloat16 or 16 E4M3 consecutive columns of a row).
+// FP8: element (R, C) is stored as RN(A_RC / s_{R / d}), saturated to +-448.
+template <int R, bool F8, class Src>
+__global__ void __launch_bounds__(256) ts_pack_kernel(Src src, int NT, int rows, int d, const float* scale,
+                                                     uint8_t* out) {
   __shared__ int ij[2];
   const long long total = ts_tiles(NT);
+  constexpr int TILE = F8 ? kTs8TileBytes : kTsTileBytes;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -383,18 +400,35 @@ __global__ void __launch_bounds__(256) ts_pack_kernel(Src src, int NT, uint8_t* 
     }
     __syncthreads();
     const int I = ij[0], J = ij[1];
-    uint8_t* tile = out + t * (long long)kTsTileBytes;
-    for (int ch = threadIdx.x; ch < kTsTile * kTsTile / 8; ch += blockDim.x) {
-      const int r = ch >> 4, c = (ch & 15) * 8;
-      const long long R = (long long)I * kTsTile + r, Cc = (long long)J * kTsTile + c;
+    uint8_t* tile = out + t * (long long)TILE;
+    for (int ch = threadIdx.x; ch < TILE / 16; ch += blockDim.x) {
       uint32_t w[4];
+      int off;
+      if constexpr (F8) {
+        const int r = ch >> 3, c = (ch & 7) * 16;
+        const long long Rr = (long long)I * kTsTile + r, Cc = (long long)J * kTsTile + c;
+        const float s = Rr < rows ? scale[Rr / d] : 1.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const __nv_bfloat16 lo = __float2bfloat16_rn(src(R, Cc + 2 * k));
-        const __nv_bfloat16 hi = __float2bfloat16_rn(src(R, Cc + 2 * k + 1));
-        w[k] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        for (int k = 0; k < 4; ++k) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            v |= (uint32_t)__nv_cvt_float_to_fp8(src(Rr, Cc + 4 * k + e) / s, __NV_SATFINITE, __NV_E4M3) << (8 * e);
+          w[k] = v;
+        }
+        off = ts8_swz(r, c);
+      } else {
+        const int r = ch >> 4, c = (ch & 15) * 8;
+        const long long Rr = (long long)I * kTsTile + r, Cc = (long long)J * kTsTile + c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const __nv_bfloat16 lo = __float2bfloat16_rn(src(Rr, Cc + 2 * k));
+          const __nv_bfloat16 hi = __float2bfloat16_rn(src(Rr, Cc + 2 * k + 1));
+          w[k] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        off = ts_swz(r, c);
       }
-      *reinterpret_cast<uint4*>(tile + ts_swz(r, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -422,64 +456,160 @@ __global__ void __launch_bounds__(256) ts_xt_kernel(const float* __restrict__ X,
   }
 }
 
+// FP8 operands, pass 1: mx[0] = max |X|, mx[1] = max |s_i X_i| (float bits; zero on entry).
+__global__ void __launch_bounds__(256) ts8_xmax_kernel(const float* __restrict__ X, const float* __restrict__ scale,
+                                                      int rows, int D, unsigned* mx, const int* skip) {
+  if (*skip) return;
+  float m0 = 0.f, m1 = 0.f;
+  const long long count = (long long)rows * D;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float x = X[e];
+    m0 = fmaxf(m0, fabsf(x));
+    m1 = fmaxf(m1, fabsf(x * scale[e / D / D]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[0], __float_as_uint(m0));
+    atomicMax(&mx[1], __float_as_uint(m1));
+  }
+}
+
+__device__ __forceinline__ void ts8_split(float v, uint32_t& hi, uint32_t& lo, int sh) {
+  const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  const __half_raw hr = __nv_cvt_fp8_to_halfraw(h, __NV_E4M3);
+  const float r = v - __half2float(__half(hr));  // exact: hi is v to 4 significant bits
+  hi |= (uint32_t)h << sh;
+  lo |= (uint32_t)__nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3) << sh;
+}
+
+// FP8 operands, pass 2: per 128-row tile J, the row operand (g_r X) and the
+// column operand (g_c s_i X_i) as hi and lo E4M3 planes of N x 128 bytes each
+// (element (n, k) = row 128 J + k, column n; zero past n*d rows).
+__global__ void __launch_bounds__(256) ts8_xt_kernel(const float* __restrict__ X, const float* __restrict__ scale,
+                                                    uint8_t* __restrict__ xt, uint8_t* __restrict__ xc, int rows,
+                                                    int D, int NT, const unsigned* mx, const int* skip) {
+  if (*skip) return;
+  const float gr = ts8_pow2(mx[0], false), gc = ts8_pow2(mx[1], false);
+  const long long chunks = (long long)NT * 8 * D;  // (tile, 16-row chunk, column), column fastest
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < chunks;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nn = (int)(e % D);
+    const long long tk = e / D;
+    const int J = (int)(tk >> 3), k0 = (int)(tk & 7) * 16;
+    uint32_t rh[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0}, cl[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const long long row = (long long)J * kTsTile + k0 + k;
+      float x = 0.f, sx = 0.f;
+      if (row < rows) {
+        x = X[row * D + nn];
+        sx = x * scale[row / D];
+      }
+      ts8_split(x * gr, rh[k >> 2], rl[k >> 2], 8 * (k & 3));
+      ts8_split(sx * gc, ch[k >> 2], cl[k >> 2], 8 * (k & 3));
+    }
+    const long long base = (long long)J * D * 256;
+    const int o = ts8_swz(nn, k0);
+    *reinterpret_cast<uint4*>(xt + base + o) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<uint4*>(xt + base + D * 128 + o) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<uint4*>(xc + base + o) = make_uint4(ch[0], ch[1], ch[2], ch[3]);
+    *reinterpret_cast<uint4*>(xc + base + D * 128 + o) = make_uint4(cl[0], cl[1], cl[2], cl[3]);
+  }
+}
+
 // ---------------------------------------------------------------- host
 bool tc_sym_supported(int d) { return d == 16 || d == 32 || d == 64; }
 
 long long tc_sym_bytes(int n, int d) { return ts_tiles(ts_tile_rows(n, d)) * (long long)kTsTileBytes; }
 
-// Bytes of the swizzled X^T tiles for (n, d).
-long long tc_sym_xt_bytes(int n, int d) { return (long long)ts_tile_rows(n, d) * d * 256; }
+// FP8 tiles plus the n block-row scales.
+long long tc_sym8_scale_offset(int n, int d) { return ts8_scale_offset(n, d); }
+long long tc_sym8_bytes(int n, int d) { return ts8_scale_offset(n, d) + ((long long)n * 4 + 15) / 16 * 16; }
 
-template <int N>
+// Bytes of the swizzled X^T tiles for (n, d): bfloat16 one set, FP8 two (row and column operands).
+long long tc_sym_xt_bytes(int n, int d) { return (long long)ts_tile_rows(n, d) * d * 256; }
+long long tc_sym8_xt_bytes(int n, int d) { return 2 * tc_sym_xt_bytes(n, d); }
+
+template <int N, bool F8>
 static cudaError_t launch_ts(const TsArgs& a, cudaStream_t st, bool prepare) {
-  using C = TsCfg<N>;
-  if (prepare) return cudaFuncSetAttribute(tc_sym_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  using C = TsCfg<N, F8>;
+  if (prepare) return cudaFuncSetAttribute(tc_sym_kernel<N, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   const long long total = ts_tiles(a.NT);
   const int grid = (int)std::min<long long>(total, num_sms());
-  tc_sym_kernel<N><<<grid, 192, C::SMEM, st>>>(a);
+  tc_sym_kernel<N, F8><<<grid, 192, C::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_ts_any(int d, const TsArgs& a, cudaStream_t st, bool prepare) {
+static cudaError_t launch_ts_any(int d, bool f8, const TsArgs& a, cudaStream_t st, bool prepare) {
   switch (d) {
-    case 16: return launch_ts<16>(a, st, prepare);
-    case 32: return launch_ts<32>(a, st, prepare);
-    case 64: return launch_ts<64>(a, st, prepare);
+    case 16: return f8 ? launch_ts<16, true>(a, st, prepare) : launch_ts<16, false>(a, st, prepare);
+    case 32: return f8 ? launch_ts<32, true>(a, st, prepare) : launch_ts<32, false>(a, st, prepare);
+    case 64: return f8 ? launch_ts<64, true>(a, st, prepare) : launch_ts<64, false>(a, st, prepare);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_sym_prepare(int d) {
+cudaError_t tc_sym_prepare(int d, bool f8) {
   TsArgs a{};
-  return launch_ts_any(d, a, 0, true);
+  return launch_ts_any(d, f8, a, 0, true);
 }
 
-cudaError_t tc_sym_product(const void* packed, int n, int d, const float* X, uint8_t* xt, float* Y, Ctl* ctl,
-                           const int* skip, cudaStream_t st) {
+cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const float* X, uint8_t* xt, float* Y,
+                           Ctl* ctl, const int* skip, cudaStream_t st) {
   const int NT = ts_tile_rows(n, d);
-  const long long chunks = (long long)NT * d * (kTsTile / 8);
-  const int g = (int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms());
-  ts_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, d, NT, skip);
-  cudaError_t e = cudaGetLastError();
+  const uint8_t* tiles = reinterpret_cast<const uint8_t*>(packed);
+  if (!f8) {
+    const long long chunks = (long long)NT * d * (kTsTile / 8);
+    const int g = (int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms());
+    ts_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, d, NT, skip);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TsArgs a{tiles, xt, xt, nullptr, Y, skip, ctl, n * d, NT};
+    return launch_ts_any(d, false, a, st, false);
+  }
+  const float* scale = reinterpret_cast<const float*>(tiles + ts8_scale_offset(n, d));
+  uint8_t* xc = xt + tc_sym_xt_bytes(n, d);
+  cudaError_t e = cudaMemsetAsync(ctl->ts8_max, 0, sizeof(ctl->ts8_max), st);
   if (e != cudaSuccess) return e;
-  TsArgs a{reinterpret_cast<const uint8_t*>(packed), xt, Y, skip, ctl, n * d, NT};
-  return launch_ts_any(d, a, st, false);
+  const long long count = (long long)n * d * d;
+  ts8_xmax_kernel<<<(int)std::min<long long>((count + 255) / 256, 2LL * num_sms()), 256, 0, st>>>(
+      X, scale, n * d, d, ctl->ts8_max, skip);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long chunks = (long long)NT * 8 * d;
+  ts8_xt_kernel<<<(int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms()), 256, 0, st>>>(
+      X, scale, xt, xc, n * d, d, NT, ctl->ts8_max, skip);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  TsArgs a{tiles, xt, xc, scale, Y, skip, ctl, n * d, NT};
+  return launch_ts_any(d, true, a, st, false);
 }
 
+// FP8: the caller has written the block-row scales at ts8_scale_offset(n, d).
 template <class Src>
-cudaError_t tc_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st) {
+cudaError_t tc_sym_pack(Src src, int n, int d, bool f8, void* packed, cudaStream_t st) {
   const int NT = ts_tile_rows(n, d);
   const int g = (int)std::min<long long>(ts_tiles(NT), 8LL * num_sms());
   uint8_t* out = reinterpret_cast<uint8_t*>(packed);
+  const float* scale = reinterpret_cast<const float*>(out + ts8_scale_offset(n, d));
+  const int rows = n * d;
+#define NSRGS_TS_PACK(DD)                                                                        \
+  if (f8)                                                                                        \
+    ts_pack_kernel<ts_strip_rows(DD), true><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);   \
+  else                                                                                           \
+    ts_pack_kernel<ts_strip_rows(DD), false><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);
   switch (d) {
-    case 16: ts_pack_kernel<TsCfg<16>::R><<<g, 256, 0, st>>>(src, NT, out); break;
-    case 32: ts_pack_kernel<TsCfg<32>::R><<<g, 256, 0, st>>>(src, NT, out); break;
-    case 64: ts_pack_kernel<TsCfg<64>::R><<<g, 256, 0, st>>>(src, NT, out); break;
+    case 16: NSRGS_TS_PACK(16) break;
+    case 32: NSRGS_TS_PACK(32) break;
+    case 64: NSRGS_TS_PACK(64) break;
     default: return cudaErrorInvalidValue;
   }
+#undef NSRGS_TS_PACK
   return cudaGetLastError();
 }
-template cudaError_t tc_sym_pack<UpperSrc>(UpperSrc, int, int, void*, cudaStream_t);
-template cudaError_t tc_sym_pack<DenseSrc>(DenseSrc, int, int, void*, cudaStream_t);
+template cudaError_t tc_sym_pack<UpperSrc>(UpperSrc, int, int, bool, void*, cudaStream_t);
+template cudaError_t tc_sym_pack<DenseSrc>(DenseSrc, int, int, bool, void*, cudaStream_t);
 
 }  // namespace nsrgs

@@ -40,12 +40,13 @@ def test_every_declared_symbol_is_exported(L):
 def test_version_and_sizes(L):
     assert "sm_103a" in L.nsrgs_version()
     # symmetric layouts: F32 any d <= 64 (panels up to 8, float32 tiles above), BF16 d <= 8
-    # and d in {16, 32, 64}, FP8 d <= 4; the dense layout any d <= 64
+    # and d in {16, 32, 64}, FP8 d <= 4 and d in {16, 32, 64}; the dense layout any d <= 64
     assert L.nsrgs_packed_bytes(200, 3, L.F32) > 0
     assert L.nsrgs_packed_bytes(200, 8, L.F32) > 0 and L.nsrgs_packed_bytes(200, 5, L.BF16) > 0
     assert L.nsrgs_packed_bytes(200, 9, L.F32) > 0 and L.nsrgs_packed_bytes(200, 64, L.F32) > 0
     assert L.nsrgs_packed_bytes(200, 65, L.F32) == 0 and L.nsrgs_packed_bytes(200, 9, L.BF16) == 0
-    assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0
+    assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0 and L.nsrgs_packed_bytes(200, 8, L.FP8E4M3) == 0
+    assert L.nsrgs_packed_bytes(200, 16, L.FP8E4M3) * 2 < L.nsrgs_packed_bytes(200, 16, L.BF16) + 4096
     # block-sparse rows: the bound for fully observed data, both triangles, d <= 8
     assert L.nsrgs_packed_bytes(200, 3, L.BCSR_F32) >= 200 * 199 * 9 * 4
     assert L.nsrgs_packed_bytes(200, 3, L.BCSR_BF16) >= 200 * 199 * 9 * 2
