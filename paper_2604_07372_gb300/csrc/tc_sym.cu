@@ -26,7 +26,7 @@
 // uses the rows s_i X_i (scale g_c, result times 1 / g_c): the block-row scale
 // runs along K there, so it is folded into the operand instead of the result.
 //
-// Per CTA (6 warps, persistent over a contiguous range of the processing order):
+// Per CTA (7 warps, persistent over a contiguous range of the processing order):
 // tiles are visited in column strips of R row tiles (a group of R row panels,
 // columns J = I0 .. NT-1, rows I0 .. I0+R-1 in each column), so the column
 // product accumulates over a whole strip (K = up to 128 R rows) before it is
@@ -37,9 +37,15 @@
 //                   and of the group's R X_I^T tiles into one buffer when a group
 //                   starts; mbarrier expect_tx.
 //   warp 1        : allocates TMEM (D1: R slots of N columns, D2: two buffers of
-//                   N columns); lane 0 issues tcgen05.mma (D1[r] += A X_J over
-//                   the tile's columns, D2 += A^T X_I over its rows) and commits
-//                   the stage, D2 at a strip's end and D1 at a group's end.
+//                   N columns); lane 0 issues the row product's tcgen05.mma
+//                   (D1[r] += A X_J over the tile's columns), commits the stage
+//                   and, at a group's end, D1.
+//   warp 6 lane 0 : issues the column product's tcgen05.mma (D2 += A^T X_I over
+//                   the tile's rows), commits the stage and, at a strip's end, D2.
+//                   A stage is free once both issuers committed it.  With one
+//                   thread issuing both products a tile took about 2000 cycles of
+//                   that thread (the issue itself, not the tensor pipe, bound the
+//                   stream); descriptors are base + constant offsets.
 //   warps 2..5    : epilogue.  tcgen05.ld of their 32-lane quarter of D2 (rows =
 //                   the strip's columns) and of the used D1 slots, then
 //                   red.global.add.v4.f32 into Y.
@@ -51,6 +57,9 @@
 #include "tc_sym.cuh"
 
 namespace nsrgs {
+
+// Threads per CTA: producer, row-product MMA issue, 4 epilogue warps, column-product MMA issue.
+constexpr int kTsThreads = 224;
 
 template <int N, bool F8>
 struct TsCfg {
@@ -100,8 +109,13 @@ __device__ __forceinline__ float ts8_pow2(unsigned mbits, bool inverse) {
   return __uint_as_float((uint32_t)(inverse ? 127 - 7 + e : 127 + 7 - e) << 23);
 }
 
+// Shared-memory descriptor of (base + off): the start address sits in the low
+// 14 bits as address / 16 and every operand lies below 256 KB, so offsets add
+// to a base descriptor without a carry.
+__device__ __forceinline__ uint64_t desc_at(uint64_t base, uint32_t off) { return base + (uint64_t)(off >> 4); }
+
 template <int N, bool F8>
-__global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
+__global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
   using C = TsCfg<N, F8>;
   constexpr int R = C::R;
   if (*a.skip) return;  // uniform: written only by earlier launches
@@ -127,20 +141,18 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::NSTAGE; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], 2);  // released by both MMA issuers
     }
     mbar_init(xi_full, 1);
     mbar_init(xi_empty, 1);
     for (int s = 0; s < 2; ++s) {
       mbar_init(&d2_full[s], 1);
       mbar_init(&d2_empty[s], 4);
-    }
-    mbar_init(d1_full, 1);
-    mbar_init(d1_empty, 4);
-    for (int s = 0; s < 2; ++s) {
       mbar_init(&xj_full[s], 1);
       mbar_init(&xj_empty[s], 1);
     }
+    mbar_init(d1_full, 1);
+    mbar_init(d1_empty, 4);
     failed = 0;
     fence_mbar_init();
   }
@@ -156,6 +168,12 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
     atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
     failed = 1;
   };
+
+  // Descriptor bases: A K-major (row product), A MN-major (column product), X^T
+  // operands (K-major).  Rows of 128 bytes; 8-row groups 1024 (FP8) or 2048
+  // (bfloat16, two 64-column halves 1024 apart) bytes apart.
+  constexpr uint32_t GRP = F8 ? 1024 : 2048;
+  const uint32_t s0 = smem_u32(smem);
 
   if (t0 < t1 && warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
@@ -209,27 +227,27 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       mbar_wait_bounded(&xj_full[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
     if (p >= 1) mbar_wait_bounded(xi_full, (uint32_t)((p - 1) & 1), kWaitLimitNs);
   } else if (t0 < t1 && warp == 1 && lane == 0) {
-    // ------------------------------------------------------------- MMA issue
+    // ------------------------------------------------ row-product MMA issue
+    // D1[r] += A_IJ X_J for the tile's row r of the group; X_J^T per strip.
+    const uint64_t dA = sw128_desc(s0, 16, GRP), dX = sw128_desc(s0 + C::OFF_XJ, 16, GRP);
     TsWalk<R> w;
     w.NT = a.NT;
     w.seek(t0);
     int st = 0, p = 0;
     uint32_t ph = 0;
-    long long k = 0;       // strips started
+    long long k = 0;  // strips started
     bool group_start = true, strip_start = true;
     uint32_t started = 0;  // D1 slots written in this group segment
     for (long long t = t0; t < t1 && !failed; ++t) {
       if (group_start) {
-        if (!mbar_wait_bounded(xi_full, (uint32_t)(p & 1), kWaitLimitNs) ||
-            (p >= 1 && !mbar_wait_bounded(d1_empty, (uint32_t)((p - 1) & 1), kWaitLimitNs))) {
+        if (p >= 1 && !mbar_wait_bounded(d1_empty, (uint32_t)((p - 1) & 1), kWaitLimitNs)) {
           fail();
           break;
         }
         started = 0;
       }
-      const int db = (int)(k & 1);  // D2 buffer and X_J^T slot of strip k
-      if (strip_start && ((k >= 2 && !mbar_wait_bounded(&d2_empty[db], (uint32_t)(((k - 2) >> 1) & 1), kWaitLimitNs)) ||
-                          !mbar_wait_bounded(&xj_full[db], (uint32_t)((k >> 1) & 1), kWaitLimitNs))) {
+      const int xs = (int)(k & 1);
+      if (strip_start && !mbar_wait_bounded(&xj_full[xs], (uint32_t)((k >> 1) & 1), kWaitLimitNs)) {
         fail();
         break;
       }
@@ -239,44 +257,89 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       }
       tc_fence_after();
       const int r = w.r;
-      const uint32_t sa = smem_u32(smem + st * C::STAGE);
-      const uint32_t sxj = smem_u32(smem + C::OFF_XJ + db * C::XB);
-      const uint32_t sxi = smem_u32(smem + C::OFF_XI + r * C::XB);
-      const bool first1 = !(started >> r & 1u);
+      const uint32_t d = tm_d1 + (uint32_t)(r * N);
+      const uint64_t a0 = desc_at(dA, (uint32_t)(st * C::STAGE)), x0 = desc_at(dX, (uint32_t)(xs * C::XB));
+      const uint32_t acc0 = (started >> r & 1u);
       if constexpr (F8) {
-        // D1[r] += A_IJ (X_J hi + X_J lo): K = the tile's 128 columns, four K = 32 steps
+        // K = the tile's 128 columns: four K = 32 steps, hi and lo planes of X_J
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
           for (int pl = 0; pl < 2; ++pl)
-            tc_mma8(tm_d1 + (uint32_t)(r * N), sw128_desc(sa + kk * 32, 16, 1024),
-                    sw128_desc(sxj + pl * N * 128 + kk * 32, 16, 1024), C::IDESC_ROW,
-                    (first1 && kk == 0 && pl == 0) ? 0u : 1u);
-        started |= 1u << r;
-        // D2 += A_IJ^T (s X_I hi + lo): K = the tile's 128 rows, four K = 32 steps of four 8-row groups
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-          for (int pl = 0; pl < 2; ++pl)
-            tc_mma8(tm_d2 + (uint32_t)(db * N), sw128_desc(sa + kk * 4096, 1024, 1024),
-                    sw128_desc(sxi + pl * N * 128 + kk * 32, 16, 1024), C::IDESC_COL,
-                    (strip_start && kk == 0 && pl == 0) ? 0u : 1u);
+            tc_mma8(d, desc_at(a0, kk * 32), desc_at(x0, pl * N * 128 + kk * 32), C::IDESC_ROW,
+                    (kk == 0 && pl == 0) ? acc0 : 1u);
       } else {
-        // D1[r] += A_IJ X_J: K = the tile's 128 columns, two 64-column halves of four K = 16 steps
+        // K = the tile's 128 columns: two 64-column halves of four K = 16 steps
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            tc_mma(tm_d1 + (uint32_t)(r * N), sw128_desc(sa + s * 1024 + kk * 32, 16, 2048),
-                   sw128_desc(sxj + s * 1024 + kk * 32, 16, 2048), C::IDESC_ROW,
-                   (first1 && s == 0 && kk == 0) ? 0u : 1u);
-        started |= 1u << r;
-        // D2 += A_IJ^T X_I: K = the tile's 128 rows, eight K = 16 steps of two 8-row groups
+            tc_mma(d, desc_at(a0, h * 1024 + kk * 32), desc_at(x0, h * 1024 + kk * 32), C::IDESC_ROW,
+                   (h == 0 && kk == 0) ? acc0 : 1u);
+      }
+      started |= 1u << r;
+      tc_commit(&empty[st]);
+      if (++st == C::NSTAGE) {
+        st = 0;
+        ph ^= 1u;
+      }
+      bool se, ge;
+      w.next(se, ge);
+      const bool last = (t + 1 == t1);
+      if (se || last) {
+        tc_commit(&xj_empty[xs]);
+        ++k;
+      }
+      if (ge || last) {
+        tc_commit(d1_full);
+        ++p;
+      }
+      strip_start = se;
+      group_start = ge;
+    }
+  } else if (t0 < t1 && warp == kTsThreads / 32 - 1 && lane == 0) {
+    // --------------------------------------------- column-product MMA issue
+    // D2 += A_IJ^T X_I over the strip's rows (the same tile read MN-major).
+    const uint64_t dA = sw128_desc(s0, 1024, GRP), dX = sw128_desc(s0 + C::OFF_XI, 16, GRP);
+    TsWalk<R> w;
+    w.NT = a.NT;
+    w.seek(t0);
+    int st = 0, p = 0;
+    uint32_t ph = 0;
+    long long k = 0;  // strips started
+    bool group_start = true, strip_start = true;
+    for (long long t = t0; t < t1 && !failed; ++t) {
+      if (group_start && !mbar_wait_bounded(xi_full, (uint32_t)(p & 1), kWaitLimitNs)) {
+        fail();
+        break;
+      }
+      const int db = (int)(k & 1);
+      if (strip_start && k >= 2 && !mbar_wait_bounded(&d2_empty[db], (uint32_t)(((k - 2) >> 1) & 1), kWaitLimitNs)) {
+        fail();
+        break;
+      }
+      if (!mbar_wait_bounded(&full[st], ph, kWaitLimitNs)) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tm_d2 + (uint32_t)(db * N);
+      const uint64_t a0 = desc_at(dA, (uint32_t)(st * C::STAGE)), x0 = desc_at(dX, (uint32_t)(w.r * C::XB));
+      const uint32_t acc0 = strip_start ? 0u : 1u;
+      if constexpr (F8) {
+        // K = the tile's 128 rows: four K = 32 steps of four 8-row groups, hi and lo planes
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int pl = 0; pl < 2; ++pl)
+            tc_mma8(d, desc_at(a0, kk * 4096), desc_at(x0, pl * N * 128 + kk * 32), C::IDESC_COL,
+                    (kk == 0 && pl == 0) ? acc0 : 1u);
+      } else {
+        // K = the tile's 128 rows: eight K = 16 steps of two 8-row groups
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          tc_mma(tm_d2 + (uint32_t)(db * N), sw128_desc(sa + kk * 4096, 1024, 2048),
-                 sw128_desc(sxi + (kk >> 2) * 1024 + (kk & 3) * 32, 16, 2048), C::IDESC_COL,
-                 (strip_start && kk == 0) ? 0u : 1u);
+          tc_mma(d, desc_at(a0, kk * 4096), desc_at(x0, (kk >> 2) * 1024 + (kk & 3) * 32), C::IDESC_COL,
+                 kk == 0 ? acc0 : 1u);
       }
       tc_commit(&empty[st]);
       if (++st == C::NSTAGE) {
@@ -288,18 +351,16 @@ __global__ void __launch_bounds__(192, 1) tc_sym_kernel(const TsArgs a) {
       const bool last = (t + 1 == t1);
       if (se || last) {
         tc_commit(&d2_full[db]);
-        tc_commit(&xj_empty[db]);
         ++k;
       }
       if (ge || last) {
-        tc_commit(d1_full);
         tc_commit(xi_empty);
         ++p;
       }
       strip_start = se;
       group_start = ge;
     }
-  } else if (t0 < t1 && warp >= 2) {
+  } else if (t0 < t1 && warp >= 2 && warp < 6) {
     // -------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lanes 32q .. 32q+31
     TsWalk<R> w;
@@ -540,7 +601,7 @@ static cudaError_t launch_ts(const TsArgs& a, cudaStream_t st, bool prepare) {
   if (prepare) return cudaFuncSetAttribute(tc_sym_kernel<N, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   const long long total = ts_tiles(a.NT);
   const int grid = (int)std::min<long long>(total, num_sms());
-  tc_sym_kernel<N, F8><<<grid, 192, C::SMEM, st>>>(a);
+  tc_sym_kernel<N, F8><<<grid, kTsThreads, C::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
