@@ -338,8 +338,9 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
                                             o, ctl);
   } else if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) {
     const uint8_t* p = reinterpret_cast<const uint8_t*>(packed);
-    if (d == 64) norm2_ts8_kernel<ts_strip_rows(64)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
-    else norm2_ts8_kernel<ts_strip_rows(16)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    if (d == 64) norm2_ts8_kernel<ts_strip_rows(64, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    else if (d == 32) norm2_ts8_kernel<ts_strip_rows(32, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    else norm2_ts8_kernel<ts_strip_rows(16, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
   } else if (storage == NSRGS_F32 && fs_sym_supported(d)) {
     // float32 tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(packed), fs_sym_bytes(n, d) / 4, 2.0, o,

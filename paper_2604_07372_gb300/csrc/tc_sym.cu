@@ -64,7 +64,12 @@ constexpr int kTsThreads = 224;
 template <int N, bool F8>
 struct TsCfg {
   static constexpr int TILE = F8 ? kTs8TileBytes : kTsTileBytes;
-  static constexpr int R = ts_strip_rows(N);             // row tiles per strip
+  static constexpr int R = ts_strip_rows(N, F8);         // row tiles per strip
+  // FP8 at N <= 32: one MMA multiplies both X planes (B = the 2N rows hi, lo), the
+  // two halves of the accumulator summed in the epilogue; at N = 64 the planes
+  // take one MMA each into the same columns (TMEM holds no 2N-wide slots there).
+  static constexpr bool MERGE = F8 && N <= 32;
+  static constexpr int NACC = MERGE ? 2 * N : N;         // accumulator columns per slot
   static constexpr int XB = N * 256;                      // one X^T tile (FP8: hi and lo planes)
   static constexpr int STAGE = TILE;                      // the ring holds A tiles only
   static constexpr int SMEM_MAX = 227 * 1024;
@@ -76,11 +81,11 @@ struct TsCfg {
   static constexpr int OFF_BARS = OFF_XI + R * XB;
   static constexpr int NBARS = 2 * NSTAGE + 2 + 4 + 2 + 4;
   static constexpr int SMEM = 1024 + OFF_BARS + NBARS * 8 + 16;
-  static constexpr int TMEM_NEED = (R + 2) * N;          // D1: R slots, D2: two buffers
+  static constexpr int TMEM_NEED = (R + 2) * NACC;       // D1: R slots, D2: two buffers
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : (TMEM_NEED <= 128 ? 128 : (TMEM_NEED <= 256 ? 256 : 512));
   // D1 += A X_J and D2 += A^T X_I (A read MN-major)
-  static constexpr uint32_t IDESC_ROW = F8 ? tc8_idesc(128, N, false) : tc_idesc(128, N, false);
-  static constexpr uint32_t IDESC_COL = F8 ? tc8_idesc(128, N, true) : tc_idesc(128, N, true);
+  static constexpr uint32_t IDESC_ROW = F8 ? tc8_idesc(128, NACC, false) : tc_idesc(128, N, false);
+  static constexpr uint32_t IDESC_COL = F8 ? tc8_idesc(128, NACC, true) : tc_idesc(128, N, true);
   static_assert(STAGE % 1024 == 0 && XB % 1024 == 0 && (N * 128) % 1024 == 0, "1024-byte swizzle alignment");
   static_assert(NSTAGE >= 3, "pipeline depth");
   static_assert(SMEM <= SMEM_MAX, "shared memory");
@@ -161,8 +166,8 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tm_d1 = tmem;                      // + r * N
-  const uint32_t tm_d2 = tmem + (uint32_t)(R * N);  // + db * N
+  const uint32_t tm_d1 = tmem;                         // + r * NACC
+  const uint32_t tm_d2 = tmem + (uint32_t)(R * C::NACC);  // + db * NACC
 
   auto fail = [&]() {
     atomicOr(&a.ctl->flags, FLAG_TIMEOUT);
@@ -257,10 +262,15 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
       }
       tc_fence_after();
       const int r = w.r;
-      const uint32_t d = tm_d1 + (uint32_t)(r * N);
+      const uint32_t d = tm_d1 + (uint32_t)(r * C::NACC);
       const uint64_t a0 = desc_at(dA, (uint32_t)(st * C::STAGE)), x0 = desc_at(dX, (uint32_t)(xs * C::XB));
       const uint32_t acc0 = (started >> r & 1u);
-      if constexpr (F8) {
+      if constexpr (C::MERGE) {
+        // K = the tile's 128 columns: four K = 32 steps, B = X_J's hi and lo planes (2N rows)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma8(d, desc_at(a0, kk * 32), desc_at(x0, kk * 32), C::IDESC_ROW, kk == 0 ? acc0 : 1u);
+      } else if constexpr (F8) {
         // K = the tile's 128 columns: four K = 32 steps, hi and lo planes of X_J
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
@@ -323,10 +333,15 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
         break;
       }
       tc_fence_after();
-      const uint32_t d = tm_d2 + (uint32_t)(db * N);
+      const uint32_t d = tm_d2 + (uint32_t)(db * C::NACC);
       const uint64_t a0 = desc_at(dA, (uint32_t)(st * C::STAGE)), x0 = desc_at(dX, (uint32_t)(w.r * C::XB));
       const uint32_t acc0 = strip_start ? 0u : 1u;
-      if constexpr (F8) {
+      if constexpr (C::MERGE) {
+        // K = the tile's 128 rows: four K = 32 steps of four 8-row groups, B = hi and lo planes
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma8(d, desc_at(a0, kk * 4096), desc_at(x0, kk * 32), C::IDESC_COL, kk == 0 ? acc0 : 1u);
+      } else if constexpr (F8) {
         // K = the tile's 128 rows: four K = 32 steps of four 8-row groups, hi and lo planes
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
@@ -376,15 +391,19 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
       inv_gc = ts8_pow2(a.ctl->ts8_max[1], true);
     }
     auto drain = [&](uint32_t taddr, int row, bool row_product) -> bool {  // TMEM rows 32q.. -> Y rows row..
-      float v[N];
+      float v[C::NACC];
 #pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 16) {
+      for (int c0 = 0; c0 < C::NACC; c0 += 16) {
         float tt[16];
         tc_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, tt);
 #pragma unroll
         for (int c = 0; c < 16; ++c) v[c0 + c] = tt[c];
       }
       tc_wait_ld();
+      if constexpr (C::MERGE) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] += v[N + c];  // A X_hi + A X_lo
+      }
       if (row < a.rows) {
         if constexpr (F8) {
           const float m = row_product ? a.rscale[row / N] * inv_gr : inv_gc;
@@ -410,7 +429,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
           break;
         }
         tc_fence_after();
-        drain(tm_d2 + (uint32_t)(db * N), J * kTsTile + 32 * q + lane, false);
+        drain(tm_d2 + (uint32_t)(db * C::NACC), J * kTsTile + 32 * q + lane, false);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&d2_empty[db]);
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
         }
         tc_fence_after();
         for (int r = 0; r < R; ++r)
-          if (used >> r & 1u) drain(tm_d1 + (uint32_t)(r * N), (I0 + r) * kTsTile + 32 * q + lane, true);
+          if (used >> r & 1u) drain(tm_d1 + (uint32_t)(r * C::NACC), (I0 + r) * kTsTile + 32 * q + lane, true);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(d1_empty);
@@ -658,9 +677,9 @@ cudaError_t tc_sym_pack(Src src, int n, int d, bool f8, void* packed, cudaStream
   const int rows = n * d;
 #define NSRGS_TS_PACK(DD)                                                                        \
   if (f8)                                                                                        \
-    ts_pack_kernel<ts_strip_rows(DD), true><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);   \
+    ts_pack_kernel<ts_strip_rows(DD, true), true><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);   \
   else                                                                                           \
-    ts_pack_kernel<ts_strip_rows(DD), false><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);
+    ts_pack_kernel<ts_strip_rows(DD, false), false><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);
   switch (d) {
     case 16: NSRGS_TS_PACK(16) break;
     case 32: NSRGS_TS_PACK(32) break;

@@ -7,9 +7,10 @@ import numpy as np
 T = 128
 
 
-def strip_rows(d):
-    """Row tiles per strip / group of the processing order."""
-    return 4 if d == 64 else 8
+def strip_rows(d, f8=False):
+    """Row tiles per strip / group of the processing order (FP8 at d = 32 keeps
+    its hi and lo accumulators side by side, so fewer fit in TMEM)."""
+    return 4 if d == 64 else (6 if f8 and d == 32 else 8)
 
 
 def swz(r, c):

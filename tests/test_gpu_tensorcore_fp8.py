@@ -110,7 +110,7 @@ def test_fp8_tiles_match_the_host_quantiser(P, n, d):
     r, c = np.meshgrid(np.arange(T), np.arange(T), indexing="ij")
     where = swz8(r, c).ravel()
     for t in range(ntiles):
-        I, J = seek(t, NT, strip_rows(d))
+        I, J = seek(t, NT, strip_rows(d, f8=True))
         vals = Up[I * T : (I + 1) * T, J * T : (J + 1) * T] / sp[I * T : (I + 1) * T, None]
         want = np.empty(16384, dtype=np.uint8)
         want[where] = e4m3_codes(vals).view(torch.uint8).numpy().ravel()

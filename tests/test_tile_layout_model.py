@@ -105,7 +105,7 @@ def test_packed_bytes_match_library(n, d):
     assert lib.nsrgs_packed_bytes(n, d, L.BF16) == NT * (NT + 1) // 2 * 32768
 
 
-@pytest.mark.parametrize("NT,R", [(1, 8), (2, 8), (8, 8), (9, 8), (17, 8), (30, 4), (7, 4), (125, 8)])
+@pytest.mark.parametrize("NT,R", [(1, 8), (2, 8), (8, 8), (9, 8), (17, 8), (30, 4), (7, 4), (125, 8), (20, 6), (5, 6)])
 def test_processing_order_covers_each_tile_once_and_seek_inverts_it(NT, R):
     seq = order(NT, R)
     assert len(seq) == NT * (NT + 1) // 2
