@@ -50,6 +50,9 @@
 //                   the strip's columns) and of the used D1 slots, then
 //                   red.global.add.v4.f32 into Y.
 // Every wait is bounded; a timeout sets FLAG_TIMEOUT and the CTA still frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "src.cuh"
@@ -74,11 +77,18 @@ struct TsCfg {
   static constexpr int STAGE = TILE;                      // the ring holds A tiles only
   static constexpr int SMEM_MAX = 227 * 1024;
   // as many stages as fit beside the two X_J^T slots and the group's R X_I^T tiles
-  static constexpr int NSTAGE_FIT = (SMEM_MAX - 1024 - 512 - (2 + R) * XB) / STAGE;
+  // Y staging of the epilogue: per warp its 32 rows as boxes of 32 rows x BW
+  // floats (128 or 64 bytes per row, swizzled like the tensor map reads them)
+  static constexpr int BW = N < 32 ? N : 32;
+  static constexpr int BOX = 32 * BW * 4;
+  static constexpr int STG_WARP = N * 128;
+  static constexpr int STG = 4 * STG_WARP;
+  static constexpr int NSTAGE_FIT = (SMEM_MAX - 1024 - 512 - (2 + R) * XB - STG) / STAGE;
   static constexpr int NSTAGE = NSTAGE_FIT > 12 ? 12 : NSTAGE_FIT;
   static constexpr int OFF_XJ = NSTAGE * STAGE;          // X_J^T of the current / next strip
   static constexpr int OFF_XI = OFF_XJ + 2 * XB;         // X^T of the group's R row tiles
-  static constexpr int OFF_BARS = OFF_XI + R * XB;
+  static constexpr int OFF_STG = OFF_XI + R * XB;       // Y staging, 4 warps
+  static constexpr int OFF_BARS = OFF_STG + STG;
   static constexpr int NBARS = 2 * NSTAGE + 2 + 4 + 2 + 4;
   static constexpr int SMEM = 1024 + OFF_BARS + NBARS * 8 + 16;
   static constexpr int TMEM_NEED = (R + 2) * NACC;       // D1: R slots, D2: two buffers
@@ -86,7 +96,8 @@ struct TsCfg {
   // D1 += A X_J and D2 += A^T X_I (A read MN-major)
   static constexpr uint32_t IDESC_ROW = F8 ? tc8_idesc(128, NACC, false) : tc_idesc(128, N, false);
   static constexpr uint32_t IDESC_COL = F8 ? tc8_idesc(128, NACC, true) : tc_idesc(128, N, true);
-  static_assert(STAGE % 1024 == 0 && XB % 1024 == 0 && (N * 128) % 1024 == 0, "1024-byte swizzle alignment");
+  static_assert(STAGE % 1024 == 0 && XB % 1024 == 0 && (N * 128) % 1024 == 0 && STG_WARP % 1024 == 0,
+                "1024-byte swizzle alignment");
   static_assert(NSTAGE >= 3, "pipeline depth");
   static_assert(SMEM <= SMEM_MAX, "shared memory");
   static_assert(TMEM_NEED <= 512, "tensor memory");
@@ -120,7 +131,7 @@ __device__ __forceinline__ float ts8_pow2(unsigned mbits, bool inverse) {
 __device__ __forceinline__ uint64_t desc_at(uint64_t base, uint32_t off) { return base + (uint64_t)(off >> 4); }
 
 template <int N, bool F8>
-__global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
+__global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const __grid_constant__ CUtensorMap tmY, const TsArgs a) {
   using C = TsCfg<N, F8>;
   constexpr int R = C::R;
   if (*a.skip) return;  // uniform: written only by earlier launches
@@ -390,6 +401,12 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
       inv_gr = ts8_pow2(a.ctl->ts8_max[0], true);
       inv_gc = ts8_pow2(a.ctl->ts8_max[1], true);
     }
+    // The warp's 32 rows go to Y through shared memory: swizzled 16-byte stores
+    // (conflict-free: the 8 rows of a phase hit 8 different bank groups), then one
+    // TMA reduce-add per 32 x BW box, rows past n*d clipped by the tensor map.
+    // One red.global per row and 16 bytes cost about 2000 cycles per 32 KB drain.
+    uint8_t* stg = smem + C::OFF_STG + (warp - 2) * C::STG_WARP;
+    const uint32_t stg_s = smem_u32(stg);
     auto drain = [&](uint32_t taddr, int row, bool row_product) -> bool {  // TMEM rows 32q.. -> Y rows row..
       float v[C::NACC];
 #pragma unroll
@@ -404,15 +421,27 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
 #pragma unroll
         for (int c = 0; c < N; ++c) v[c] += v[N + c];  // A X_hi + A X_lo
       }
-      if (row < a.rows) {
-        if constexpr (F8) {
-          const float m = row_product ? a.rscale[row / N] * inv_gr : inv_gc;
+      if constexpr (F8) {
+        const float m = row_product ? (row < a.rows ? a.rscale[row / N] : 0.f) * inv_gr : inv_gc;
 #pragma unroll
-          for (int c = 0; c < N; ++c) v[c] *= m;
-        }
-        float* y = a.Y + (long long)row * N;
+        for (int c = 0; c < N; ++c) v[c] *= m;
+      }
+      if (lane == 0) bulk_wait_read_all();  // the previous drain's boxes have left the staging
+      __syncwarp();
+      const int sw = C::BW == 32 ? (lane & 7) : ((lane >> 1) & 3);
 #pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 4) red_add_v4_f32(y + c0, v[c0], v[c0 + 1], v[c0 + 2], v[c0 + 3]);
+      for (int c = 0; c < N / 4; ++c) {
+        const int b = c / (C::BW / 4), k = c % (C::BW / 4);
+        st_shared_v4(stg + b * C::BOX + lane * (C::BW * 4) + ((k ^ sw) << 4), v[4 * c], v[4 * c + 1], v[4 * c + 2],
+                     v[4 * c + 3]);
+      }
+      fence_proxy_async_shared();
+      __syncwarp();
+      const int row0 = row - lane;
+      if (lane == 0 && row0 < a.rows) {
+#pragma unroll
+        for (int b = 0; b < N / C::BW; ++b) tma_reduce_add_2d(&tmY, stg_s + b * C::BOX, b * C::BW, row0);
+        bulk_commit_group();
       }
       return true;
     };
@@ -450,6 +479,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const TsArgs a) {
         ++p;
       }
     }
+    if (lane == 0) bulk_wait_all();  // the reduce-adds into Y are complete
   }
   tc_fence_before();
   __syncthreads();
@@ -614,13 +644,45 @@ long long tc_sym8_bytes(int n, int d) { return ts8_scale_offset(n, d) + ((long l
 long long tc_sym_xt_bytes(int n, int d) { return (long long)ts_tile_rows(n, d) * d * 256; }
 long long tc_sym8_xt_bytes(int n, int d) { return 2 * tc_sym_xt_bytes(n, d); }
 
+static PFN_cuTensorMapEncodeTiled_v12000 ts_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Y (rows x N float32, row-major) as the epilogue's reduce-add target: boxes of
+// 32 rows x BW floats, swizzled as the staging is written.
+template <int N, bool F8>
+static cudaError_t y_map(CUtensorMap* tm, float* Y, int rows) {
+  using C = TsCfg<N, F8>;
+  auto fn = ts_encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)N * 4};
+  cuuint32_t box[2] = {(cuuint32_t)C::BW, 32};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        C::BW == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int N, bool F8>
 static cudaError_t launch_ts(const TsArgs& a, cudaStream_t st, bool prepare) {
   using C = TsCfg<N, F8>;
   if (prepare) return cudaFuncSetAttribute(tc_sym_kernel<N, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  CUtensorMap tm;
+  const cudaError_t e = y_map<N, F8>(&tm, a.Y, a.rows);
+  if (e != cudaSuccess) return e;
   const long long total = ts_tiles(a.NT);
   const int grid = (int)std::min<long long>(total, num_sms());
-  tc_sym_kernel<N, F8><<<grid, kTsThreads, C::SMEM, st>>>(a);
+  tc_sym_kernel<N, F8><<<grid, kTsThreads, C::SMEM, st>>>(tm, a);
   return cudaGetLastError();
 }
 
