@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const __grid_cons
     w.seek(t0);
     int st = 0, p = 0;
     uint32_t ph = 0;
+    const uint64_t pol = l2_evict_first_policy();
     long long it = 0, kx = 0;  // tiles issued, strips started
     bool group_start = true, strip_start = true;
     for (long long t = t0; t < t1 && !failed; ++t, ++it) {
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const __grid_cons
         break;
       }
       mbar_arrive_expect_tx(&full[st], C::STAGE);
-      bulk_g2s(smem + st * C::STAGE, a.tiles + t * (long long)C::TILE, C::TILE, &full[st]);
+      bulk_g2s_hint(smem + st * C::STAGE, a.tiles + t * (long long)C::TILE, C::TILE, &full[st], pol);
       if (++st == C::NSTAGE) {
         st = 0;
         ph ^= 1u;
