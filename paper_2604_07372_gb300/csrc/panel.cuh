@@ -26,6 +26,8 @@
 // instance's control block and ends the kernel instead of hanging.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace nsrgs {
@@ -303,6 +305,15 @@ __device__ __forceinline__ void panel_init_barriers() {
 // thread of the CTA calls it; warps leave it at different times (the caller
 // synchronises afterwards when it needs the result).  Barriers must have been
 // initialised; `pp` carries the thread's pipeline position between calls.
+// Sources whose panels are read once per pass (one instance streamed from HBM)
+// declare kStreamOnce = true: their copies carry an L2 evict-first policy so that
+// they do not push X and Y out of L2.  The batched sources keep the default
+// policy, under which small instances stay in L2 from one pass to the next.
+template <class S, class = void>
+struct stream_once : std::false_type {};
+template <class S>
+struct stream_once<S, std::void_t<decltype(S::kStreamOnce)>> : std::bool_constant<S::kStreamOnce> {};
+
 template <int D, int ST, class Src>
 __device__ __forceinline__ void panel_stream_range(const Src& src, long long g0, long long g1, PanelPipe& pp,
                                                    int res_mode) {
@@ -323,6 +334,7 @@ __device__ __forceinline__ void panel_stream_range(const Src& src, long long g0,
     // X may have been written by generic stores since the last pass (of this
     // launch, in a persistent kernel): order them before this thread's bulk copies
     asm volatile("fence.proxy.async.global;" ::: "memory");
+    const uint64_t pol = l2_evict_first_policy();
     int& st = pp.st;
     uint32_t& ph = pp.ph;
     long long& issued = pp.it;
@@ -374,7 +386,10 @@ __device__ __forceinline__ void panel_stream_range(const Src& src, long long g0,
         } else {
           uint8_t* stage = smem + st * C::STAGE_BYTES;
           mbar_arrive_expect_tx(&full[st], bytesA + C::STAGE_X);
-          bulk_g2s(stage, srcA, bytesA, &full[st]);
+          if constexpr (stream_once<Src>::value)
+            bulk_g2s_hint(stage, srcA, bytesA, &full[st], pol);
+          else
+            bulk_g2s(stage, srcA, bytesA, &full[st]);
           bulk_g2s(stage + C::STAGE_A, srcX, C::STAGE_X, &full[st]);
         }
         off += bytesA;

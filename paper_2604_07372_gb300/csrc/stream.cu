@@ -16,6 +16,7 @@ struct StreamArgs {
 
 // One instance taken from the kernel parameters.
 struct SingleSrc {
+  static constexpr bool kStreamOnce = true;  // A is read once per pass: L2 evict-first
   const StreamArgs* a;
   __device__ __forceinline__ int count() const { return 1; }
   __device__ __forceinline__ int find(long long) const { return 0; }

@@ -78,24 +78,6 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
-// L2 policy for data read once (the A stream): evicted first, so that it does not
-// push out what is reused (X tiles, Y under its reduce-adds).
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-
-// bulk_g2s with an L2 cache policy.
-__device__ __forceinline__ void bulk_g2s_hint(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar,
-                                              uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-          smem_u32(smem_dst)),
-      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
-
 // 2-D TMA reduce-add of a shared-memory box into global memory (f32), bulk-group
 // completion; coordinates {x = column, y = row} must be >= 0, x * 4 a multiple of 16.
 __device__ __forceinline__ void tma_reduce_add_2d(const void* tmap, uint32_t saddr, int x, int y) {
