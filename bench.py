@@ -376,6 +376,7 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
                 ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
                 ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
                 ent["spectral_iters"], ent["flags"] = info.spectral_iters, info.flags
+                ent["spectral_residual"] = info.spectral_residual
                 # the A stream alone inside a solve (CUDA events around each launch in the graph)
                 P.nsrgs_set_kernel_timing(True)
                 P.nsrgs_solve(pa, 1.0 / n, T, 2, spectral_max_iters=SMAX, X=Xs, ws=ws, info=False)
@@ -453,6 +454,7 @@ def sparse_leg(P, synth, seed: int, n: int = 8000, d: int = 3, ps=(0.05, 0.2, 0.
                 ent["solve_ms"] = 1e3 * (time.perf_counter() - t)
                 ent["final_dF_to_truth"] = P.nsrgs_dF(Xs, Zs, n, d, ws=ws)
                 ent["spectral_iters"], ent["flags"] = info.spectral_iters, info.flags
+                ent["spectral_residual"] = info.spectral_residual
                 res[name] = ent
                 del pa, ws, X, Y
             except Exception as e:

@@ -44,8 +44,8 @@ cudaError_t launch_epilogue(const float*, float*, float*, int, int, float, int, 
                             cudaStream_t);
 cudaError_t launch_gpm_epilogue(const float*, float*, float*, int, int, double, Ctl*, cudaStream_t);
 cudaError_t launch_spec_v0(float*, long long, int, double*, cudaStream_t);
-cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, int, const SpecScratch&, Ctl*,
-                             cudaStream_t);
+cudaError_t launch_spec_gram(const float*, float*, float*, long long, int, float, int, int, const SpecScratch&,
+                             Ctl*, cudaStream_t);
 cudaError_t launch_spec_update(const float*, const float*, float*, long long, int, const SpecScratch&, double, int,
                                Ctl*, cudaStream_t);
 cudaError_t launch_polar_blocks(const float*, float*, int, int, cudaStream_t);
@@ -266,18 +266,20 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
   const int n = A->n, d = A->d;
   const long long rows = (long long)n * d;
   // the tensor-core streams round V (bfloat16, or E4M3 hi / lo planes): their passes
-  // may also stop at the residual floor that rounding sets
+  // may also stop at the residual floor that rounding sets, and their float64-free
+  // Gram and update (float32 inner products over 64-row chunks, about 1e-7 of the
+  // terms) stay far below that floor
   const int counted = (A->storage == NSRGS_DENSE_BF16 || tile_upper(A->storage, d)) ? 2 : 1;
   cudaError_t e;
   if ((e = launch_spec_v0(w.X[0], rows, d, w.s.scal + 3, st)) != cudaSuccess) return e;
   // orthonormalise the start: W = V0 (Y is zero), V1 = W chol(W^T W)^{-1}
-  if ((e = launch_spec_gram(w.X[0], w.Y, w.W, rows, d, 1.0f, 0, w.s, w.ctl, st)) != cudaSuccess) return e;
+  if ((e = launch_spec_gram(w.X[0], w.Y, w.W, rows, d, 1.0f, 0, 0, w.s, w.ctl, st)) != cudaSuccess) return e;
   if ((e = launch_spec_update(w.X[0], w.W, w.X[1], rows, d, w.s, tol, 0, w.ctl, st)) != cudaSuccess) return e;
   for (int k = 0; k < max_iters; ++k) {
     const float* V = w.X[(k + 1) & 1];
     float* Vn = w.X[k & 1];
     if ((e = stream_AX(A, g, V, w, &w.ctl->spec_skip, st)) != cudaSuccess) return e;
-    if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, 1, w.s, w.ctl, st)) != cudaSuccess) return e;
+    if ((e = launch_spec_gram(V, w.Y, w.W, rows, d, 1.0f, 1, counted == 2, w.s, w.ctl, st)) != cudaSuccess) return e;
     if ((e = launch_spec_update(V, w.W, Vn, rows, d, w.s, tol, counted, w.ctl, st)) != cudaSuccess) return e;
   }
   // final basis -> W, then X0 = sgn_n(W)

@@ -9,6 +9,8 @@
 //   * d_F(X, Y) (§1.4).
 #include <math.h>
 
+#include <type_traits>
+
 #include "blockops.cuh"
 
 namespace nsrgs {
@@ -291,107 +293,192 @@ __global__ void __launch_bounds__(256) polar_generic_kernel(const float* __restr
 }
 
 // ----------------------------------------------------- Gram reductions
-// Partial sums over a chunk of rows of P^T Q (and, when W_out is given,
-// W = Y + shift V first: then P = W, Q = W and a second product V^T W).
-// Outputs o in [0, nout): o < D*D -> (P^T Q)[o]; o >= D*D -> (V^T W)[o - D*D].
+// Partial sums over chunks of rows of P^T Q (and, in the spectral mode, first
+// W = Y + shift V, then P = Q = W and a second product V^T W).
+// Outputs: (P^T Q)[a][b] (mode 0: W^T W into s.WW; mode 1: Yv^T Xq into s.M) and, in
+// mode 0, (V^T W)[a][b] into s.H.
+// A chunk of 64 rows is staged in shared memory (as T, columns padded to DP, a
+// multiple of 8); each thread owns a 4 x 8 tile of one product's outputs, so a
+// row of the chunk costs it 12 shared loads for 32 FMAs.  T: the arithmetic of the
+// inner products (float64; float32 for the tensor-core storages, whose residual
+// floor sits near 1e-3: then a CTA sums its rows in float32 and the CTAs' sums
+// are added in float64).
 constexpr int kRowsPerCta = 64;
 
+template <typename T>
 __global__ void __launch_bounds__(256) gram_generic_kernel(const float* __restrict__ V, float* __restrict__ Yv,
                                                            float* __restrict__ W, const float* __restrict__ Xq,
                                                            long long rows, int D, float shift, int dev_shift,
                                                            int mode, SpecScratch s, Ctl* ctl) {
-  // mode 0: spectral Gram (W = Y + shift V; outputs W^T W and V^T W); mode 1: M = Yv^T Xq.
-  // The chunk is staged as float64 (exact conversions, once per element), so the
-  // inner products are float64 FMAs alone: GB300 runs float64 conversions on the
-  // same slow pipe as float64 arithmetic.
-  extern __shared__ __align__(16) double smg[];
+  extern __shared__ __align__(16) double smg_raw[];
+  T* smg = reinterpret_cast<T*>(smg_raw);
   if (mode == 0 && ctl->spec_skip) return;
   // spectral mode: W = Y + c V, c the orthonormalising pass's `shift` or the current
   // shift; a restart pass (after a failed algebraic top-d test) takes W = V^0
   const bool restart = mode == 0 && dev_shift && ctl->spec_restart;
   const float c = (mode == 0 && dev_shift) ? (float)s.scal[3] : shift;
   const int DD = D * D;
-  const int nout = mode == 0 ? 2 * DD : DD;
-  double* P = smg;                     // kRowsPerCta x D
-  double* Q = smg + kRowsPerCta * D;   // kRowsPerCta x D
-  double acc[32];  // outputs o = threadIdx.x + k * 256, k < nout / 256 <= 2 * 64 * 64 / 256
-  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+  const int DP = (D + 7) & ~7;
+  const int nprod = mode == 0 ? 2 : 1;
+  T* Pm = smg;                    // kRowsPerCta x DP: V (mode 0) or Yv (mode 1)
+  T* Qm = smg + kRowsPerCta * DP; // kRowsPerCta x DP: W (mode 0) or Xq (mode 1)
+  // thread -> (product g, 4-row block ta, 8-column block tb)
+  const int tb_n = DP / 8, tiles = (DP / 4) * tb_n;
+  const int g = threadIdx.x / tiles, rem = threadIdx.x % tiles;
+  const bool active = g < nprod;
+  const int a0 = (rem / tb_n) * 4, b0 = (rem % tb_n) * 8;
+  // mode 0: g = 0 -> W^T W (P = Q = W), g = 1 -> V^T W; mode 1: Yv^T Xq
+  const T* Pg = (mode == 0 && g == 0) ? Qm : Pm;
+  double acc[4][8];
+  float accf[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0, accf[i][j] = 0.f;
   for (long long r0 = (long long)blockIdx.x * kRowsPerCta; r0 < rows; r0 += (long long)gridDim.x * kRowsPerCta) {
     const int nr = (int)min((long long)kRowsPerCta, rows - r0);
     __syncthreads();
     for (int e = threadIdx.x; e < nr * D; e += blockDim.x) {
       const long long ge = r0 * D + e;
+      const int si = (e / D) * DP + e % D;
       if (mode == 0) {
         const float v = V[ge];
         const float w = restart ? spec_v0_entry(ge) : Yv[ge] + c * v;
         W[ge] = w;
         Yv[ge] = 0.f;
-        P[e] = v;
-        Q[e] = w;
+        Pm[si] = (T)v;
+        Qm[si] = (T)w;
       } else {
-        P[e] = Yv[ge];
-        Q[e] = Xq[ge];
+        Pm[si] = (T)Yv[ge];
+        Qm[si] = (T)Xq[ge];
       }
     }
     __syncthreads();
-    int k = 0;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x, ++k) {
-      const int oo = o % DD;
-      const int a = oo / D, b = oo % D;
-      double sum = 0.0;
-      if (mode == 0 && o < DD) {
-        for (int r = 0; r < nr; ++r) sum += Q[r * D + a] * Q[r * D + b];
-      } else {
-        for (int r = 0; r < nr; ++r) sum += P[r * D + a] * Q[r * D + b];
+    if constexpr (std::is_same<T, double>::value) {  // float64: straight into the totals
+      if (!active) continue;
+      for (int r = 0; r < nr; ++r) {
+        double p[4], q[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = (double)Pg[r * DP + a0 + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = (double)Qm[r * DP + b0 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] += p[i] * q[j];
       }
-      acc[k] += sum;
+    } else {
+      // float32: the whole CTA range in float32 registers (a few thousand rows at
+      // most, ~1e-6 relative against a residual floor near 1e-3)
+      if (!active) continue;
+      for (int r = 0; r < nr; ++r) {
+        float p[4], q[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = (float)Pg[r * DP + a0 + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = (float)Qm[r * DP + b0 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) accf[i][j] += p[i] * q[j];
+      }
     }
   }
+  const int nout = nprod * DD;
   double* part = s.partials + (long long)blockIdx.x * nout;
-  {
-    int k = 0;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x, ++k) part[o] = acc[k];
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (a0 + i < D && b0 + j < D)
+          part[g * DD + (a0 + i) * D + b0 + j] = std::is_same<T, double>::value ? acc[i][j] : (double)accf[i][j];
   }
-  if (last_block(&ctl->counter)) {
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      double a = 0.0;
-      for (unsigned int bb = 0; bb < gridDim.x; ++bb) a += s.partials[(long long)bb * nout + o];
-      if (mode == 0) {
-        if (o < DD) s.WW[o] = a; else s.H[o - DD] = a;
-      } else {
-        s.M[o] = a;
-      }
+}
+
+// The CTAs' partial sums of gram_generic_kernel added up (thread per output,
+// coalesced over the partials), then, by the last CTA: mode 0 ||H||_F^2 and the
+// Cholesky factor of W^T W with its inverse (R^T R = W^T W, all threads of the
+// CTA; R^{-1} by columns), mode 1 nothing more.  Dynamic shared memory: D x D doubles.
+__global__ void __launch_bounds__(256) gram_finish_kernel(int nparts, int D, int mode, SpecScratch s, Ctl* ctl) {
+  extern __shared__ __align__(16) double smf[];
+  __shared__ double sh[32];
+  if (mode == 0 && ctl->spec_skip) return;
+  const int DD = D * D, nout = (mode == 0 ? 2 : 1) * DD;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < nout) {
+    double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b = 0;
+    for (; b + 8 <= nparts; b += 8)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] += s.partials[(long long)(b + u) * nout + o];
+    for (; b < nparts; ++b) t[0] += s.partials[(long long)b * nout + o];
+    const double a = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    if (mode == 0) {
+      if (o < DD) s.WW[o] = a; else s.H[o - DD] = a;
+    } else {
+      s.M[o] = a;
     }
-    __syncthreads();
+  }
+  if (!last_block(&ctl->counter)) return;
+  if (mode != 0) {
     if (threadIdx.x == 0) {
-      if (mode == 0) {
-        double h2 = 0.0;
-        for (int o = 0; o < DD; ++o) h2 += s.H[o] * s.H[o];
-        s.scal[0] = h2;
-        chol_inv(s.WW, s.Rinv, D, s.Q);  // s.Q as Cholesky scratch here
-        s.scal[2] = 0.0;
-      } else {
-        s.scal[1] = 0.0;
-      }
+      s.scal[1] = 0.0;
       ctl->counter = 0u;
     }
+    return;
+  }
+  double h2 = 0.0;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) h2 += s.H[e] * s.H[e];
+  h2 = block_sum(h2, sh);
+  // right-looking Cholesky in shared memory: row j of R = A[j][j..] after step j
+  double* A = smf;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) A[e] = s.WW[e];
+  __syncthreads();
+  for (int j = 0; j < D; ++j) {
+    if (threadIdx.x == 0) A[j * D + j] = sqrt(fmax(A[j * D + j], 1e-300));
+    __syncthreads();
+    const double rjj = A[j * D + j];
+    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) A[j * D + i] /= rjj;
+    __syncthreads();
+    const int m = D - j - 1;  // trailing block rows/columns j+1 .. D-1, upper part
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int r = j + 1 + e / m, c = j + 1 + e % m;
+      if (c >= r) A[r * D + c] -= A[j * D + r] * A[j * D + c];
+    }
+    __syncthreads();
+  }
+  // R^{-1} (upper triangular) by back substitution, one column per thread
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    for (int r = D - 1; r >= 0; --r) {
+      double t = (r == c) ? 1.0 : 0.0;
+      for (int k = r + 1; k <= c; ++k) t -= A[r * D + k] * s.Rinv[k * D + c];
+      s.Rinv[r * D + c] = (r <= c) ? t / A[r * D + r] : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    s.scal[0] = h2;
+    s.scal[2] = 0.0;
+    ctl->counter = 0u;
   }
 }
 
 // Vnew = W Rinv and the residual ||W - V H||^2 (thread per row); the last CTA
-// finishes ||A V - V H||_F / ||H||_F.  Dynamic shared memory: Rinv and H (float64).
+// finishes ||A V - V H||_F / ||H||_F.  Dynamic shared memory: Rinv and H (as T;
+// T as in gram_generic_kernel, the residual summed in float64).
+template <typename T>
 __global__ void __launch_bounds__(256) update_generic_kernel(const float* __restrict__ V, const float* __restrict__ W,
                                                              float* __restrict__ Vnew, long long rows, int D,
                                                              SpecScratch s, double tol, int count_pass, Ctl* ctl) {
-  extern __shared__ __align__(16) double smu[];
+  extern __shared__ __align__(16) double smu_raw[];
   __shared__ double sh[32];
   if (ctl->spec_skip) return;
   const int DD = D * D;
-  double* rinv = smu;
-  double* hh = smu + DD;
+  T* rinv = reinterpret_cast<T*>(smu_raw);
+  T* hh = rinv + DD;
   for (int o = threadIdx.x; o < DD; o += blockDim.x) {
-    rinv[o] = s.Rinv[o];
-    hh[o] = s.H[o];
+    rinv[o] = (T)s.Rinv[o];
+    hh[o] = (T)s.H[o];
   }
   __syncthreads();
   // Columns in tiles of 16 with k outer, so each row element is converted to
@@ -403,11 +490,11 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
     const float* w = W + r * D;
     const float* v = V + r * D;
     for (int c0 = 0; c0 < D; c0 += kTile) {
-      double nv[kTile], vh[kTile];
+      T nv[kTile], vh[kTile];
 #pragma unroll
-      for (int j = 0; j < kTile; ++j) nv[j] = vh[j] = 0.0;
+      for (int j = 0; j < kTile; ++j) nv[j] = vh[j] = 0;
       for (int k = 0; k < D; ++k) {
-        const double wk = w[k], vk = v[k];
+        const T wk = w[k], vk = v[k];
 #pragma unroll
         for (int j = 0; j < kTile; ++j)
           if (c0 + j < D) {
@@ -420,8 +507,8 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
         if (c0 + j < D) {
           const int c = c0 + j;
           Vnew[r * D + c] = (float)nv[j];
-          const double e = (double)w[c] - vh[j];
-          res += e * e;
+          const T e = (T)w[c] - vh[j];
+          res += (double)e * (double)e;
         }
     }
   }
@@ -482,9 +569,12 @@ cudaError_t generic_prepare(int d) {
   if ((e = set_smem((const void*)gpm_generic_kernel, 3 * d * d * sizeof(float))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)polar_generic_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)polar_single_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)update_generic_kernel, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)update_generic_kernel<double>, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)update_generic_kernel<float>, 2 * d * d * sizeof(float))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)gram_generic_kernel<float>, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(float))) != cudaSuccess)
+    return e;
   if ((e = set_smem((const void*)dist_generic_kernel, d * d * sizeof(double))) != cudaSuccess) return e;
-  return set_smem((const void*)gram_generic_kernel, 2 * kRowsPerCta * d * sizeof(double));
+  return set_smem((const void*)gram_generic_kernel<double>, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(double));
 }
 
 static int gram_grid(long long rows) {
@@ -505,17 +595,34 @@ cudaError_t launch_gpm_generic(const float* X, float* Y, float* Xout, int n, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_spec_gram_generic(const float* V, float* Y, float* W, long long rows, int d, float shift,
-                                     int dev_shift, const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
-  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(V, Y, W, nullptr, rows, d,
-                                                                                        shift, dev_shift, 0, s, ctl);
+static cudaError_t launch_gram_finish(long long rows, int d, int mode, const SpecScratch& s, Ctl* ctl,
+                                      cudaStream_t st) {
+  const int nout = (mode == 0 ? 2 : 1) * d * d;
+  gram_finish_kernel<<<(nout + 255) / 256, 256, d * d * sizeof(double), st>>>(gram_grid(rows), d, mode, s, ctl);
   return cudaGetLastError();
 }
 
+cudaError_t launch_spec_gram_generic(const float* V, float* Y, float* W, long long rows, int d, float shift,
+                                     int dev_shift, int fp32, const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+  if (fp32)
+    gram_generic_kernel<float><<<gram_grid(rows), 256, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(float), st>>>(
+        V, Y, W, nullptr, rows, d, shift, dev_shift, 0, s, ctl);
+  else
+    gram_generic_kernel<double><<<gram_grid(rows), 256, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(double), st>>>(
+        V, Y, W, nullptr, rows, d, shift, dev_shift, 0, s, ctl);
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_gram_finish(rows, d, 0, s, ctl, st);
+}
+
+// count_pass == 2 (a pass of a rounded-operand product) runs the update in float32.
 cudaError_t launch_spec_update_generic(const float* V, const float* W, float* Vnew, long long rows, int d,
                                        const SpecScratch& s, double tol, int count_pass, Ctl* ctl, cudaStream_t st) {
-  update_generic_kernel<<<reduce_grid(rows), 256, 2 * d * d * sizeof(double), st>>>(V, W, Vnew, rows, d, s, tol,
-                                                                                   count_pass, ctl);
+  if (count_pass == 2)
+    update_generic_kernel<float><<<reduce_grid(rows), 256, 2 * d * d * sizeof(float), st>>>(V, W, Vnew, rows, d, s,
+                                                                                          tol, count_pass, ctl);
+  else
+    update_generic_kernel<double><<<reduce_grid(rows), 256, 2 * d * d * sizeof(double), st>>>(V, W, Vnew, rows, d, s,
+                                                                                            tol, count_pass, ctl);
   return cudaGetLastError();
 }
 
@@ -526,10 +633,10 @@ cudaError_t launch_polar_generic(const float* V, float* X0, int n, int d, cudaSt
 
 cudaError_t launch_dF_generic(const float* X, const float* Yv, long long rows, int d, const SpecScratch& s, Ctl* ctl,
                               cudaStream_t st) {
-  gram_generic_kernel<<<gram_grid(rows), 256, 2 * kRowsPerCta * d * sizeof(double), st>>>(nullptr, const_cast<float*>(Yv),
-                                                                                        nullptr, X, rows, d, 0.f, 0, 1,
-                                                                                        s, ctl);
+  gram_generic_kernel<double><<<gram_grid(rows), 256, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(double), st>>>(
+      nullptr, const_cast<float*>(Yv), nullptr, X, rows, d, 0.f, 0, 1, s, ctl);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_gram_finish(rows, d, 1, s, ctl, st);
   if (e != cudaSuccess) return e;
   polar_single_kernel<<<1, 256, 4 * d * d * sizeof(double), st>>>(s, d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

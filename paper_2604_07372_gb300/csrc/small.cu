@@ -353,8 +353,8 @@ __global__ void select_copy_kernel(const float* __restrict__ B0, const float* __
 // Runtime-d versions for 8 < d <= 64 (generic.cu).
 cudaError_t launch_epilogue_generic(const float*, float*, float*, int, int, float, int, int, double, Ctl*, double*,
                                     cudaStream_t);
-cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, int, const SpecScratch&,
-                                     Ctl*, cudaStream_t);
+cudaError_t launch_spec_gram_generic(const float*, float*, float*, long long, int, float, int, int,
+                                     const SpecScratch&, Ctl*, cudaStream_t);
 cudaError_t launch_spec_update_generic(const float*, const float*, float*, long long, int, const SpecScratch&,
                                        double, int, Ctl*, cudaStream_t);
 cudaError_t launch_polar_generic(const float*, float*, int, int, cudaStream_t);
@@ -395,9 +395,10 @@ cudaError_t launch_spec_v0(float* V, long long rows, int d, double* shift_slot, 
   return cudaGetLastError();
 }
 
+// fp32: the chunk inner products in float32 (rounded-operand products, d > 8 only).
 cudaError_t launch_spec_gram(const float* V, float* Y, float* W, long long rows, int d, float shift, int dev_shift,
-                             const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
-  if (d > kDmaxSmall) return launch_spec_gram_generic(V, Y, W, rows, d, shift, dev_shift, s, ctl, st);
+                             int fp32, const SpecScratch& s, Ctl* ctl, cudaStream_t st) {
+  if (d > kDmaxSmall) return launch_spec_gram_generic(V, Y, W, rows, d, shift, dev_shift, fp32, s, ctl, st);
   const int grid = reduce_grid(rows);
 #define L(DD) spec_gram_kernel<DD><<<grid, 256, 0, st>>>(V, Y, W, rows, shift, dev_shift, s, ctl)
   NSRGS_DISPATCH_D(d, L)
