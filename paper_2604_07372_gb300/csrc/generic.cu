@@ -16,15 +16,50 @@
 namespace nsrgs {
 
 // C = alpha * op(A) * B + beta * C0 for D x D row-major matrices in shared memory
-// (op(A) = A or A^T); every thread computes a strided subset of the entries.
+// (op(A) = A or A^T).  Each thread owns TS x TS tiles of C, TS the largest of 4, 2,
+// 1 that still gives every thread of the CTA a tile (one 4 x 4 tile per thread at
+// D = 64: a k step costs 8 shared loads for 16 FMAs); C must not alias A or B.
+template <typename T, int TS>
+__device__ void cta_mm_ts(const T* A, bool transA, const T* B, T* C, int D, T alpha, const T* C0, T beta) {
+  const int tn = (D + TS - 1) / TS, tiles = tn * tn;
+  for (int tt = threadIdx.x; tt < tiles; tt += blockDim.x) {
+    const int r0 = (tt / tn) * TS, c0 = (tt % tn) * TS;
+    T acc[TS][TS];
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) acc[i][j] = 0;
+    for (int k = 0; k < D; ++k) {
+      T a[TS], b[TS];
+#pragma unroll
+      for (int i = 0; i < TS; ++i) {
+        const int r = r0 + i, c = c0 + i;
+        a[i] = r < D ? (transA ? A[k * D + r] : A[r * D + k]) : T(0);
+        b[i] = c < D ? B[k * D + c] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < TS; ++j) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        const int r = r0 + i, c = c0 + j;
+        if (r < D && c < D) C[r * D + c] = alpha * acc[i][j] + (C0 ? beta * C0[r * D + c] : T(0));
+      }
+  }
+}
+
 template <typename T>
 __device__ void cta_mm(const T* A, bool transA, const T* B, T* C, int D, T alpha, const T* C0, T beta) {
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-    const int r = e / D, c = e % D;
-    T acc = 0;
-    for (int k = 0; k < D; ++k) acc += (transA ? A[k * D + r] : A[r * D + k]) * B[k * D + c];
-    C[e] = alpha * acc + (C0 ? beta * C0[e] : T(0));
-  }
+  if (D * D >= 16 * (int)blockDim.x)
+    cta_mm_ts<T, 4>(A, transA, B, C, D, alpha, C0, beta);
+  else if (D * D >= 4 * (int)blockDim.x)
+    cta_mm_ts<T, 2>(A, transA, B, C, D, alpha, C0, beta);
+  else
+    cta_mm_ts<T, 1>(A, transA, B, C, D, alpha, C0, beta);
 }
 
 // ------------------------------------------------------------ epilogue
@@ -245,9 +280,14 @@ __global__ void __launch_bounds__(256) gpm_generic_kernel(const float* __restric
 }
 
 // ------------------------------------------------- exact sign (float64)
-// S <- M / ||M||_F, then S <- S (3I - S^T S)/2 until ||I - S^T S||_F < 1e-14.
-// Shared scratch: 3 D x D doubles (S, T, U).  Result in S.
-__device__ void cta_polar_ns64(const double* M, double* S, double* T, double* U, int D, double* sh) {
+// S <- M / ||M||_F, then S <- S (3I - S^T S)/2 until ||I - S^T S||_F < 1e-14.  The
+// iterations far from the polar factor run in float32 (GB300's float64 pipe is a
+// small fraction of its float32 one) until ||I - S^T S||_F < 1e-4; the quadratic
+// convergence then takes the float64 iterations from there to rounding level in
+// two or three steps.  Shared scratch: 3 D x D doubles (S, T, U) and 3 D x D floats
+// (Sf, Tf, Uf).  Result in S.
+__device__ void cta_polar_ns64(const double* M, double* S, double* T, double* U, float* Sf, float* Tf, float* Uf,
+                               int D, double* sh) {
   const int DD = D * D;
   double f2 = 0.0;
   for (int e = threadIdx.x; e < DD; e += blockDim.x) f2 += M[e] * M[e];
@@ -256,7 +296,27 @@ __device__ void cta_polar_ns64(const double* M, double* S, double* T, double* U,
   __shared__ int s_done;
   if (threadIdx.x == 0) s_norm = f2 > 0.0 ? 1.0 / sqrt(f2) : 0.0;
   __syncthreads();
-  for (int e = threadIdx.x; e < DD; e += blockDim.x) S[e] = M[e] * s_norm;
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) Sf[e] = (float)(M[e] * s_norm);
+  for (int it = 0; it < 100; ++it) {
+    __syncthreads();
+    cta_mm<float>(Sf, true, Sf, Tf, D, 1.f, nullptr, 0.f);  // S^T S
+    __syncthreads();
+    double err = 0.0;
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+      const float v = ((e / D == e % D) ? 1.f : 0.f) - Tf[e];
+      err += (double)v * v;
+      Tf[e] = ((e / D == e % D) ? 3.f : 0.f) - Tf[e];
+    }
+    err = block_sum(err, sh);
+    if (threadIdx.x == 0) s_done = err < 1e-8;
+    __syncthreads();
+    if (s_done) break;
+    cta_mm<float>(Sf, false, Tf, Uf, D, 0.5f, nullptr, 0.f);
+    __syncthreads();
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) Sf[e] = Uf[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < DD; e += blockDim.x) S[e] = (double)Sf[e];
   for (int it = 0; it < 100; ++it) {
     __syncthreads();
     cta_mm<double>(S, true, S, T, D, 1.0, nullptr, 0.0);  // S^T S
@@ -279,16 +339,17 @@ __device__ void cta_polar_ns64(const double* M, double* S, double* T, double* U,
   __syncthreads();
 }
 
-// X0_i = sgn(V_i), CTA per block.  Dynamic shared memory: 4 D x D doubles.
+// X0_i = sgn(V_i), CTA per block.  Dynamic shared memory: 4 D x D doubles, 3 D x D floats.
 __global__ void __launch_bounds__(256) polar_generic_kernel(const float* __restrict__ V, float* __restrict__ X0, int D) {
   extern __shared__ __align__(16) double smd[];
   __shared__ double sh[32];
   const int DD = D * D;
   double* M = smd;
+  float* f = reinterpret_cast<float*>(smd + 4 * DD);
   const long long base = (long long)blockIdx.x * DD;
   for (int e = threadIdx.x; e < DD; e += blockDim.x) M[e] = V[base + e];
   __syncthreads();
-  cta_polar_ns64(M, smd + DD, smd + 2 * DD, smd + 3 * DD, D, sh);
+  cta_polar_ns64(M, smd + DD, smd + 2 * DD, smd + 3 * DD, f, f + DD, f + 2 * DD, D, sh);
   for (int e = threadIdx.x; e < DD; e += blockDim.x) X0[base + e] = (float)smd[DD + e];
 }
 
@@ -523,14 +584,15 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
   }
 }
 
-// Q = sgn(M) for the d_F minimiser (one CTA).  Dynamic shared memory: 4 D x D doubles.
+// Q = sgn(M) for the d_F minimiser (one CTA).  Dynamic shared memory: 4 D x D doubles, 3 D x D floats.
 __global__ void __launch_bounds__(256) polar_single_kernel(SpecScratch s, int D) {
   extern __shared__ __align__(16) double smp[];
   __shared__ double sh[32];
   const int DD = D * D;
   for (int e = threadIdx.x; e < DD; e += blockDim.x) smp[e] = s.M[e];
   __syncthreads();
-  cta_polar_ns64(smp, smp + DD, smp + 2 * DD, smp + 3 * DD, D, sh);
+  float* f = reinterpret_cast<float*>(smp + 4 * DD);
+  cta_polar_ns64(smp, smp + DD, smp + 2 * DD, smp + 3 * DD, f, f + DD, f + 2 * DD, D, sh);
   for (int e = threadIdx.x; e < DD; e += blockDim.x) s.Q[e] = smp[DD + e];
 }
 
@@ -567,8 +629,9 @@ cudaError_t generic_prepare(int d) {
   cudaError_t e;
   if ((e = set_smem((const void*)epilogue_generic_kernel, 5 * d * d * sizeof(float))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)gpm_generic_kernel, 3 * d * d * sizeof(float))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)polar_generic_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)polar_single_kernel, 4 * d * d * sizeof(double))) != cudaSuccess) return e;
+  const size_t polar_smem = 4 * d * d * sizeof(double) + 3 * d * d * sizeof(float);
+  if ((e = set_smem((const void*)polar_generic_kernel, polar_smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)polar_single_kernel, polar_smem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)update_generic_kernel<double>, 2 * d * d * sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)update_generic_kernel<float>, 2 * d * d * sizeof(float))) != cudaSuccess) return e;
   if ((e = set_smem((const void*)gram_generic_kernel<float>, 2 * kRowsPerCta * ((d + 7) & ~7) * sizeof(float))) != cudaSuccess)
@@ -627,7 +690,7 @@ cudaError_t launch_spec_update_generic(const float* V, const float* W, float* Vn
 }
 
 cudaError_t launch_polar_generic(const float* V, float* X0, int n, int d, cudaStream_t st) {
-  polar_generic_kernel<<<n, 256, 4 * d * d * sizeof(double), st>>>(V, X0, d);
+  polar_generic_kernel<<<n, 256, 4 * d * d * sizeof(double) + 3 * d * d * sizeof(float), st>>>(V, X0, d);
   return cudaGetLastError();
 }
 
@@ -638,7 +701,7 @@ cudaError_t launch_dF_generic(const float* X, const float* Yv, long long rows, i
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_gram_finish(rows, d, 1, s, ctl, st);
   if (e != cudaSuccess) return e;
-  polar_single_kernel<<<1, 256, 4 * d * d * sizeof(double), st>>>(s, d);
+  polar_single_kernel<<<1, 256, 4 * d * d * sizeof(double) + 3 * d * d * sizeof(float), st>>>(s, d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   dist_generic_kernel<<<reduce_grid(rows), 256, d * d * sizeof(double), st>>>(X, Yv, rows, d, s, ctl);
   return cudaGetLastError();
