@@ -129,7 +129,8 @@ typedef struct nsrgs_info {
                               bit 6: the spectral initialisation restarted with a larger
                               shift to reach the algebraic top-d (see nsrgs_spectral_init);
                               bit 7: the spectral initialisation stopped at its product's
-                              precision floor, above tol (tensor-core storage only) */
+                              precision floor, above tol (tensor-core storages, and F32 at
+                              8 < d <= 64; see nsrgs_spectral_init) */
   double objective;        /* nsrgs_solve_objective: F(X) of eq. (1) at the returned X; NaN otherwise */
   double rel_decrease;     /* nsrgs_solve_objective: the last relative decrease R^t formed; NaN otherwise */
 } nsrgs_info;
@@ -186,7 +187,9 @@ nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* p
  * hi + lo planes, about 2^-8 relative), which puts a floor under the residual,
  * typically 1e-4 .. 1e-3: there the passes also count as converged once the
  * residual is at most 1e-2 and no smaller than the previous pass's (info flags
- * bit 7), and the same positive-definiteness test follows.
+ * bit 7), and the same positive-definiteness test follows.  F32 storage at
+ * 8 < d <= 64 (float32 tiles, sums of thousands of float32 products per output)
+ * floors near 1e-6 for n d around 10^5 and stops the same way below 1e-4.
  * The per-block matrix sign is exact (float64 one-sided Jacobi SVD).  Returns
  * NSRGS_ERR_NOT_CONVERGED (X0 still written) when max_iters ran out; with
  * `residual` non-null the final residual is written there (host; synchronises). */

@@ -269,7 +269,10 @@ static cudaError_t enqueue_spectral(const nsrgs_A* A, const PanelGeom& g, const 
   // may also stop at the residual floor that rounding sets, and their float64-free
   // Gram and update (float32 inner products over 64-row chunks, about 1e-7 of the
   // terms) stay far below that floor
-  const int counted = (A->storage == NSRGS_DENSE_BF16 || tile_upper(A->storage, d)) ? 2 : 1;
+  // (mode 3: the float32 tile stream, whose long float32 sums floor near 1e-6)
+  const int counted = (A->storage == NSRGS_DENSE_BF16 || tile_upper(A->storage, d))
+                          ? 2
+                          : ((A->storage == NSRGS_F32 && fs_sym_supported(d)) ? 3 : 1);
   cudaError_t e;
   if ((e = launch_spec_v0(w.X[0], rows, d, w.s.scal + 3, st)) != cudaSuccess) return e;
   // orthonormalise the start: W = V0 (Y is zero), V1 = W chol(W^T W)^{-1}

@@ -264,13 +264,13 @@ __device__ __forceinline__ float spec_v0_entry(long long e) {
 
 // End of a counted spectral pass (one thread): `tot` = ||W - V H||_F^2.  A restart
 // pass only orthonormalises V^0.  Otherwise the relative residual is recorded
-// and, once it is <= tol (or, with `floor_stop`, once it sits at the product's
-// precision floor: at most kSpecFloorMax and no smaller than the previous pass's),
+// and, once it is <= tol (or, with floor_max > 0, once it sits at the product's
+// precision floor: at most floor_max and no smaller than the previous pass's),
 // the algebraic top-d test decides: stop, or restart from V^0 with the larger
 // shift (at most kSpecMaxRestarts times; after that the passes halt with
 // spec_stop clear, reported as not converged).
 __device__ inline void spec_finish_pass(double tot, int D, double tol, const SpecScratch& s, Ctl* ctl,
-                                        bool floor_stop) {
+                                        double floor_max) {
   ctl->spec_iters += 1;
   if (ctl->spec_restart) {
     ctl->spec_restart = 0;
@@ -280,7 +280,7 @@ __device__ inline void spec_finish_pass(double tot, int D, double tol, const Spe
   const double prev = ctl->spec_prev_res;
   ctl->spec_res = rel;
   ctl->spec_prev_res = rel;
-  const bool at_floor = floor_stop && prev > 0.0 && rel <= kSpecFloorMax && rel >= prev;
+  const bool at_floor = floor_max > 0.0 && prev > 0.0 && rel <= floor_max && rel >= prev;
   if (!(rel <= tol) && !at_floor) return;
   const double c2 = spec_shift_after(s.H, D, s.scal[3], s.M);
   if (c2 == 0.0) {

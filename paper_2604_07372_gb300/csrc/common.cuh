@@ -64,8 +64,17 @@ struct Ctl {
 // the operand's precision times ||A_off V_perp|| / ||A_off V||: below the floor
 // further passes only move V within that rounding.  Such a start also stops once
 // its residual, at most kSpecFloorMax, failed to decrease from one pass to the
-// next (and reports FLAG_SPEC_AT_FLOOR).
+// next (and reports FLAG_SPEC_AT_FLOOR).  The float32 tile stream (8 < d <= 64)
+// sums thousands of float32 products per output; its floor sits near 1e-6 at
+// n d = 64000..128000, so it stops the same way below kSpecFloorMaxF32.
 constexpr double kSpecFloorMax = 1e-2;
+constexpr double kSpecFloorMaxF32 = 1e-4;
+// The counted-pass modes of the spectral update: 1 plain, 2 rounded-operand
+// product (float32 d x d work, floor at kSpecFloorMax), 3 float32 tile stream
+// (float64 d x d work, floor at kSpecFloorMaxF32).
+__host__ __device__ constexpr double spec_floor_max(int count_pass) {
+  return count_pass == 2 ? kSpecFloorMax : (count_pass == 3 ? kSpecFloorMaxF32 : 0.0);
+}
 
 // Restarts the spectral start may take with a larger shift before it gives up
 // (then it reports the subspace as not converged).

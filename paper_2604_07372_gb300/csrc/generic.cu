@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(256) update_generic_kernel(const float* __rest
     if (threadIdx.x == 0) {
       const double tot = atomicAdd(&s.scal[2], 0.0);
       ctl->counter = 0u;
-      if (count_pass) spec_finish_pass(tot, D, tol, s, ctl, count_pass == 2);
+      if (count_pass) spec_finish_pass(tot, D, tol, s, ctl, spec_floor_max(count_pass));
     }
   }
 }
