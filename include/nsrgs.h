@@ -61,7 +61,7 @@ typedef enum {
  *            upper triangle, each feeding Y_I += A_IJ X_J and Y_J += A_IJ^T X_I on
  *            the CUDA cores): half the bytes of DENSE_F32.
  *  BF16    : A rounded to bfloat16 (round to nearest even).  For d <= 8 the panel
- *            layout on the CUDA cores; for d in {16, 32, 64} the tile-upper layout
+ *            layout on the CUDA cores; for 8 < d <= 64 the tile-upper layout
  *            on the tensor cores (128 x 128 tiles of the upper triangle, each feeding
  *            Y_I += A_IJ X_J and Y_J += A_IJ^T X_I through tcgen05 with X rounded to
  *            bfloat16, float32 accumulation in TMEM): half the bytes of DENSE_BF16.
@@ -69,7 +69,7 @@ typedef enum {
  *            float32 scale per block row i: s_i = max_{j>i} max|A_ij| / 448 and
  *            A_ij ~ s_i * q_ij.  The per-block-row scale is this library's choice;
  *            the paper does not discuss reduced precision.  For d <= 4 the panel
- *            layout on the CUDA cores (X float32).  For d in {16, 32, 64} the
+ *            layout on the CUDA cores (X float32).  For 8 < d <= 64 the
  *            tile-upper layout of BF16 with one byte per element (16 KB tiles, the n
  *            scales behind them) on the tensor cores (tcgen05 kind::f8f6f4): X
  *            enters as two E4M3 planes hi = RN(g X), lo = RN(g X - hi) at a
@@ -138,7 +138,7 @@ typedef struct nsrgs_info {
 /* ---------------------------------------------------------------- sizes */
 
 /* Bytes of the packed buffer for (n, d, storage); 0 if the combination is not
- * supported (F32: any d <= 64; BF16: d <= 8 and d in {16, 32, 64}; FP8E4M3: d <= 4 and d in {16, 32, 64};
+ * supported (F32: any d <= 64; BF16: any d <= 64; FP8E4M3: d <= 4 and 8 < d <= 64;
  * DENSE_F32: any d <= 64; DENSE_BF16: d in {16, 32, 64}; BCSR_*: d <= 8, the
  * bound for fully observed data -- see nsrgs_bcsr_packed_bytes for the exact size). */
 size_t nsrgs_packed_bytes(int n, int d, int storage);
@@ -183,7 +183,7 @@ nsrgs_status nsrgs_pack_dense(const float* A, int n, int d, int storage, void* p
  * that d x d matrix), at most 3 times (info flags bit 6).  Restarts count
  * against max_iters; a basis that still fails after the last restart is
  * reported as not converged.  The tensor-core storages (NSRGS_DENSE_BF16, and
- * BF16 / FP8E4M3 at d in {16, 32, 64}) multiply a rounded V (bfloat16, or E4M3
+ * BF16 / FP8E4M3 at 8 < d <= 64) multiply a rounded V (bfloat16, or E4M3
  * hi + lo planes, about 2^-8 relative), which puts a floor under the residual,
  * typically 1e-4 .. 1e-3: there the passes also count as converged once the
  * residual is at most 1e-2 and no smaller than the previous pass's (info flags

@@ -75,10 +75,8 @@ cudaError_t tc_sym_prepare(int d, bool f8);
 cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const float* X, uint8_t* xt, float* Y,
                            Ctl* ctl, const int* skip, cudaStream_t st);
 
-// Tile-upper tensor-core storage: BF16 or FP8 at d in {16, 32, 64}.
-static bool tile_upper(int storage, int d) {
-  return (storage == NSRGS_BF16 || storage == NSRGS_FP8E4M3) && tc_sym_supported(d);
-}
+// Tile-upper tensor-core storage (tile_storage in common.cuh).
+static bool tile_upper(int storage, int d) { return tile_storage(storage, d); }
 bool fs_sym_supported(int d);
 long long fs_sym_bytes(int n, int d);
 long long fs_sym_xt_bytes(int n, int d);
@@ -141,10 +139,11 @@ static Workspace map_workspace(void* base, int n, int d) {
     // (or two sets of E4M3 hi / lo planes) for the tile-upper tensor-core stream,
     // float32 64-row tiles for the float32 tile stream
     long long a = fs_sym_xt_bytes(n, d);
+    const long long c = tc_sym8_xt_bytes(n, d);
+    a = a > c ? a : c;
     if (d >= 16) {
-      const long long b = (long long)d * dense_bf16_pitch(n, d) * 2, c = tc_sym8_xt_bytes(n, d);
+      const long long b = (long long)d * dense_bf16_pitch(n, d) * 2;
       a = a > b ? a : b;
-      a = a > c ? a : c;
     }
     w.XT = reinterpret_cast<__nv_bfloat16*>(take((size_t)a));
   }
@@ -190,17 +189,17 @@ static nsrgs_status check_A(const nsrgs_A* A, PanelGeom* g) {
     }
     return NSRGS_OK;
   }
-  NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
   if (tile_upper(A->storage, A->d)) {
-    NSRGS_CUDA_TRY(tc_sym_prepare(A->d, A->storage == NSRGS_FP8E4M3));
+    NSRGS_CUDA_TRY(tc_sym_prepare(A->d, tile_fp8(A->storage)));
     return NSRGS_OK;
   }
+  NSRGS_CHECK_ARG(A->storage >= NSRGS_F32 && A->storage <= NSRGS_FP8E4M3, "unknown storage");
   if (A->storage == NSRGS_F32 && fs_sym_supported(A->d)) {
     NSRGS_CUDA_TRY(fs_sym_prepare(A->d));
     return NSRGS_OK;
   }
   if (!make_panel_geom(A->n, A->d, A->storage, g)) {
-    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4 or d in {16, 32, 64}; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with any d <= 64, FP8 with d <= 4 or 8 < d <= 64; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   NSRGS_CUDA_TRY(stream_panel_prepare(*g));
@@ -224,7 +223,7 @@ static cudaError_t stream_AX(const nsrgs_A* A, const PanelGeom& g, const float* 
   if (A->storage == NSRGS_DENSE_F32) return stream_dense(A->packed, A->n, A->d, X, w.Y, skip, st);
   if (A->storage == NSRGS_DENSE_BF16) return tc_dense_product(A->packed, A->n, A->d, X, w.XT, w.Y, w.ctl, skip, st);
   if (tile_upper(A->storage, A->d))
-    return tc_sym_product(A->packed, A->n, A->d, A->storage == NSRGS_FP8E4M3, X, reinterpret_cast<uint8_t*>(w.XT),
+    return tc_sym_product(A->packed, A->n, A->d, tile_fp8(A->storage), X, reinterpret_cast<uint8_t*>(w.XT),
                           w.Y, w.ctl, skip, st);
   if (A->storage == NSRGS_F32 && fs_sym_supported(A->d))
     return fs_sym_product(A->packed, A->n, A->d, X, reinterpret_cast<float*>(w.XT), w.Y, w.ctl, skip, st);
@@ -428,8 +427,7 @@ size_t nsrgs_packed_bytes(int n, int d, int storage) {
   if (storage == NSRGS_DENSE_F32) return (size_t)n * d * (size_t)dense_pitch(n, d) * sizeof(float);
   if (storage == NSRGS_DENSE_BF16)
     return tc_dense_supported(d) ? (size_t)n * d * (size_t)dense_bf16_pitch(n, d) * 2 : 0;
-  if (storage == NSRGS_BF16 && tc_sym_supported(d)) return (size_t)tc_sym_bytes(n, d);
-  if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) return (size_t)tc_sym8_bytes(n, d);
+  if (tile_upper(storage, d)) return (size_t)(tile_fp8(storage) ? tc_sym8_bytes(n, d) : tc_sym_bytes(n, d));
   if (storage == NSRGS_F32 && fs_sym_supported(d)) return (size_t)fs_sym_bytes(n, d);
   if (bcsr_storage(storage)) return d <= 8 ? (size_t)bcsr_bytes(n, d, storage, (long long)n * (n - 1)) : 0;
   PanelGeom g;

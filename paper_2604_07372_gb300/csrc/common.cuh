@@ -76,6 +76,13 @@ __host__ __device__ constexpr double spec_floor_max(int count_pass) {
   return count_pass == 2 ? kSpecFloorMax : (count_pass == 3 ? kSpecFloorMaxF32 : 0.0);
 }
 
+// Storages held in the tile-upper tensor-core layout: BF16 and FP8E4M3 above d = 8
+// (the CUDA-core panels at d <= 8; FP8 panels stop at d = 4).
+__host__ __device__ inline bool tile_storage(int storage, int d) {
+  return (storage == NSRGS_BF16 || storage == NSRGS_FP8E4M3) && d > 8 && d <= 64;
+}
+__host__ __device__ inline bool tile_fp8(int storage) { return storage == NSRGS_FP8E4M3; }
+
 // Restarts the spectral start may take with a larger shift before it gives up
 // (then it reports the subspace as not converged).
 constexpr int kSpecMaxRestarts = 3;

@@ -332,14 +332,15 @@ cudaError_t launch_norm2(const void* packed, int n, int d, int storage, const Pa
     norm2_bcsr_kernel<float><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(packed), d, o, ctl);
   } else if (storage == NSRGS_BCSR_BF16) {
     norm2_bcsr_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(packed), d, o, ctl);
-  } else if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
+  } else if (tile_storage(storage, d) && !tile_fp8(storage)) {
     // tile-upper layout: the upper triangle once, everything else zero
     norm2_flat_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(packed), tc_sym_bytes(n, d) / 2, 2.0,
                                             o, ctl);
-  } else if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) {
+  } else if (tile_storage(storage, d)) {
     const uint8_t* p = reinterpret_cast<const uint8_t*>(packed);
-    if (d == 64) norm2_ts8_kernel<ts_strip_rows(64, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
-    else if (d == 32) norm2_ts8_kernel<ts_strip_rows(32, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    const int w = ts_width(d);  // the visiting order follows the tile width
+    if (w == 64) norm2_ts8_kernel<ts_strip_rows(64, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
+    else if (w == 32) norm2_ts8_kernel<ts_strip_rows(32, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
     else norm2_ts8_kernel<ts_strip_rows(16, true)><<<grid, 256, 0, st>>>(p, n, d, o, ctl);
   } else if (storage == NSRGS_F32 && fs_sym_supported(d)) {
     // float32 tile-upper layout: the upper triangle once, everything else zero

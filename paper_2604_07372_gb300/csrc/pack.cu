@@ -186,11 +186,11 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
     return NSRGS_OK;
   }
   if constexpr (!std::is_same_v<Src, SeAugSrc>) {  // the SE(d) form uses panels only
-    if (storage == NSRGS_BF16 && tc_sym_supported(d)) {
+    if (tile_storage(storage, d) && !tile_fp8(storage)) {
       NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, false, packed, st));
       return NSRGS_OK;
     }
-    if (storage == NSRGS_FP8E4M3 && tc_sym_supported(d)) {  // block-row scales first, behind the tiles
+    if (tile_storage(storage, d)) {  // FP8: block-row scales first, behind the tiles
       fp8_scale_kernel<<<n, 256, 0, st>>>(src, n, d, (float*)((uint8_t*)packed + tc_sym8_scale_offset(n, d)));
       NSRGS_CUDA_TRY(cudaGetLastError());
       NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, true, packed, st));
@@ -203,7 +203,7 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
   }
   PanelGeom g;
   if (!make_panel_geom(n, d, storage, &g)) {
-    set_error("symmetric storage needs F32 (any d <= 64), BF16 with d <= 8 or d in {16, 32, 64}, or FP8 with d <= 4 or d in {16, 32, 64}; use NSRGS_DENSE_F32");
+    set_error("symmetric storage needs F32 (any d <= 64), BF16 with any d <= 64, FP8 with d <= 4 or 8 < d <= 64; use NSRGS_DENSE_F32");
     return NSRGS_ERR_UNSUPPORTED;
   }
   std::vector<long long> tab;

@@ -1,6 +1,9 @@
 // Y = A_off X on the tensor cores reading only the upper triangle of A, for
-// d in {16, 32, 64} with A stored in bfloat16 (NSRGS_BF16 at these d) or in
-// FP8-E4M3 with one float32 scale per block row (NSRGS_FP8E4M3 at these d).
+// 8 < d <= 64 with A stored in bfloat16 (NSRGS_BF16 at these d) or in FP8-E4M3
+// with one float32 scale per block row (NSRGS_FP8E4M3 at these d).  The MMA's N
+// is the tile width ts_width(d) (16, 32 or 64); X^T rows past d are zero, and
+// where d does not divide 128 blocks straddle tiles (a stored tile keeps the
+// elements with block(row) < block(col), so nothing needs a special case).
 //
 // Layout ("tile-upper"): the nd x nd matrix is cut into 128 x 128 tiles; tile
 // (I, J) is stored for J >= I only, in the order the kernel visits them (groups
@@ -113,6 +116,7 @@ struct TsArgs {
   Ctl* ctl;
   int rows;              // n * d
   int NT;
+  int D;                 // block size d <= N (Y and X rows hold d floats; X^T rows past d are zero)
 };
 
 // FP8 operand scale: g = 2^(7 - floor(log2 m)) puts m = max |value| in [128, 256)
@@ -423,9 +427,18 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_sym_kernel(const __grid_cons
         for (int c = 0; c < N; ++c) v[c] += v[N + c];  // A X_hi + A X_lo
       }
       if constexpr (F8) {
-        const float m = row_product ? (row < a.rows ? a.rscale[row / N] : 0.f) * inv_gr : inv_gc;
+        const float m = row_product ? (row < a.rows ? a.rscale[row / a.D] : 0.f) * inv_gr : inv_gc;
 #pragma unroll
         for (int c = 0; c < N; ++c) v[c] *= m;
+      }
+      if (a.D != N) {  // d < N: rows of d floats, not 16-byte multiples; element-wise adds
+        if (row < a.rows) {
+          float* y = a.Y + (long long)row * a.D;
+#pragma unroll
+          for (int c = 0; c < N; ++c)
+            if (c < a.D) red_add_f32(y + c, v[c]);
+        }
+        return true;
       }
       if (lane == 0) bulk_wait_read_all();  // the previous drain's boxes have left the staging
       __syncwarp();
@@ -544,26 +557,27 @@ __global__ void __launch_bounds__(256) ts_pack_kernel(Src src, int NT, int rows,
   }
 }
 
-// X^T tiles: element (n, k) of tile J is X[128 J + k][n] in bfloat16 (zero past n*d rows).
+// X^T tiles: element (nn, k) of tile J is X[128 J + k][nn] in bfloat16 (zero past n*d
+// rows and for nn >= D, the block size, up to the tile width N).
 __global__ void __launch_bounds__(256) ts_xt_kernel(const float* __restrict__ X, uint8_t* __restrict__ xt, int rows,
-                                                   int D, int NT, const int* skip) {
+                                                   int D, int N, int NT, const int* skip) {
   if (*skip) return;
-  const long long chunks = (long long)NT * D * (kTsTile / 8);
+  const long long chunks = (long long)NT * N * (kTsTile / 8);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < chunks;
        e += (long long)gridDim.x * blockDim.x) {
-    const int J = (int)(e / (D * (kTsTile / 8)));
-    const int rem = (int)(e % (D * (kTsTile / 8)));
+    const int J = (int)(e / (N * (kTsTile / 8)));
+    const int rem = (int)(e % (N * (kTsTile / 8)));
     const int nn = rem / (kTsTile / 8), k0 = (rem % (kTsTile / 8)) * 8;
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const long long r0 = (long long)J * kTsTile + k0 + 2 * k;
-      const float a = r0 < rows ? X[r0 * D + nn] : 0.f;
-      const float b = r0 + 1 < rows ? X[(r0 + 1) * D + nn] : 0.f;
+      const float a = (nn < D && r0 < rows) ? X[r0 * D + nn] : 0.f;
+      const float b = (nn < D && r0 + 1 < rows) ? X[(r0 + 1) * D + nn] : 0.f;
       w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
     }
-    *reinterpret_cast<uint4*>(xt + (long long)J * D * 256 + ts_swz(nn, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(xt + (long long)J * N * 256 + ts_swz(nn, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -599,41 +613,43 @@ __device__ __forceinline__ void ts8_split(float v, uint32_t& hi, uint32_t& lo, i
 
 // FP8 operands, pass 2: per 128-row tile J, the row operand (g_r X) and the
 // column operand (g_c s_i X_i) as hi and lo E4M3 planes of N x 128 bytes each
-// (element (n, k) = row 128 J + k, column n; zero past n*d rows).
+// (element (nn, k) = row 128 J + k, column nn; zero past n*d rows and for nn >= D).
 __global__ void __launch_bounds__(256) ts8_xt_kernel(const float* __restrict__ X, const float* __restrict__ scale,
                                                     uint8_t* __restrict__ xt, uint8_t* __restrict__ xc, int rows,
-                                                    int D, int NT, const unsigned* mx, const int* skip) {
+                                                    int D, int N, int NT, const unsigned* mx, const int* skip) {
   if (*skip) return;
   const float gr = ts8_pow2(mx[0], false), gc = ts8_pow2(mx[1], false);
-  const long long chunks = (long long)NT * 8 * D;  // (tile, 16-row chunk, column), column fastest
+  const long long chunks = (long long)NT * 8 * N;  // (tile, 16-row chunk, column), column fastest
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < chunks;
        e += (long long)gridDim.x * blockDim.x) {
-    const int nn = (int)(e % D);
-    const long long tk = e / D;
+    const int nn = (int)(e % N);
+    const long long tk = e / N;
     const int J = (int)(tk >> 3), k0 = (int)(tk & 7) * 16;
     uint32_t rh[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0}, cl[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const long long row = (long long)J * kTsTile + k0 + k;
       float x = 0.f, sx = 0.f;
-      if (row < rows) {
+      if (row < rows && nn < D) {
         x = X[row * D + nn];
         sx = x * scale[row / D];
       }
       ts8_split(x * gr, rh[k >> 2], rl[k >> 2], 8 * (k & 3));
       ts8_split(sx * gc, ch[k >> 2], cl[k >> 2], 8 * (k & 3));
     }
-    const long long base = (long long)J * D * 256;
+    const long long base = (long long)J * N * 256;
     const int o = ts8_swz(nn, k0);
     *reinterpret_cast<uint4*>(xt + base + o) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-    *reinterpret_cast<uint4*>(xt + base + D * 128 + o) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<uint4*>(xt + base + N * 128 + o) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
     *reinterpret_cast<uint4*>(xc + base + o) = make_uint4(ch[0], ch[1], ch[2], ch[3]);
-    *reinterpret_cast<uint4*>(xc + base + D * 128 + o) = make_uint4(cl[0], cl[1], cl[2], cl[3]);
+    *reinterpret_cast<uint4*>(xc + base + N * 128 + o) = make_uint4(cl[0], cl[1], cl[2], cl[3]);
   }
 }
 
 // ---------------------------------------------------------------- host
-bool tc_sym_supported(int d) { return d == 16 || d == 32 || d == 64; }
+// Block sizes the tile-upper layout takes: any d <= 64 (tile width ts_width(d); BF16
+// and FP8 storage use it above d = 8).
+bool tc_sym_supported(int d) { return d >= 1 && d <= 64; }
 
 long long tc_sym_bytes(int n, int d) { return ts_tiles(ts_tile_rows(n, d)) * (long long)kTsTileBytes; }
 
@@ -642,7 +658,7 @@ long long tc_sym8_scale_offset(int n, int d) { return ts8_scale_offset(n, d); }
 long long tc_sym8_bytes(int n, int d) { return ts8_scale_offset(n, d) + ((long long)n * 4 + 15) / 16 * 16; }
 
 // Bytes of the swizzled X^T tiles for (n, d): bfloat16 one set, FP8 two (row and column operands).
-long long tc_sym_xt_bytes(int n, int d) { return (long long)ts_tile_rows(n, d) * d * 256; }
+long long tc_sym_xt_bytes(int n, int d) { return (long long)ts_tile_rows(n, d) * ts_width(d) * 256; }
 long long tc_sym8_xt_bytes(int n, int d) { return 2 * tc_sym_xt_bytes(n, d); }
 
 static PFN_cuTensorMapEncodeTiled_v12000 ts_encode_fn() {
@@ -678,9 +694,11 @@ template <int N, bool F8>
 static cudaError_t launch_ts(const TsArgs& a, cudaStream_t st, bool prepare) {
   using C = TsCfg<N, F8>;
   if (prepare) return cudaFuncSetAttribute(tc_sym_kernel<N, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  CUtensorMap tm;
-  const cudaError_t e = y_map<N, F8>(&tm, a.Y, a.rows);
-  if (e != cudaSuccess) return e;
+  CUtensorMap tm{};  // Y as a TMA target when its rows are the tile width (d = N); unused otherwise
+  if (a.D == N) {
+    const cudaError_t e = y_map<N, F8>(&tm, a.Y, a.rows);
+    if (e != cudaSuccess) return e;
+  }
   const long long total = ts_tiles(a.NT);
   const int grid = (int)std::min<long long>(total, num_sms());
   tc_sym_kernel<N, F8><<<grid, kTsThreads, C::SMEM, st>>>(tm, a);
@@ -688,7 +706,7 @@ static cudaError_t launch_ts(const TsArgs& a, cudaStream_t st, bool prepare) {
 }
 
 static cudaError_t launch_ts_any(int d, bool f8, const TsArgs& a, cudaStream_t st, bool prepare) {
-  switch (d) {
+  switch (ts_width(d)) {
     case 16: return f8 ? launch_ts<16, true>(a, st, prepare) : launch_ts<16, false>(a, st, prepare);
     case 32: return f8 ? launch_ts<32, true>(a, st, prepare) : launch_ts<32, false>(a, st, prepare);
     case 64: return f8 ? launch_ts<64, true>(a, st, prepare) : launch_ts<64, false>(a, st, prepare);
@@ -703,15 +721,15 @@ cudaError_t tc_sym_prepare(int d, bool f8) {
 
 cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const float* X, uint8_t* xt, float* Y,
                            Ctl* ctl, const int* skip, cudaStream_t st) {
-  const int NT = ts_tile_rows(n, d);
+  const int NT = ts_tile_rows(n, d), N = ts_width(d);
   const uint8_t* tiles = reinterpret_cast<const uint8_t*>(packed);
   if (!f8) {
-    const long long chunks = (long long)NT * d * (kTsTile / 8);
+    const long long chunks = (long long)NT * N * (kTsTile / 8);
     const int g = (int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms());
-    ts_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, d, NT, skip);
+    ts_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, d, N, NT, skip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    TsArgs a{tiles, xt, xt, nullptr, Y, skip, ctl, n * d, NT};
+    TsArgs a{tiles, xt, xt, nullptr, Y, skip, ctl, n * d, NT, d};
     return launch_ts_any(d, false, a, st, false);
   }
   const float* scale = reinterpret_cast<const float*>(tiles + ts8_scale_offset(n, d));
@@ -722,11 +740,11 @@ cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const floa
   ts8_xmax_kernel<<<(int)std::min<long long>((count + 255) / 256, 2LL * num_sms()), 256, 0, st>>>(
       X, scale, n * d, d, ctl->ts8_max, skip);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long chunks = (long long)NT * 8 * d;
+  const long long chunks = (long long)NT * 8 * N;
   ts8_xt_kernel<<<(int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms()), 256, 0, st>>>(
-      X, scale, xt, xc, n * d, d, NT, ctl->ts8_max, skip);
+      X, scale, xt, xc, n * d, d, N, NT, ctl->ts8_max, skip);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  TsArgs a{tiles, xt, xc, scale, Y, skip, ctl, n * d, NT};
+  TsArgs a{tiles, xt, xc, scale, Y, skip, ctl, n * d, NT, d};
   return launch_ts_any(d, true, a, st, false);
 }
 
@@ -743,7 +761,7 @@ cudaError_t tc_sym_pack(Src src, int n, int d, bool f8, void* packed, cudaStream
     ts_pack_kernel<ts_strip_rows(DD, true), true><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);   \
   else                                                                                           \
     ts_pack_kernel<ts_strip_rows(DD, false), false><<<g, 256, 0, st>>>(src, NT, rows, d, scale, out);
-  switch (d) {
+  switch (ts_width(d)) {  // the visiting order follows the tile width
     case 16: NSRGS_TS_PACK(16) break;
     case 32: NSRGS_TS_PACK(32) break;
     case 64: NSRGS_TS_PACK(64) break;

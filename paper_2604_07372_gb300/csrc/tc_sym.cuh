@@ -14,7 +14,11 @@ constexpr int kTs8TileBytes = kTsTile * kTsTile;     // FP8-E4M3 tile: 16 KB
 __host__ __device__ inline int ts_tile_rows(int n, int d) { return (int)(((long long)n * d + kTsTile - 1) / kTsTile); }
 __host__ __device__ inline long long ts_tiles(int NT) { return (long long)NT * (NT + 1) / 2; }
 
-// Row tiles per strip (and per group) of the processing order: as many as the
+// Tile width (MMA N) of the tensor-core stream for block size d <= 64: X^T tiles
+// carry N rows, the ones past d zero.
+__host__ __device__ constexpr int ts_width(int d) { return d <= 16 ? 16 : (d <= 32 ? 32 : 64); }
+
+// Row tiles per strip (and per group) of the processing order (by tile width): as many as the
 // stream's TMEM holds, R row accumulators plus two column buffers of 512
 // columns (FP8 at d <= 32 keeps its hi and lo products side by side: 2d each).
 __host__ __device__ constexpr int ts_strip_rows(int d, bool f8) { return d == 64 ? 4 : (f8 && d == 32 ? 6 : 8); }

@@ -7,10 +7,16 @@ import numpy as np
 T = 128
 
 
+def width(d):
+    """Tile width (the MMA's N) for block size d: d rounded up to 16, 32 or 64."""
+    return 16 if d <= 16 else (32 if d <= 32 else 64)
+
+
 def strip_rows(d, f8=False):
     """Row tiles per strip / group of the processing order (FP8 at d = 32 keeps
-    its hi and lo accumulators side by side, so fewer fit in TMEM)."""
-    return 4 if d == 64 else (6 if f8 and d == 32 else 8)
+    its hi and lo accumulators side by side, so fewer fit in TMEM); by tile width."""
+    w = width(d)
+    return 4 if w == 64 else (6 if f8 and w == 32 else 8)
 
 
 def swz(r, c):

@@ -40,11 +40,15 @@ def test_every_declared_symbol_is_exported(L):
 def test_version_and_sizes(L):
     assert "sm_103a" in L.nsrgs_version()
     # symmetric layouts: F32 any d <= 64 (panels up to 8, float32 tiles above), BF16 d <= 8
-    # and d in {16, 32, 64}, FP8 d <= 4 and d in {16, 32, 64}; the dense layout any d <= 64
+    # and 8 < d <= 64 (tiles), FP8 d <= 4 and 8 < d <= 64; the dense layout any d <= 64
     assert L.nsrgs_packed_bytes(200, 3, L.F32) > 0
     assert L.nsrgs_packed_bytes(200, 8, L.F32) > 0 and L.nsrgs_packed_bytes(200, 5, L.BF16) > 0
     assert L.nsrgs_packed_bytes(200, 9, L.F32) > 0 and L.nsrgs_packed_bytes(200, 64, L.F32) > 0
-    assert L.nsrgs_packed_bytes(200, 65, L.F32) == 0 and L.nsrgs_packed_bytes(200, 9, L.BF16) == 0
+    assert L.nsrgs_packed_bytes(200, 65, L.F32) == 0 and L.nsrgs_packed_bytes(200, 65, L.BF16) == 0
+    # BF16 / FP8 above d = 8: the tile-upper layout at every d (tile width 16, 32 or 64)
+    NT = -(-(200 * 9) // 128)
+    assert L.nsrgs_packed_bytes(200, 9, L.BF16) == NT * (NT + 1) // 2 * 32768
+    assert L.nsrgs_packed_bytes(200, 25, L.FP8E4M3) > 0 and L.nsrgs_packed_bytes(200, 8, L.FP8E4M3) == 0
     assert L.nsrgs_packed_bytes(200, 5, L.FP8E4M3) == 0 and L.nsrgs_packed_bytes(200, 8, L.FP8E4M3) == 0
     assert L.nsrgs_packed_bytes(200, 16, L.FP8E4M3) * 2 < L.nsrgs_packed_bytes(200, 16, L.BF16) + 4096
     # block-sparse rows: the bound for fully observed data, both triangles, d <= 8

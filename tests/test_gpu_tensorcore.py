@@ -54,6 +54,28 @@ def test_tensor_core_product(P, n, d, storage):
     assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-6), np.max(np.abs(got - ref) / (scale + 1e-6))
 
 
+# BF16 above d = 8 at block sizes other than the tile width: X^T rows past d are
+# zero, blocks straddle the 128-row tiles, Y is added element-wise
+ODD_D_CASES = [(30, 9), (7, 13), (20, 25), (11, 40), (9, 48), (3, 63)]
+
+
+@pytest.mark.parametrize("n,d", ODD_D_CASES)
+def test_tile_upper_product_at_any_d(P, n, d):
+    inst = synth.make_instance(n, d, 0.5, seed=n + 7 * d, dtype=np.float32)
+    A = inst.dense()
+    for i in range(n):
+        A[i * d : (i + 1) * d, i * d : (i + 1) * d] = 0.0
+    X = np.random.default_rng(d).standard_normal((n * d, d)).astype(np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BF16)
+    Y = P.nsrgs_product(pa, torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    Ab, Xb = bf16_round(A), bf16_round(X)
+    ref = Ab @ Xb
+    scale = np.abs(Ab) @ np.abs(Xb)
+    got = Y.double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-6), np.max(np.abs(got - ref) / (scale + 1e-6))
+
+
 @pytest.mark.parametrize("storage", ["dense_bf16", "bf16"])
 @pytest.mark.parametrize("n,d", [(200, 16), (80, 32), (40, 64)])
 def test_tensor_core_solve_within_one_percent(P, n, d, storage):
@@ -116,3 +138,18 @@ def test_tensor_core_spectral_start_stops_at_its_floor(P, n, d, storage):
     X0o, _ = O.spectral_init(A, n, d)
     dist = O.dF(X0.double().cpu().numpy(), X0o, d) / math.sqrt(n * d)
     assert dist <= 4.0 * sin_bound + 1e-5, (dist, sin_bound, res, info.as_dict())
+
+
+@pytest.mark.parametrize("n,d", [(100, 25), (60, 12)])
+def test_tile_upper_solve_at_the_papers_d(P, n, d):
+    """d = 25 (the setting of §4.1's Table 1) and d = 12 on the BF16 tile stream:
+    final d_F(X, Z) within 1% of the FP64 oracle's."""
+    T, K = 40, 2
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=3 * d, dtype=np.float32)
+    Xo, _ = O.nsrgs(inst.dense(), n, d, 1.0 / n, T, K)
+    Xb, info = P.nsrgs_solve(P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BF16), 1.0 / n, T, K)
+    torch.cuda.synchronize()
+    Z = inst.Zstack()
+    eo, eb = O.dF(Xo, Z, d), O.dF(Xb.double().cpu().numpy(), Z, d)
+    assert info.iters == T and not (info.flags & 4), info.as_dict()
+    assert abs(eb - eo) / eo <= 0.01, (eo, eb)

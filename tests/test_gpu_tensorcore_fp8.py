@@ -90,7 +90,8 @@ def pack(P, inst):
     return P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), inst.n, inst.d, P.FP8E4M3)
 
 
-@pytest.mark.parametrize("n,d", [(2, 16), (9, 16), (300, 16), (20, 32), (130, 32), (3, 64), (17, 64)])
+@pytest.mark.parametrize("n,d", [(2, 16), (9, 16), (300, 16), (20, 32), (130, 32), (3, 64), (17, 64), (20, 25),
+                                 (9, 12), (5, 48)])
 def test_fp8_tiles_match_the_host_quantiser(P, n, d):
     inst = synth.make_instance(n, d, 0.5, seed=4 * n + d, dtype=np.float32)
     pa = pack(P, inst)
@@ -120,7 +121,8 @@ def test_fp8_tiles_match_the_host_quantiser(P, n, d):
             raise AssertionError(f"tile {t} = ({I}, {J}): bytes {bad} got {got[bad]} want {want[bad]}")
 
 
-PRODUCT_CASES = [(2, 16), (20, 16), (8, 16), (300, 16), (1000, 16), (9, 32), (130, 32), (5, 64), (70, 64), (17, 64)]
+PRODUCT_CASES = [(2, 16), (20, 16), (8, 16), (300, 16), (1000, 16), (9, 32), (130, 32), (5, 64), (70, 64), (17, 64),
+                 (30, 9), (20, 25), (9, 48), (3, 63)]
 
 
 @pytest.mark.parametrize("n,d", PRODUCT_CASES)
@@ -154,7 +156,7 @@ def test_fp8_product_is_exact_under_power_of_two_scaling(P, n, d):
     assert torch.count_nonzero(Yz).item() == 0
 
 
-@pytest.mark.parametrize("n,d", [(200, 16), (80, 32), (40, 64)])
+@pytest.mark.parametrize("n,d", [(200, 16), (80, 32), (40, 64), (100, 25)])
 def test_fp8_solve_within_one_percent_of_the_oracle(P, n, d):
     """Final d_F(X, Z) of an FP8 tile-upper solve within 1% of the FP64 oracle's (unrounded A)."""
     T_, K = 40, 2
