@@ -320,8 +320,11 @@ nsrgs_status nsrgs_solve_ex(const nsrgs_A* A, float eta, int T, int K, const nsr
  *   G_i = X_i (X^T X - X_i^T X_i) - sum_{j != i} A_ij X_j
  *   F_i = X_i - eta (G_i - sym(G_i X_i^T) X_i)
  *   X_i^{t+1} = S_K(F_i),  S <- (3I - S S^T) S / 2   (Algorithm 1 by rows).
- * With p = d and X_i orthogonal these are Algorithm 2's steps exactly.  A must
- * be NSRGS_DENSE_F32 (the product runs with p columns of X).  X0 (device,
+ * With p = d and X_i orthogonal these are Algorithm 2's steps exactly.  A is
+ * NSRGS_DENSE_F32 (any d), or for d > 8 the symmetric tile layouts NSRGS_F32
+ * (float32 tiles) and NSRGS_BF16 (tensor-core tiles, X rounded to bfloat16 for
+ * the product; p must fall in the same tile-width class as d: both <= 32 or both
+ * > 32): the product runs with p columns of X, the tiles read once.  X0 (device,
  * nd x p, row-orthonormal blocks, e.g. [X_i^0, 0] from the O(d) start) is
  * required; X (device, nd x p) receives the last iterate.  tol > 0 stops after
  * the first iteration with ||X^{t+1} - X^t||_F / sqrt(ndp) < tol.  info: iters,

@@ -435,18 +435,29 @@ cudaError_t fs_sym_prepare(int d) {
   return launch_fs_any(d, a, 0, true);
 }
 
-cudaError_t fs_sym_product(const void* packed, int n, int d, const float* X, float* xt, float* Y, Ctl* ctl,
-                           const int* skip, cudaStream_t st) {
+// Y = A_off X for A packed with block size d and X of `width` columns (width = d
+// in Algorithm 2; the Stiefel form's p >= d): the tiles hold elements, so only
+// the number of rows (n d) and the width of X enter the product.
+cudaError_t fs_sym_product_w(const void* packed, int n, int d, int width, const float* X, float* xt, float* Y,
+                             Ctl* ctl, const int* skip, cudaStream_t st) {
   const int NT = fs_nt(n, d);
-  const int DP = fs_dp(d);
+  const int DP = fs_dp(width);
   const long long count = (long long)NT * DP * kFsT;
   const int g = (int)std::min<long long>((count + 255) / 256, 4LL * num_sms());
-  fs_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, d, DP, NT, skip);
+  fs_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, width, DP, NT, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  FsArgs a{reinterpret_cast<const uint8_t*>(packed), xt, Y, skip, ctl, n * d, d, NT};
-  return launch_fs_any(d, a, st, false);
+  FsArgs a{reinterpret_cast<const uint8_t*>(packed), xt, Y, skip, ctl, n * d, width, NT};
+  return launch_fs_any(width, a, st, false);
 }
+
+cudaError_t fs_sym_product(const void* packed, int n, int d, const float* X, float* xt, float* Y, Ctl* ctl,
+                           const int* skip, cudaStream_t st) {
+  return fs_sym_product_w(packed, n, d, d, X, xt, Y, ctl, skip, st);
+}
+
+// Bytes of the X^T tiles of fs_sym_product_w.
+long long fs_sym_xt_bytes_w(int n, int d, int width) { return (long long)fs_nt(n, d) * fs_dp(width) * kFsT * 4; }
 
 template <class Src>
 cudaError_t fs_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st) {

@@ -6,8 +6,10 @@
 //   G_i = X_i (C - X_i^T X_i) - Y_i        (with X_j in O(d): (n-1) X_i - Y_i)
 //   P_i = G_i - sym(G_i X_i^T) X_i          (tangent space: H X_i^T + X_i H^T = 0)
 //   F_i = X_i - eta P_i,   S <- (3I - S S^T) S / 2, K times (Algorithm 1 by rows).
-// With p = d every step is Algorithm 2's.  A is the dense float32 layout (the
-// product's X has p columns); the d x p work is one CTA per block in shared memory.
+// With p = d every step is Algorithm 2's.  A is the dense float32 layout, or for
+// d > 8 a symmetric tile layout (float32 or bfloat16 tiles, read once per
+// product); the product's X has p columns.  The d x p work is one CTA per block
+// in shared memory.
 #include <math.h>
 #include <string.h>
 
@@ -17,6 +19,16 @@ namespace nsrgs {
 
 cudaError_t stream_dense_width(const void* packed, int n, int d, int width, const float* X, float* Y,
                                const int* skip, cudaStream_t st);
+cudaError_t fs_sym_product_w(const void* packed, int n, int d, int width, const float* X, float* xt, float* Y,
+                             Ctl* ctl, const int* skip, cudaStream_t st);
+long long fs_sym_xt_bytes_w(int n, int d, int width);
+bool fs_sym_supported(int d);
+cudaError_t fs_sym_prepare(int d);
+cudaError_t tc_sym_product_w(const void* packed, int n, int d, int width, const float* X, uint8_t* xt, float* Y,
+                             Ctl* ctl, const int* skip, cudaStream_t st);
+long long tc_sym_xt_bytes_w(int n, int d, int width);
+bool tc_sym_width_ok(int d, int width);
+cudaError_t tc_sym_prepare(int d, bool f8);
 long long dense_pitch(int n, int d);
 int reduce_grid(long long rows);
 
@@ -179,6 +191,7 @@ struct StiefelWs {
   float* Y;
   double* C;
   double* partials;
+  void* XT;  // d > 8: X^T tiles of the symmetric products
   size_t bytes;
 };
 
@@ -200,6 +213,10 @@ static StiefelWs map_stiefel(void* base, int n, int d, int p) {
   w.Y = reinterpret_cast<float*>(take(vec));
   w.C = reinterpret_cast<double*>(take((size_t)p * p * sizeof(double)));
   w.partials = reinterpret_cast<double*>(take((size_t)kStGramGrid * p * p * sizeof(double)));
+  if (d > 8) {
+    const long long a = fs_sym_xt_bytes_w(n, d, p), c = tc_sym_xt_bytes_w(n, d, p);
+    w.XT = take((size_t)(a > c ? a : c));
+  }
   w.bytes = off;
   return w;
 }
@@ -219,10 +236,15 @@ extern "C" nsrgs_status nsrgs_stiefel_solve(const nsrgs_A* A, int p, float eta, 
                                             const float* X0, float* X, nsrgs_info* info, void* ws, size_t ws_bytes,
                                             void* stv) {
   NSRGS_CHECK_ARG(A && A->packed && X0 && X, "null argument");
-  NSRGS_CHECK_ARG(A->storage == NSRGS_DENSE_F32, "the Stiefel form streams NSRGS_DENSE_F32");
   const int n = A->n, d = A->d;
+  const bool sym_f32 = A->storage == NSRGS_F32 && d > 8 && fs_sym_supported(d);
+  const bool sym_bf16 = A->storage == NSRGS_BF16 && d > 8 && d <= 64;
+  NSRGS_CHECK_ARG(A->storage == NSRGS_DENSE_F32 || sym_f32 || sym_bf16,
+                  "the Stiefel form streams NSRGS_DENSE_F32, or NSRGS_F32 / NSRGS_BF16 tiles for d > 8");
   NSRGS_CHECK_ARG(n >= 2 && d >= 1 && d <= 64 && (long long)n * d <= (1LL << 24), "n, d out of range");
   NSRGS_CHECK_ARG(p >= d && p <= 64, "need d <= p <= 64");
+  NSRGS_CHECK_ARG(!sym_bf16 || tc_sym_width_ok(d, p),
+                  "NSRGS_BF16 tiles need d and p in the same tile-width class (both <= 32 or both > 32)");
   NSRGS_CHECK_ARG(eta > 0.f && isfinite(eta), "eta must be finite and > 0");
   NSRGS_CHECK_ARG(T >= 0 && T <= 100000 && K >= 0 && K <= 64, "T in [0, 100000], K in [0, 64]");
   NSRGS_CHECK_ARG(tol >= 0.0 && isfinite(tol), "tol must be finite and >= 0");
@@ -236,13 +258,26 @@ extern "C" nsrgs_status nsrgs_stiefel_solve(const nsrgs_A* A, int p, float eta, 
   const StiefelWs w = map_stiefel(ws, n, d, p);
   const size_t smem = stiefel_smem(d, p);
   NSRGS_CUDA_TRY(cudaFuncSetAttribute(stiefel_epilogue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (sym_f32) NSRGS_CUDA_TRY(fs_sym_prepare(p));
+  if (sym_bf16) NSRGS_CUDA_TRY(tc_sym_prepare(p, false));
+  const size_t ybytes = (size_t)n * d * p * sizeof(float) + 64 * p * sizeof(float);
   const long long count = (long long)n * d * p;
   NSRGS_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
   NSRGS_CUDA_TRY(cudaMemcpyAsync(w.X[0], X0, count * sizeof(float), cudaMemcpyDeviceToDevice, st));
   for (int t = 0; t < T; ++t) {
     const float* Xt = w.X[t & 1];
     float* Xn = w.X[(t + 1) & 1];
-    NSRGS_CUDA_TRY(stream_dense_width(A->packed, n, d, p, Xt, w.Y, &w.ctl->stop, st));
+    if (sym_f32 || sym_bf16) {  // the tile streams add into Y
+      NSRGS_CUDA_TRY(cudaMemsetAsync(w.Y, 0, ybytes, st));
+      if (sym_f32)
+        NSRGS_CUDA_TRY(fs_sym_product_w(A->packed, n, d, p, Xt, reinterpret_cast<float*>(w.XT), w.Y, w.ctl,
+                                        &w.ctl->stop, st));
+      else
+        NSRGS_CUDA_TRY(tc_sym_product_w(A->packed, n, d, p, Xt, reinterpret_cast<uint8_t*>(w.XT), w.Y, w.ctl,
+                                        &w.ctl->stop, st));
+    } else {
+      NSRGS_CUDA_TRY(stream_dense_width(A->packed, n, d, p, Xt, w.Y, &w.ctl->stop, st));
+    }
     stiefel_gram_kernel<<<kStGramGrid, kStGramThreads, 0, st>>>(Xt, (long long)n * d, p, w.partials, w.C, w.ctl);
     NSRGS_CUDA_TRY(cudaGetLastError());
     stiefel_epilogue_kernel<<<n, 256, smem, st>>>(Xt, w.Y, w.C, Xn, n, d, p, eta, K, tol, w.ctl);

@@ -719,6 +719,27 @@ cudaError_t tc_sym_prepare(int d, bool f8) {
   return launch_ts_any(d, f8, a, 0, true);
 }
 
+// BF16 tiles packed with block size d against X of `width` columns (the Stiefel
+// form's p >= d); the visiting order's strip length must be the same for the
+// two tile widths (tc_sym_width_ok), since it is part of the packed layout.
+bool tc_sym_width_ok(int d, int width) {
+  return width >= d && width <= 64 && ts_strip_rows(ts_width(width), false) == ts_strip_rows(ts_width(d), false);
+}
+long long tc_sym_xt_bytes_w(int n, int d, int width) { return (long long)ts_tile_rows(n, d) * ts_width(width) * 256; }
+
+cudaError_t tc_sym_product_w(const void* packed, int n, int d, int width, const float* X, uint8_t* xt, float* Y,
+                             Ctl* ctl, const int* skip, cudaStream_t st) {
+  if (!tc_sym_width_ok(d, width)) return cudaErrorInvalidValue;
+  const int NT = ts_tile_rows(n, d), N = ts_width(width);
+  const long long chunks = (long long)NT * N * (kTsTile / 8);
+  const int g = (int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms());
+  ts_xt_kernel<<<g, 256, 0, st>>>(X, xt, n * d, width, N, NT, skip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TsArgs a{reinterpret_cast<const uint8_t*>(packed), xt, xt, nullptr, Y, skip, ctl, n * d, NT, width};
+  return launch_ts_any(width, false, a, st, false);
+}
+
 cudaError_t tc_sym_product(const void* packed, int n, int d, bool f8, const float* X, uint8_t* xt, float* Y,
                            Ctl* ctl, const int* skip, cudaStream_t st) {
   const int NT = ts_tile_rows(n, d), N = ts_width(d);

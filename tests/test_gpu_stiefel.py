@@ -82,3 +82,36 @@ def test_stiefel_update_norm_stop(P):
     assert info.iters < 500 and info.last_update_norm < 1e-6
     Xb = to64(X).reshape(n, d, p)
     assert np.max(np.abs(Xb @ np.swapaxes(Xb, 1, 2) - np.eye(d))) < 1e-4  # rows stay orthonormal
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("n,d,p", [(40, 16, 24), (30, 10, 13), (12, 40, 48)])
+def test_stiefel_on_symmetric_tiles(P, n, d, p, storage):
+    """d > 8: the product reads the symmetric tiles once (float32 tiles on the CUDA
+    cores, bfloat16 tiles on the tensor cores) with X of p columns.  Float32 tiles
+    match the oracle as the dense form does; bfloat16 tiles (A and X rounded for the
+    product) stay within 1e-3 RMS of it over 5 iterations."""
+    T, K = 5, 2
+    inst = synth.make_instance(n, d, synth.sigma_rule(0.3, n, d), seed=n + d + p, dtype=np.float32)
+    A = inst.dense()
+    X0 = start(inst, A, n, d, p)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.STORAGE[storage])
+    x0 = torch.from_numpy(X0.astype(np.float32)).cuda()
+    XT, info = P.nsrgs_stiefel_solve(pa, p, 1.0 / n, T, K, x0)
+    torch.cuda.synchronize()
+    ref = X0
+    for _ in range(T):
+        ref = O.stiefel_iteration(A, ref, n, d, 1.0 / n, K)
+    assert info.iters == T and info.flags == 0, info.as_dict()
+    err = np.linalg.norm(to64(XT) - ref) / math.sqrt(n * d * p)
+    assert err <= (1e-5 if storage == "f32" else 1e-3), err
+
+
+def test_stiefel_bf16_tiles_refuse_a_width_class_change(P):
+    """The bfloat16 tiles' visiting order depends on the tile width; p must keep d's class."""
+    n, d, p = 10, 16, 40
+    inst = synth.make_instance(n, d, 0.3, seed=2, dtype=np.float32)
+    pa = P.nsrgs_pack_upper(torch.from_numpy(inst.upper).cuda(), n, d, P.BF16)
+    x0 = torch.zeros(n * d, p, device="cuda")
+    with pytest.raises(P.NsrgsError):
+        P.nsrgs_stiefel_solve(pa, p, 0.1, 1, 2, x0)
