@@ -350,8 +350,10 @@ nsrgs_status nsrgs_stiefel_solve(const nsrgs_A* A, int p, float eta, int T, int 
  * whose tangent projection vanishes on O(d), is dropped as Algorithm 2 drops
  * X_j^T X_j).  The whole gradient comes from one read of a packed matrix of
  * augmented (d+1) x (d+1) blocks B_ij = [[A_ij, sqrt(kappa) c_ij], [0, w_ij]] in the
- * symmetric panel layout, multiplied with [[X_j, 0], [sqrt(kappa) t_j^T, 1]].
- * d <= 7; storage NSRGS_F32 or NSRGS_BF16 (FP8's per-row scale would store the unit
+ * symmetric layout of that block size (panels up to d + 1 = 8, the float32 or
+ * bfloat16 tiles above), multiplied with [[X_j, 0], [sqrt(kappa) t_j^T, 1]].
+ * d <= 63 (the node update in registers up to d = 7, a CTA per node above);
+ * storage NSRGS_F32 or NSRGS_BF16 (FP8's per-row scale would store the unit
  * weights w_ij inexactly and skew the translations). */
 
 /* Bytes of the packed augmented matrix: nsrgs_packed_bytes(n, d + 1, storage);

@@ -30,6 +30,7 @@ nsrgs_status pack_se_impl(const float*, const float*, int, int, float, int, void
 cudaError_t se_launch(int what, int d, const float* X, float* t, const float* Xa0, float* Ya, float* Xa1, int n,
                       float eta, float eta_t, float kappa, int K, double tol, Ctl* ctl, float* Xout,
                       cudaStream_t st);
+cudaError_t se_prepare(int d);
 long long dense_pitch(int n, int d);
 cudaError_t stream_panel(const void* packed, const PanelGeom& g, const float* X, float* Y, Ctl* ctl,
                          const int* skip, cudaStream_t st);
@@ -788,12 +789,12 @@ static nsrgs_status solve_impl(const nsrgs_A* A, float eta, int T, int K, double
 static bool se_storage(int storage) { return storage == NSRGS_F32 || storage == NSRGS_BF16; }
 
 size_t nsrgs_se_packed_bytes(int n, int d, int storage) {
-  if (d < 1 || d > 7 || !se_storage(storage)) return 0;
+  if (d < 1 || d > 63 || !se_storage(storage)) return 0;
   return nsrgs_packed_bytes(n, d + 1, storage);
 }
 
 size_t nsrgs_se_workspace_bytes(int n, int d) {
-  if (d < 1 || d > 7) return 0;
+  if (d < 1 || d > 63) return 0;
   return nsrgs_workspace_bytes(n, d + 1);
 }
 
@@ -801,8 +802,8 @@ nsrgs_status nsrgs_se_pack(const float* upper_a, const float* upper_c, int n, in
                            void* packed, void* stv) {
   nsrgs_status s = check_nd(n, d);
   if (s != NSRGS_OK) return s;
-  NSRGS_CHECK_ARG(d <= 7, "the SE(d) form covers d <= 7 (augmented blocks of d + 1 <= 8)");
-  NSRGS_CHECK_ARG(se_storage(storage), "the SE(d) form stores NSRGS_F32 or NSRGS_BF16 panels");
+  NSRGS_CHECK_ARG(d <= 63, "the SE(d) form covers d <= 63 (augmented blocks of d + 1 <= 64)");
+  NSRGS_CHECK_ARG(se_storage(storage), "the SE(d) form stores NSRGS_F32 or NSRGS_BF16");
   NSRGS_CHECK_ARG(kappa >= 0.f && isfinite(kappa), "kappa must be finite and >= 0");
   NSRGS_CHECK_ARG(upper_a && upper_c && packed && aligned16(packed), "null or misaligned pointer");
   return pack_se_impl(upper_a, upper_c, n, d, kappa, storage, packed, (cudaStream_t)stv);
@@ -811,8 +812,8 @@ nsrgs_status nsrgs_se_pack(const float* upper_a, const float* upper_c, int n, in
 nsrgs_status nsrgs_se_solve(const nsrgs_A* B, float kappa, float eta, float eta_t, int T, int K, double tol,
                             float* X, float* t, nsrgs_info* info, void* ws, size_t ws_bytes, void* stv) {
   NSRGS_CHECK_ARG(B != nullptr, "B is null");
-  NSRGS_CHECK_ARG(B->d >= 2 && B->d <= 8 && se_storage(B->storage),
-                  "B must be an nsrgs_se_pack result: d + 1 in [2, 8], panel storage");
+  NSRGS_CHECK_ARG(B->d >= 2 && B->d <= 64 && se_storage(B->storage),
+                  "B must be an nsrgs_se_pack result: d + 1 in [2, 64], NSRGS_F32 or NSRGS_BF16");
   PanelGeom g{};
   nsrgs_status s = check_A(B, &g);
   if (s != NSRGS_OK) return s;
@@ -832,6 +833,7 @@ nsrgs_status nsrgs_se_solve(const nsrgs_A* B, float kappa, float eta, float eta_
   const bool timing = g_timing != 0;
   if (timing) NSRGS_CUDA_TRY(ensure_events(dev, T));
   const cudaEvent_t* ev = timing ? g_timing_state[dev].ev.data() : nullptr;
+  NSRGS_CUDA_TRY(se_prepare(d));
   NSRGS_CUDA_TRY(reset_ws(w, n, D, st));
   NSRGS_CUDA_TRY(se_launch(0, d, X, t, nullptr, nullptr, w.X[0], n, eta, eta_t, kappa, K, tol, w.ctl, nullptr, st));
   for (int it = 0; it < T; ++it) {

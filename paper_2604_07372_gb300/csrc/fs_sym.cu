@@ -468,5 +468,6 @@ cudaError_t fs_sym_pack(Src src, int n, int d, void* packed, cudaStream_t st) {
 }
 template cudaError_t fs_sym_pack<UpperSrc>(UpperSrc, int, int, void*, cudaStream_t);
 template cudaError_t fs_sym_pack<DenseSrc>(DenseSrc, int, int, void*, cudaStream_t);
+template cudaError_t fs_sym_pack<SeAugSrc>(SeAugSrc, int, int, void*, cudaStream_t);
 
 }  // namespace nsrgs

@@ -185,7 +185,7 @@ static nsrgs_status pack_any(Src src, int n, int d, int storage, void* packed, c
     NSRGS_CUDA_TRY(cudaGetLastError());
     return NSRGS_OK;
   }
-  if constexpr (!std::is_same_v<Src, SeAugSrc>) {  // the SE(d) form uses panels only
+  {  // tile layouts (also the SE(d) form's augmented blocks above D = 8)
     if (tile_storage(storage, d) && !tile_fp8(storage)) {
       NSRGS_CUDA_TRY(tc_sym_pack(src, n, d, false, packed, st));
       return NSRGS_OK;

@@ -793,5 +793,6 @@ cudaError_t tc_sym_pack(Src src, int n, int d, bool f8, void* packed, cudaStream
 }
 template cudaError_t tc_sym_pack<UpperSrc>(UpperSrc, int, int, bool, void*, cudaStream_t);
 template cudaError_t tc_sym_pack<DenseSrc>(DenseSrc, int, int, bool, void*, cudaStream_t);
+template cudaError_t tc_sym_pack<SeAugSrc>(SeAugSrc, int, int, bool, void*, cudaStream_t);
 
 }  // namespace nsrgs

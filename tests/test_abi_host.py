@@ -90,12 +90,13 @@ def test_bad_arguments_are_rejected_without_a_device(L):
                                 None) == 1
     assert b"header" in lib.nsrgs_last_error()
     # SE(d) form: shapes outside it are rejected before any device work
-    assert lib.nsrgs_se_packed_bytes(100, 8, 0) == 0 and lib.nsrgs_se_packed_bytes(100, 3, 2) == 0
+    assert lib.nsrgs_se_packed_bytes(100, 64, 0) == 0 and lib.nsrgs_se_packed_bytes(100, 3, 2) == 0
+    assert lib.nsrgs_se_packed_bytes(100, 8, 0) == lib.nsrgs_packed_bytes(100, 9, 0) > 0  # float32 tiles
     assert lib.nsrgs_se_packed_bytes(100, 3, 0) == lib.nsrgs_packed_bytes(100, 4, 0) > 0
     assert lib.nsrgs_se_workspace_bytes(100, 3) == lib.nsrgs_workspace_bytes(100, 4) > 0
-    assert lib.nsrgs_se_pack(buf, buf, 100, 8, 0.1, 0, buf, None) == 1
+    assert lib.nsrgs_se_pack(buf, buf, 100, 64, 0.1, 0, buf, None) == 1
     assert lib.nsrgs_se_pack(buf, buf, 100, 3, -0.1, 0, buf, None) == 1
-    A = L._lib._A(16, 100, 9, 0)  # augmented blocks of 9: outside the form
+    A = L._lib._A(16, 100, 65, 0)  # augmented blocks of 65: outside the form
     assert lib.nsrgs_se_solve(ctypes.byref(A), 0.1, 0.01, 1.0, 5, 2, 0.0, buf, buf, None, buf, 0, None) == 1
 
 

@@ -150,8 +150,8 @@ def test_reduced_precision_errors_within_one_percent(P, storage):
 
 def test_unsupported_shapes_are_rejected(P):
     s = make(10, 3, seed=1)
-    with pytest.raises(P.NsrgsError):
-        P.nsrgs_se_pack(dev(np.zeros((45, 8, 8))), dev(np.zeros((45, 8))), 10, 8, 0.1, P.F32)
+    with pytest.raises(P.NsrgsError):  # augmented blocks of 65 > 64
+        P.nsrgs_se_pack(dev(np.zeros((45, 64, 64))), dev(np.zeros((45, 64))), 10, 64, 0.1, P.F32)
     with pytest.raises(P.NsrgsError):
         P.nsrgs_se_pack(dev(s.rot.upper), dev(s.c_upper), 10, 3, -1.0, P.F32)
     with pytest.raises(P.NsrgsError):
@@ -193,3 +193,43 @@ def test_largest_d_one_iteration_matches_oracle(P, storage):
     assert info.iters == 1 and info.flags == 0, info.as_dict()
     assert np.max(np.abs(X.double().cpu().numpy() - Xo)) <= 2e-5
     assert np.max(np.abs(t.double().cpu().numpy() - to)) <= 1e-4
+
+
+@pytest.mark.parametrize("n,d,storage", [(40, 8, "f32"), (30, 15, "f32"), (16, 31, "f32"), (30, 15, "bf16")])
+def test_generic_d_one_iteration_matches_oracle(P, n, d, storage):
+    """d >= 8: augmented blocks of d + 1 >= 9 in the tile layouts (float32 tiles on
+    the CUDA cores, bfloat16 tiles on the tensor cores) and the node update on a CTA
+    per node.  Float32 tiles match the oracle as the panels do; bfloat16 tiles round
+    both the measurements and the augmented iterate for the product (about 2^-8 of
+    each term), within 3e-3 (X) and 2e-2 (t) of the oracle on the unrounded data."""
+    s = make(n, d, seed=5 * d + n)
+    kappa = 1.0 / (4 * d)
+    eta, eta_t = 1.0 / n, 1.0 / (kappa * n)
+    A, C, W = oracle_inputs(s)
+    X0, t0 = start(s)
+    Xo, to = O.se_iteration(A, C, W, X0, t0, n, d, eta, eta_t, kappa, 2)
+    B = se_pack(P, s, kappa, P.STORAGE[storage])
+    X, t, info = P.nsrgs_se_solve(B, kappa, eta, eta_t, 1, 2, dev(X0), dev(t0))
+    torch.cuda.synchronize()
+    assert info.iters == 1 and info.flags == 0, info.as_dict()
+    tx, tt = (2e-5, 1e-4) if storage == "f32" else (3e-3, 2e-2)
+    assert np.max(np.abs(X.double().cpu().numpy() - Xo)) <= tx
+    assert np.max(np.abs(t.double().cpu().numpy() - to)) <= tt
+
+
+def test_generic_d_solve_matches_oracle(P):
+    """d = 12, ten iterations on float32 tiles against the oracle's SE(d) loop."""
+    n, d, T, K = 40, 12, 10, 2
+    s = make(n, d, seed=12)
+    kappa = 1.0 / (4 * d)
+    eta, eta_t = 1.0 / n, 1.0 / (kappa * n)
+    A, C, W = oracle_inputs(s)
+    X0, t0 = start(s)
+    Xo, to = X0, t0
+    for _ in range(T):
+        Xo, to = O.se_iteration(A, C, W, Xo, to, n, d, eta, eta_t, kappa, K)
+    X, t, info = P.nsrgs_se_solve(se_pack(P, s, kappa, P.F32), kappa, eta, eta_t, T, K, dev(X0), dev(t0))
+    torch.cuda.synchronize()
+    assert info.iters == T
+    assert np.linalg.norm(X.double().cpu().numpy() - Xo) / math.sqrt(n * d * d) <= 1e-5
+    assert np.linalg.norm(t.double().cpu().numpy() - to) / math.sqrt(n * d) <= 1e-4
