@@ -60,7 +60,7 @@ def parse_args():
                     help="run only one extra leg (prints its JSON, no metric line), for profiling")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-n", type=int, default=500, help="n of every instance in --leg batch_paths")
-    ap.add_argument("--sweep-dims", default="3,8,16,32,64")
+    ap.add_argument("--sweep-dims", default="3,8,16,25,32,64")
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-n", type=int, default=2000, help="n of the dimension-sweep leg")
     ap.add_argument("--se-n", type=int, default=10000, help="n of the SE(d) leg (--leg se)")
@@ -331,9 +331,9 @@ def batch_paths_leg(P, synth, seed: int, count: int = 152, n: int = 500, T: int 
 
 
 # ------------------------------------------------------- dimension sweep
-def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps: int = 5, T: int = 20,
+def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 25, 32, 64), reps: int = 5, T: int = 20,
                only=None):
-    """n = 2000, d in {3, 8, 16, 32, 64}, c = 0.3: the A-stream product per storage
+    """n = 2000, d in {3, 8, 16, 25, 32, 64}, c = 0.3: the A-stream product per storage
     (ms, algorithmic GB/s), and short solves (T = 20) for iterations/s and final d_F."""
     import numpy as np
     import torch
@@ -342,8 +342,11 @@ def dsweep_leg(P, synth, seed: int, n: int = 2000, dims=(3, 8, 16, 32, 64), reps
     for d in dims:
         Z, up = synth.device_upper(n, d, synth.sigma_rule(0.3, n, d), seed=seed + d)
         # f32: panels for d <= 8, the float32 tile-upper stream above (CUDA cores, half the dense bytes)
-        storages = (["dense_f32", "f32"] + (["bf16"] if d <= 8 else []) +
-                    (["dense_bf16", "bf16", "fp8"] if d in (16, 32, 64) else []))
+        # d not in {16, 32, 64} above 8 (the paper's d = 25): BF16 / FP8 on tiles of width
+        # 32 with the rows past d zero; the plain dense forms are left out there
+        storages = ((["dense_f32", "f32"] if d <= 8 or d in (16, 32, 64) else ["f32"]) +
+                    (["bf16"] if d <= 8 else []) +
+                    (["dense_bf16", "bf16", "fp8"] if d in (16, 32, 64) else (["bf16", "fp8"] if d > 8 else [])))
         if only:
             storages = [x for x in storages if x in only]
         res = {}
